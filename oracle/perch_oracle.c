@@ -1,0 +1,571 @@
+/*
+ * PERCH 2.0 hypothesis scoring -- plain, slow CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the parity reference for the CUDA
+ * path.  Only the tests, the smoke check and the CPU-baseline leg of the bench
+ * may load it; the product library never links, calls or falls back to it, and
+ * it shares no code, header or table with the CUDA sources.
+ *
+ * What it computes, per object-pose hypothesis h (Sec. III-B Eq. 1-2,
+ * Sec. IV-A "Parallel Rendering" / "Parallel Cost Computation", Eq. 3,
+ * Sec. IV-B Eq. 4, Sec. V-C):
+ *   render the mesh at h into an integer depth z-buffer, back-project the
+ *   visible pixels, drop those hidden behind the observed depth (R \ C), and
+ *   classify each remaining rendered point q against the observed cloud I:
+ *   q is explained iff its nearest observed neighbour p lies within delta
+ *   (Eq. 2) and, with the colour check on, the CIEDE2000 difference of the two
+ *   colours is at most tau_c (Eq. 4).  J_r counts the unexplained q.  Each
+ *   observed p inside the admissible set V(h) is an inlier iff it was found as
+ *   the nearest neighbour of an explained q (the J_o kernel of Sec. IV-A);
+ *   J_o counts the others.
+ *
+ * Every float line is one IEEE binary32 operation, evaluated in the order
+ * written, with no contraction (build with -ffp-contract=off, no fast-math);
+ * integer rounding is rintf/llrintf (ties to even).  Edge functions are exact
+ * integers (int64 here; their magnitude stays below 2^31 by the guard band).
+ * Nearest neighbours are found by brute force over all of I (Eq. 2 as
+ * written).  Colour conversion and CIEDE2000 are evaluated in binary32 with
+ * the C library's float functions -- the same precision as the CUDA path --
+ * and every rendered point whose colour difference lies within 1e-3 of tau_c,
+ * or whose hue difference lies within 1e-3 degree of the 180-degree wrap, is
+ * counted in a per-hypothesis band report.
+ *
+ * Readings of the paper (it is silent on these): pixel centres at integer
+ * coordinates; 4 sub-pixel bits; no clipping (triangles with a vertex nearer
+ * than z_near or outside [-W,2W)x[-H,2H) are culled whole); two-sided
+ * rasterisation; top-left style tie rule; perspective-correct 1/Z depth;
+ * nearest depth wins, then lowest triangle id; affine integer colour
+ * interpolation; occluder margin m; nearest-neighbour ties to the lowest pixel
+ * index; V(h) is the object's inscribed cylinder about its z axis, or
+ * labels == object label inside the ROI when labels are used (Sec. V-C).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_EMPTY UINT64_MAX
+#define OR_NWORK 8
+
+typedef struct {
+    int32_t W, H;
+    float fx, fy, cx, cy;
+    const uint16_t *depth;    /* H*W, 0.1 mm units, 0 = invalid            */
+    const uint8_t *rgb;       /* H*W*3                                      */
+    const int32_t *labels;    /* H*W or NULL                                */
+    float delta;              /* metres                                     */
+    float tau_c;              /* CIEDE2000 threshold                        */
+    int32_t color_check;      /* 0/1                                        */
+    int32_t stride;           /* image-space downsampling factor s >= 1     */
+    int32_t occ_margin;       /* occluder margin m, 0.1 mm units            */
+    float z_near;             /* metres                                     */
+} or_scene;
+
+typedef struct {
+    const float *verts;       /* V*3 object frame, metres                   */
+    const uint8_t *rgb;       /* V*3                                        */
+    int32_t n_verts;
+    const int32_t *tris;      /* T*3                                        */
+    int32_t n_tris;
+    float vol_r, vol_h;       /* admissible cylinder                        */
+} or_mesh;
+
+/* ---------------------------------------------------------------------- */
+/* colour: sRGB (IEC 61966-2-1) -> XYZ (D65) -> CIELAB, binary32           */
+/* ---------------------------------------------------------------------- */
+
+static float srgb_to_linear(uint8_t c8)
+{
+    float c = (float)c8 / 255.0f;
+    if (c <= 0.04045f)
+        return c / 12.92f;
+    return powf((c + 0.055f) / 1.055f, 2.4f);
+}
+
+static float lab_f(float t)
+{
+    const float eps = 216.0f / 24389.0f;     /* (6/29)^3            */
+    const float kappa = 24389.0f / 27.0f;    /* (29/3)^3            */
+    if (t > eps)
+        return cbrtf(t);
+    return (kappa * t + 16.0f) / 116.0f;
+}
+
+void or_srgb_to_lab(const uint8_t rgb[3], float lab[3])
+{
+    float r = srgb_to_linear(rgb[0]);
+    float g = srgb_to_linear(rgb[1]);
+    float b = srgb_to_linear(rgb[2]);
+    float X = (0.4124564f * r + 0.3575761f * g) + 0.1804375f * b;
+    float Y = (0.2126729f * r + 0.7151522f * g) + 0.0721750f * b;
+    float Z = (0.0193339f * r + 0.1191920f * g) + 0.9503041f * b;
+    float fx = lab_f(X / 0.95047f);
+    float fy = lab_f(Y / 1.00000f);
+    float fz = lab_f(Z / 1.08883f);
+    lab[0] = 116.0f * fy - 16.0f;
+    lab[1] = 500.0f * (fx - fy);
+    lab[2] = 200.0f * (fy - fz);
+}
+
+/* CIEDE2000 colour difference (kL = kC = kH = 1), binary32.  The optional
+ * output wrap_gap is | |h1' - h2'| - 180 deg | in degrees (or 1e9 when a
+ * chroma is zero), used for the hue-wrap band. */
+float or_ciede2000(const float lab1[3], const float lab2[3], float *wrap_gap)
+{
+    const float PI = 3.14159265358979f;
+    const float DEG = PI / 180.0f;
+    const float P25_7 = 6103515625.0f;     /* 25^7 */
+    float L1 = lab1[0], a1 = lab1[1], b1 = lab1[2];
+    float L2 = lab2[0], a2 = lab2[1], b2 = lab2[2];
+
+    float C1 = sqrtf(a1 * a1 + b1 * b1);
+    float C2 = sqrtf(a2 * a2 + b2 * b2);
+    float Cb = (C1 + C2) / 2.0f;
+    float Cb7 = Cb * Cb * Cb * Cb * Cb * Cb * Cb;
+    float G = 0.5f * (1.0f - sqrtf(Cb7 / (Cb7 + P25_7)));
+    float a1p = (1.0f + G) * a1;
+    float a2p = (1.0f + G) * a2;
+    float C1p = sqrtf(a1p * a1p + b1 * b1);
+    float C2p = sqrtf(a2p * a2p + b2 * b2);
+
+    float h1p = (a1p == 0.0f && b1 == 0.0f) ? 0.0f : atan2f(b1, a1p);
+    if (h1p < 0.0f) h1p += 2.0f * PI;
+    float h2p = (a2p == 0.0f && b2 == 0.0f) ? 0.0f : atan2f(b2, a2p);
+    if (h2p < 0.0f) h2p += 2.0f * PI;
+
+    float dLp = L2 - L1;
+    float dCp = C2p - C1p;
+    float CC = C1p * C2p;
+    float dhp = 0.0f;
+    if (CC != 0.0f) {
+        dhp = h2p - h1p;
+        if (dhp > PI) dhp -= 2.0f * PI;
+        else if (dhp < -PI) dhp += 2.0f * PI;
+    }
+    float dHp = 2.0f * sqrtf(CC) * sinf(dhp / 2.0f);
+
+    float Lbp = (L1 + L2) / 2.0f;
+    float Cbp = (C1p + C2p) / 2.0f;
+    float hbp;
+    if (CC == 0.0f)
+        hbp = h1p + h2p;
+    else if (fabsf(h1p - h2p) <= PI)
+        hbp = (h1p + h2p) / 2.0f;
+    else if (h1p + h2p < 2.0f * PI)
+        hbp = (h1p + h2p + 2.0f * PI) / 2.0f;
+    else
+        hbp = (h1p + h2p - 2.0f * PI) / 2.0f;
+    if (wrap_gap)
+        *wrap_gap = (CC == 0.0f) ? 1e9f : fabsf(fabsf(h1p - h2p) - PI) / DEG;
+
+    float T = 1.0f - 0.17f * cosf(hbp - 30.0f * DEG) + 0.24f * cosf(2.0f * hbp)
+              + 0.32f * cosf(3.0f * hbp + 6.0f * DEG) - 0.20f * cosf(4.0f * hbp - 63.0f * DEG);
+    float hdeg = hbp / DEG;
+    float q = (hdeg - 275.0f) / 25.0f;
+    float dtheta = 30.0f * DEG * expf(-(q * q));
+    float Cbp7 = Cbp * Cbp * Cbp * Cbp * Cbp * Cbp * Cbp;
+    float RC = 2.0f * sqrtf(Cbp7 / (Cbp7 + P25_7));
+    float l50 = (Lbp - 50.0f) * (Lbp - 50.0f);
+    float SL = 1.0f + 0.015f * l50 / sqrtf(20.0f + l50);
+    float SC = 1.0f + 0.045f * Cbp;
+    float SH = 1.0f + 0.015f * Cbp * T;
+    float RT = -sinf(2.0f * dtheta) * RC;
+    float tL = dLp / SL, tC = dCp / SC, tH = dHp / SH;
+    return sqrtf(tL * tL + tC * tC + tH * tH + RT * tC * tH);
+}
+
+/* ---------------------------------------------------------------------- */
+/* rasterisation                                                           */
+/* ---------------------------------------------------------------------- */
+
+/* Edge function E(a,b,p) = (b.x-a.x)(p.y-a.y) - (b.y-a.y)(p.x-a.x). */
+static int64_t edge(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t px, int64_t py)
+{
+    return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+/* An edge with direction (dx,dy) owns the samples lying exactly on it iff
+ * dy > 0, or dy == 0 and dx < 0. */
+static int owns_edge(int64_t dx, int64_t dy)
+{
+    return dy > 0 || (dy == 0 && dx < 0);
+}
+
+static int64_t floor_div16(int64_t x) { return x >= 0 ? x / 16 : -((-x + 15) / 16); }
+static int64_t ceil_div16(int64_t x) { return -floor_div16(-x); }
+
+/* Screen-space set-up of one triangle at a pose: returns 0 if culled or
+ * degenerate.  xs/ys are the snapped vertex positions (1/16 px), iz = 1/Z,
+ * vid the mesh vertex ids after the orientation swap, A > 0 the doubled area. */
+typedef struct {
+    int64_t xs[3], ys[3];
+    float iz[3];
+    int32_t vid[3];
+    int64_t A;
+} or_tri;
+
+static int setup_triangle(const or_scene *sc, const or_mesh *m, const float *P, int32_t t,
+                          or_tri *o, int *culled)
+{
+    *culled = 0;
+    for (int k = 0; k < 3; k++) {
+        int32_t vi = m->tris[3 * t + k];
+        float vx = m->verts[3 * vi + 0], vy = m->verts[3 * vi + 1], vz = m->verts[3 * vi + 2];
+        /* C1: X = R v + t */
+        float X = ((P[0] * vx + P[1] * vy) + P[2] * vz) + P[3];
+        float Y = ((P[4] * vx + P[5] * vy) + P[6] * vz) + P[7];
+        float Z = ((P[8] * vx + P[9] * vy) + P[10] * vz) + P[11];
+        if (!(Z >= sc->z_near)) { *culled = 1; return 0; }
+        /* C2: pinhole projection, 4 sub-pixel bits */
+        float px = sc->fx * (X / Z) + sc->cx;
+        float py = sc->fy * (Y / Z) + sc->cy;
+        float sx = px * 16.0f;
+        float sy = py * 16.0f;
+        if (!(sx >= (float)(-16 * sc->W)) || !(sx < (float)(32 * sc->W)) ||
+            !(sy >= (float)(-16 * sc->H)) || !(sy < (float)(32 * sc->H))) {
+            *culled = 1;
+            return 0;
+        }
+        o->xs[k] = (int64_t)llrintf(sx);
+        o->ys[k] = (int64_t)llrintf(sy);
+        o->iz[k] = 1.0f / Z;
+        o->vid[k] = vi;
+    }
+    int64_t A = edge(o->xs[0], o->ys[0], o->xs[1], o->ys[1], o->xs[2], o->ys[2]);
+    if (A == 0)
+        return 0;
+    if (A < 0) {   /* two-sided: swap b and c */
+        int64_t tx = o->xs[1], ty = o->ys[1];
+        float ti = o->iz[1];
+        int32_t tv = o->vid[1];
+        o->xs[1] = o->xs[2]; o->ys[1] = o->ys[2]; o->iz[1] = o->iz[2]; o->vid[1] = o->vid[2];
+        o->xs[2] = tx; o->ys[2] = ty; o->iz[2] = ti; o->vid[2] = tv;
+        A = -A;
+    }
+    o->A = A;
+    return 1;
+}
+
+/* Edge values (w0,w1,w2) of pixel (u,v); returns 1 iff the sample is covered. */
+static int coverage(const or_tri *o, int64_t u, int64_t v, int64_t w[3])
+{
+    int64_t sx = 16 * u, sy = 16 * v;
+    const int64_t *x = o->xs, *y = o->ys;
+    w[0] = edge(x[1], y[1], x[2], y[2], sx, sy);   /* edge b -> c */
+    w[1] = edge(x[2], y[2], x[0], y[0], sx, sy);   /* edge c -> a */
+    w[2] = edge(x[0], y[0], x[1], y[1], sx, sy);   /* edge a -> b */
+    int64_t dxs[3] = {x[2] - x[1], x[0] - x[2], x[1] - x[0]};
+    int64_t dys[3] = {y[2] - y[1], y[0] - y[2], y[1] - y[0]};
+    for (int i = 0; i < 3; i++) {
+        if (w[i] > 0)
+            continue;
+        if (w[i] == 0 && owns_edge(dxs[i], dys[i]))
+            continue;
+        return 0;
+    }
+    return 1;
+}
+
+static void clip_roi(const or_scene *sc, const int32_t roi[4], int64_t *u0, int64_t *v0,
+                     int64_t *u1, int64_t *v1)
+{
+    *u0 = roi[0] > 0 ? roi[0] : 0;
+    *v0 = roi[1] > 0 ? roi[1] : 0;
+    *u1 = roi[2] < sc->W ? roi[2] : sc->W;
+    *v1 = roi[3] < sc->H ? roi[3] : sc->H;
+}
+
+/* Render one hypothesis into keys[H*W]: key = (d << 32) | triangle id, the
+ * smallest key wins (nearest depth, then lowest id); OR_EMPTY where nothing
+ * covers.  work (may be NULL) accumulates [setups, culled, fragments]. */
+int or_render_keys(const or_scene *sc, const or_mesh *m, const float pose[12],
+                   const int32_t roi[4], uint64_t *keys, int64_t *work)
+{
+    int64_t W = sc->W, H = sc->H;
+    for (int64_t i = 0; i < W * H; i++)
+        keys[i] = OR_EMPTY;
+    int64_t ru0, rv0, ru1, rv1;
+    clip_roi(sc, roi, &ru0, &rv0, &ru1, &rv1);
+    for (int32_t t = 0; t < m->n_tris; t++) {
+        or_tri o;
+        int culled;
+        if (work) work[0]++;
+        if (!setup_triangle(sc, m, pose, t, &o, &culled)) {
+            if (work && culled) work[1]++;
+            continue;
+        }
+        int64_t xmin = o.xs[0], xmax = o.xs[0], ymin = o.ys[0], ymax = o.ys[0];
+        for (int k = 1; k < 3; k++) {
+            if (o.xs[k] < xmin) xmin = o.xs[k];
+            if (o.xs[k] > xmax) xmax = o.xs[k];
+            if (o.ys[k] < ymin) ymin = o.ys[k];
+            if (o.ys[k] > ymax) ymax = o.ys[k];
+        }
+        int64_t u0 = ceil_div16(xmin), u1 = floor_div16(xmax);
+        int64_t v0 = ceil_div16(ymin), v1 = floor_div16(ymax);
+        if (u0 < ru0) u0 = ru0;
+        if (v0 < rv0) v0 = rv0;
+        if (u1 > ru1 - 1) u1 = ru1 - 1;
+        if (v1 > rv1 - 1) v1 = rv1 - 1;
+        for (int64_t v = v0; v <= v1; v++) {
+            for (int64_t u = u0; u <= u1; u++) {
+                int64_t w[3];
+                if (!coverage(&o, u, v, w))
+                    continue;
+                /* C4: perspective-correct depth from interpolated 1/Z */
+                float num = ((float)w[0] * o.iz[0] + (float)w[1] * o.iz[1]) + (float)w[2] * o.iz[2];
+                float iz = num / (float)o.A;
+                float z = 1.0f / iz;
+                float dz = z * 10000.0f;
+                if (!(dz < 4294967296.0f))
+                    continue;
+                int64_t d = (int64_t)llrintf(dz);
+                if (d < 1 || d > 4294967295LL)
+                    continue;
+                if (work) work[2]++;
+                uint64_t key = ((uint64_t)d << 32) | (uint64_t)(uint32_t)t;
+                if (key < keys[v * W + u])
+                    keys[v * W + u] = key;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* point clouds                                                            */
+/* ---------------------------------------------------------------------- */
+
+/* C7: back-projection of pixel (u,v) at integer depth d (0.1 mm). */
+static void back_project(const or_scene *sc, int64_t u, int64_t v, int64_t d, float p[3])
+{
+    float z = (float)d / 10000.0f;
+    p[0] = (((float)u - sc->cx) * z) / sc->fx;
+    p[1] = (((float)v - sc->cy) * z) / sc->fy;
+    p[2] = z;
+}
+
+/* The observed cloud I: every valid pixel whose coordinates are multiples of
+ * the stride, in increasing pixel index.  xyz (n*3), lab (n*3), pix (n) may be
+ * NULL; returns n. */
+int64_t or_observed_points(const or_scene *sc, float *xyz, float *lab, int32_t *pix)
+{
+    int64_t n = 0, s = sc->stride;
+    for (int64_t v = 0; v < sc->H; v++)
+        for (int64_t u = 0; u < sc->W; u++) {
+            int64_t i = v * sc->W + u;
+            if (u % s != 0 || v % s != 0 || sc->depth[i] == 0)
+                continue;
+            if (xyz) back_project(sc, u, v, sc->depth[i], xyz + 3 * n);
+            if (lab) or_srgb_to_lab(sc->rgb + 3 * i, lab + 3 * n);
+            if (pix) pix[n] = (int32_t)i;
+            n++;
+        }
+    return n;
+}
+
+/* Resolve the key buffer of one hypothesis into its rendered cloud R \ C:
+ * visible pixels at stride positions that are not hidden behind the observed
+ * depth (C5-C7).  Outputs (capacity H*W): xyz n*3, rgb n*3, pix n.  Returns n. */
+int64_t or_rendered_points(const or_scene *sc, const or_mesh *m, const float pose[12],
+                           int32_t label, const uint64_t *keys, float *xyz, uint8_t *rgb,
+                           int32_t *pix)
+{
+    int64_t n = 0, s = sc->stride;
+    for (int64_t v = 0; v < sc->H; v++)
+        for (int64_t u = 0; u < sc->W; u++) {
+            int64_t i = v * sc->W + u;
+            uint64_t key = keys[i];
+            if (key == OR_EMPTY || u % s != 0 || v % s != 0)
+                continue;
+            int64_t d = (int64_t)(key >> 32);
+            int32_t t = (int32_t)(key & 0xffffffffu);
+            /* C6: occluders -- the observed surface is nearer by more than m */
+            int64_t dobs = sc->depth[i];
+            if (dobs > 0 && dobs + sc->occ_margin < d &&
+                (label < 0 || sc->labels == NULL || sc->labels[i] != label))
+                continue;
+            or_tri o;
+            int culled;
+            setup_triangle(sc, m, pose, t, &o, &culled);
+            int64_t w[3];
+            coverage(&o, u, v, w);
+            /* C5: affine integer colour, rounded half up */
+            for (int k = 0; k < 3; k++) {
+                int64_t c = w[0] * m->rgb[3 * o.vid[0] + k] + w[1] * m->rgb[3 * o.vid[1] + k]
+                            + w[2] * m->rgb[3 * o.vid[2] + k] + o.A / 2;
+                if (rgb) rgb[3 * n + k] = (uint8_t)(c / o.A);
+            }
+            if (xyz) back_project(sc, u, v, d, xyz + 3 * n);
+            if (pix) pix[n] = (int32_t)i;
+            n++;
+        }
+    return n;
+}
+
+/* C11: is observed point p (pixel i) in the admissible set V(h)? */
+static int in_volume(const or_scene *sc, const or_mesh *m, const float *P, int32_t label,
+                     const int32_t roi[4], int64_t i, const float p[3])
+{
+    if (label >= 0) {
+        int64_t u = i % sc->W, v = i / sc->W;
+        return sc->labels[i] == label && u >= roi[0] && u < roi[2] && v >= roi[1] && v < roi[3];
+    }
+    float e0 = p[0] - P[3], e1 = p[1] - P[7], e2 = p[2] - P[11];
+    float q0 = (P[0] * e0 + P[4] * e1) + P[8] * e2;    /* R^T (p - t) */
+    float q1 = (P[1] * e0 + P[5] * e1) + P[9] * e2;
+    float q2 = (P[2] * e0 + P[6] * e1) + P[10] * e2;
+    return (q0 * q0 + q1 * q1) <= m->vol_r * m->vol_r && q2 >= 0.0f && q2 <= m->vol_h;
+}
+
+/* ---------------------------------------------------------------------- */
+/* scoring                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Score n hypotheses.  costs[2h] = J_o, costs[2h+1] = J_r.  band[h] (may be
+ * NULL) = rendered points whose colour decision lies in the tolerance band.
+ * work[8h..8h+7] (may be NULL) = triangle set-ups, culled triangles,
+ * fragments, visible pixels, kept rendered points L, delta-cell candidates
+ * (observed points in the 27 cells of edge delta around q's cell), |I cap V|,
+ * explained points.  n_threads <= 0 uses the OpenMP default. */
+int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t roi[4],
+             const float *poses, int64_t n, int32_t *costs, int32_t *band, int64_t *work,
+             int32_t n_threads)
+{
+    int64_t WH = (int64_t)sc->W * sc->H;
+    float *Ixyz = malloc(sizeof(float) * 3 * (WH + 1));
+    float *Ilab = malloc(sizeof(float) * 3 * (WH + 1));
+    int32_t *Ipix = malloc(sizeof(int32_t) * (WH + 1));
+    int32_t *Icell = malloc(sizeof(int32_t) * 3 * (WH + 1));
+    if (!Ixyz || !Ilab || !Ipix || !Icell) {
+        free(Ixyz); free(Ilab); free(Ipix); free(Icell);
+        return -2;
+    }
+    int64_t nI = or_observed_points(sc, Ixyz, Ilab, Ipix);
+    for (int64_t j = 0; j < 3 * nI; j++)
+        Icell[j] = (int32_t)floorf(Ixyz[j] / sc->delta);
+    float delta2 = sc->delta * sc->delta;
+    int rc = 0;
+#ifdef _OPENMP
+    if (n_threads > 0)
+        omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+#pragma omp parallel
+    {
+        uint64_t *keys = malloc(sizeof(uint64_t) * WH);
+        float *Rxyz = malloc(sizeof(float) * 3 * WH);
+        uint8_t *Rrgb = malloc(3 * WH);
+        int32_t *Rpix = malloc(sizeof(int32_t) * WH);
+        uint8_t *mark = malloc(nI + 1);
+        int ok = keys && Rxyz && Rrgb && Rpix && mark;
+        if (!ok) {
+#pragma omp atomic write
+            rc = -2;
+        }
+        /* every thread reaches the work-sharing loop, even one whose buffers failed */
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t h = 0; h < n; h++) {
+            if (!ok)
+                continue;
+            {
+                const float *P = poses + 12 * h;
+                int64_t wk[OR_NWORK] = {0};
+                or_render_keys(sc, m, P, roi, keys, wk);
+                for (int64_t i = 0; i < WH; i++)
+                    wk[3] += keys[i] != OR_EMPTY;
+                int64_t L = or_rendered_points(sc, m, P, label, keys, Rxyz, Rrgb, Rpix);
+                wk[4] = L;
+                memset(mark, 0, nI + 1);
+                int32_t Jr = 0, nband = 0;
+                for (int64_t k = 0; k < L; k++) {
+                    const float *q = Rxyz + 3 * k;
+                    int32_t qc0 = (int32_t)floorf(q[0] / sc->delta);
+                    int32_t qc1 = (int32_t)floorf(q[1] / sc->delta);
+                    int32_t qc2 = (int32_t)floorf(q[2] / sc->delta);
+                    float best = INFINITY;
+                    int64_t bj = -1;
+                    /* Eq. 2: nearest neighbour over all of I, ties to lowest index */
+                    for (int64_t j = 0; j < nI; j++) {
+                        const float *p = Ixyz + 3 * j;
+                        float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
+                        float d2 = (dx * dx + dy * dy) + dz * dz;
+                        if (d2 < best) { best = d2; bj = j; }
+                        const int32_t *pc = Icell + 3 * j;
+                        if (abs(pc[0] - qc0) <= 1 && abs(pc[1] - qc1) <= 1 && abs(pc[2] - qc2) <= 1)
+                            wk[5]++;
+                    }
+                    int explained = bj >= 0 && best <= delta2;
+                    if (explained && sc->color_check) {
+                        /* Eq. 4: colour of q against its nearest neighbour p'' */
+                        float lq[3], gap;
+                        or_srgb_to_lab(Rrgb + 3 * k, lq);
+                        float dE = or_ciede2000(lq, Ilab + 3 * bj, &gap);
+                        if (fabsf(dE - sc->tau_c) <= 1e-3f || gap <= 1e-3f)
+                            nband++;
+                        if (dE > sc->tau_c)
+                            explained = 0;
+                    }
+                    if (explained) {
+                        mark[bj] = 1;
+                        wk[7]++;
+                    } else {
+                        Jr++;
+                    }
+                }
+                int32_t Jo = 0;
+                for (int64_t j = 0; j < nI; j++) {
+                    if (!in_volume(sc, m, P, label, roi, Ipix[j], Ixyz + 3 * j))
+                        continue;
+                    wk[6]++;
+                    if (!mark[j])
+                        Jo++;
+                }
+                costs[2 * h] = Jo;
+                costs[2 * h + 1] = Jr;
+                if (band) band[h] = nband;
+                if (work)
+                    memcpy(work + OR_NWORK * h, wk, sizeof(wk));
+            }
+        }
+        free(keys); free(Rxyz); free(Rrgb); free(Rpix); free(mark);
+    }
+    free(Ixyz); free(Ilab); free(Ipix); free(Icell);
+    return rc;
+}
+
+/* C12: J = J_o + J_r; best = minimum J, ties to the lowest id (ids NULL: the
+ * index).  Returns -1 if n < 1. */
+int or_best(const int32_t *costs, const uint64_t *ids, int64_t n, int64_t *best_index,
+            int32_t *best_cost)
+{
+    if (n < 1)
+        return -1;
+    int64_t bi = 0;
+    int64_t bJ = (int64_t)costs[0] + costs[1];
+    for (int64_t h = 1; h < n; h++) {
+        int64_t J = (int64_t)costs[2 * h] + costs[2 * h + 1];
+        uint64_t idh = ids ? ids[h] : (uint64_t)h;
+        uint64_t idb = ids ? ids[bi] : (uint64_t)bi;
+        if (J < bJ || (J == bJ && idh < idb)) {
+            bJ = J;
+            bi = h;
+        }
+    }
+    *best_index = bi;
+    *best_cost = (int32_t)bJ;
+    return 0;
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,188 @@
+/*
+ * perch.h -- C ABI of libperch: PERCH 2.0 hypothesis scoring on one GB300 (sm_103a).
+ *
+ * The library scores object-pose hypotheses against an RGB-D observation the
+ * way PERCH 2.0 does (Agarwal, Han, Likhachev, "PERCH 2.0: Fast and Accurate
+ * GPU-based Perception via Search for Object Pose Estimation"):
+ *   for each pose h the object mesh is rendered into an integer depth z-buffer
+ *   (Sec. IV-A "Parallel Rendering"), the visible pixels are back-projected and
+ *   down-sampled in image space (Sec. IV-A), pixels hidden behind the observed
+ *   depth are removed as extraneous occluders (R_K \ C_K, Eq. 3), every
+ *   remaining rendered point q is tested against the observed cloud I within
+ *   radius delta (Eq. 2) and, optionally, by CIEDE2000 colour (Eq. 4), and the
+ *   costs J_r (unexplained rendered points) and J_o (observed points of the
+ *   admissible set V(O) not found as a nearest neighbour, Sec. IV-A "Parallel
+ *   Cost Computation") are returned per hypothesis; perch_best takes the
+ *   per-object argmin of J = J_o + J_r (Eq. 1, Sec. IV-A "Parallel Search").
+ *
+ * Conventions used by every call:
+ *   - image W x H, pixel (u,v) has its centre at integer (u,v); intrinsics
+ *     fx, fy, cx, cy map a camera point (X,Y,Z) to (fx X/Z + cx, fy Y/Z + cy);
+ *   - depth is uint16 in 0.1 mm units, 0 = no return;
+ *   - a pose is 12 float32, row-major 3x4 [R | t], object frame -> camera
+ *     frame (x right, y down, z forward), metres;
+ *   - a ROI is int32[4] = {u0, v0, u1, v1}, half-open, clipped to the image;
+ *     NULL means the whole image;
+ *   - costs are int32 pairs {J_o, J_r} per hypothesis.
+ *
+ * Error behaviour: every call returns a perch_status; nothing aborts or exits.
+ * On failure the call has no effect on the caller's buffers beyond what the
+ * message from perch_last_error() states; device-side failures are reported
+ * as PERCH_E_CUDA.  There is no CPU fallback: a context cannot be created
+ * without a CUDA device.
+ *
+ * Threading: a context may be used by one host thread at a time.
+ */
+#ifndef PERCH_H
+#define PERCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PERCH_API __attribute__((visibility("default")))
+#else
+#define PERCH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct perch_ctx perch_ctx;   /* opaque; owns all device memory it allocates */
+typedef int32_t perch_status;
+
+#define PERCH_OK          0
+#define PERCH_E_INVALID  (-1)   /* bad argument (null pointer, size, id, range)          */
+#define PERCH_E_NOMEM    (-2)   /* cudaMalloc or host allocation failed                   */
+#define PERCH_E_BUDGET   (-3)   /* the allocation would exceed the context's HBM budget   */
+#define PERCH_E_NOTFOUND (-4)   /* unknown scene, mesh or ticket id                       */
+#define PERCH_E_CUDA     (-5)   /* a CUDA runtime call or kernel failed                   */
+#define PERCH_E_TIMEOUT  (-6)   /* a bounded wait ran out                                 */
+#define PERCH_E_BUSY     (-7)   /* resource in use (e.g. releasing a scene with work)     */
+
+/* Scoring parameters, fixed per observation.
+ *   delta_m          sensor resolution delta of Eq. 2, metres, 1e-4 <= delta_m <= 1.
+ *   tau_c            CIEDE2000 threshold tau_c of Eq. 4 (the paper uses 12.5).
+ *   color_check      0: Eq. 2 only; 1: Eq. 4 (distance and colour).
+ *   stride           image-space down-sampling factor s >= 1 (Sec. IV-A): only
+ *                    pixels with u % s == 0 and v % s == 0 enter I and R.
+ *   occ_margin_units occluder margin m (0.1 mm): a rendered pixel of depth d is
+ *                    an occluded one (in C_K, Eq. 3) iff the observed depth
+ *                    d_obs > 0 and d_obs + m < d (and, when scoring by label,
+ *                    the pixel's label differs from the object's, Sec. V-C).
+ *   z_near_m         triangles with a vertex nearer than this are culled.
+ *   jo_mode          0: J_o from nearest-neighbour marks (Sec. IV-A). Others reserved. */
+typedef struct perch_params {
+    float delta_m;
+    float tau_c;
+    int32_t color_check;
+    int32_t stride;
+    int32_t occ_margin_units;
+    float z_near_m;
+    int32_t jo_mode;
+} perch_params;
+
+/* Fill *p with the defaults: delta 1 cm, tau_c 12.5, colour on, stride 1,
+ * margin = delta (100 units), z_near 5 cm, jo_mode 0. */
+PERCH_API perch_status perch_default_params(perch_params *p);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold (0 = no cap); every allocation is charged to it
+ * and refused with PERCH_E_BUDGET when it would exceed it.  *out receives the
+ * context (NULL on failure).  PERCH_E_CUDA if the device cannot be used. */
+PERCH_API perch_status perch_create(perch_ctx **out, int32_t device, uint64_t hbm_budget_bytes);
+
+/* Free every device allocation of the context and the context itself.  Waits
+ * for the context's own work.  ctx may be NULL. */
+PERCH_API perch_status perch_destroy(perch_ctx *ctx);
+
+/* Message of the last failing call on this context ("" if none).  The string
+ * is owned by the context and valid until its next call. */
+PERCH_API const char *perch_last_error(const perch_ctx *ctx);
+
+/* Bytes of device memory the context currently holds (charged to the budget). */
+PERCH_API uint64_t perch_hbm_used(const perch_ctx *ctx);
+
+/* Upload an object model (Sec. III-A: the 3-D models of the N objects).
+ *   verts_xyz  host, n_verts*3 float32, object frame (z up, base on z = 0), metres
+ *   rgb        host, n_verts*3 uint8 per-vertex colour
+ *   tris       host, n_tris*3 int32 vertex indices (any winding; rendered two-sided)
+ *   vol_radius_m, vol_height_m  the inscribed cylinder V(O) about the object's z axis,
+ *              0 <= z <= height (notation table: admissible volume)
+ * Limits: 1 <= n_verts, 1 <= n_tris <= 2^31-1, indices in [0, n_verts).
+ * The data are copied; the caller keeps ownership.  *mesh_id receives the id. */
+PERCH_API perch_status perch_load_mesh(perch_ctx *ctx, const float *verts_xyz, const uint8_t *rgb,
+                             int32_t n_verts, const int32_t *tris, int32_t n_tris,
+                             float vol_radius_m, float vol_height_m, int32_t *mesh_id);
+
+/* Release a mesh and its device memory. */
+PERCH_API perch_status perch_release_mesh(perch_ctx *ctx, int32_t mesh_id);
+
+/* Upload an observation (Sec. III-B: the input cloud I from the RGB-D image and
+ * the intrinsics) and build its device-resident data: the back-projected
+ * cloud, per-pixel CIELAB, and a voxel hash over I with cells of edge
+ * delta*(1+1/64) used for the radius search.
+ *   depth   host, H*W uint16 (0.1 mm, 0 = invalid)
+ *   rgb     host, H*W*3 uint8
+ *   labels  host, H*W int32 segmentation labels, or NULL (Sec. V-C)
+ *   W, H    1 <= W, H; W*H <= 466033 (keeps the fixed-point edge functions in int32)
+ *   params  scoring parameters (copied)
+ * The data are copied; *scene_id receives the id.  PERCH_E_INVALID when the
+ * parameters are out of range or the image is too large for delta (the cell
+ * coordinates of the cloud must stay below 1e5 cells). */
+PERCH_API perch_status perch_set_observation(perch_ctx *ctx, const uint16_t *depth, const uint8_t *rgb,
+                                   const int32_t *labels, int32_t W, int32_t H, float fx,
+                                   float fy, float cx, float cy, const perch_params *params,
+                                   int32_t *scene_id);
+
+/* Release an observation and its device memory. */
+PERCH_API perch_status perch_release_scene(perch_ctx *ctx, int32_t scene_id);
+
+/* Score n pose hypotheses of one mesh against one observation.
+ *   label  -1: V(O) is the mesh's cylinder at each pose (3-DoF, Sec. IV-A);
+ *          >= 0: V(O) = {p in I : labels(p) == label, p inside the ROI} and
+ *          occluders must carry a different label (6-DoF, Sec. V-C); needs labels.
+ *   roi    rendering is restricted to this rectangle (NULL = whole image).
+ *   poses  n*12 float32, costs n*2 int32 {J_o, J_r}.
+ *   cuda_stream NULL: poses and costs are HOST pointers, the call copies them,
+ *          runs and returns when costs are written.
+ *          non-NULL (a cudaStream_t): poses and costs are DEVICE pointers; the
+ *          work is enqueued on that stream and the call returns at once; both
+ *          buffers must stay valid until the stream reaches that point.
+ * n == 0 is a no-op.  Results do not depend on the order of the hypotheses. */
+PERCH_API perch_status perch_score_hypotheses(perch_ctx *ctx, int32_t scene_id, int32_t mesh_id,
+                                    int32_t label, const int32_t *roi, const float *poses,
+                                    int64_t n, int32_t *costs, void *cuda_stream);
+
+/* Argmin of J = J_o + J_r over n hypotheses (Eq. 1; "find the one
+ * corresponding to the minimum cost for each object", Sec. IV-A), computed on
+ * the device.  Ties go to the lowest id; ids = NULL uses the index.
+ *   costs n*2 int32, ids n uint64 or NULL, n >= 1 (n < 2^31).
+ *   best_index (int64) and best_cost (int32) receive the winner.
+ * cuda_stream NULL: all pointers are host pointers; otherwise all are device
+ * pointers and the result is written when the stream reaches the call. */
+PERCH_API perch_status perch_best(perch_ctx *ctx, const int32_t *costs, const uint64_t *ids, int64_t n,
+                        int64_t *best_index, int32_t *best_cost, void *cuda_stream);
+
+/* Launch shape of the scoring kernel for this context: threads per block (128,
+ * 256 or 512) and the capacity of the shared-memory z-buffer in 32-bit words
+ * (1024 <= zbuf_words <= 49152; a 32-bit key per pixel when the mesh has fewer
+ * than 65536 triangles and the hypothesis lies within 6.5 m, else a 64-bit key
+ * per pixel).  Pixel boxes larger than the z-buffer are processed in tiles.
+ * Results do not depend on this choice; only speed does.  The autotuner of
+ * the batched form calls it.  PERCH_E_INVALID outside the ranges. */
+PERCH_API perch_status perch_set_launch_config(perch_ctx *ctx, int32_t threads, int32_t zbuf_words);
+
+/* Debug view of the rasteriser used by perch_score_hypotheses: the z-buffer of
+ * one pose as 64-bit keys (depth << 32) | triangle id, 0xFFFFFFFFFFFFFFFF where
+ * nothing is covered.  keys is a HOST buffer of W*H uint64 of the scene; the
+ * call is synchronous. */
+PERCH_API perch_status perch_debug_render_keys(perch_ctx *ctx, int32_t scene_id, int32_t mesh_id,
+                                     const int32_t *roi, const float *pose, uint64_t *keys);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERCH_H */

@@ -1,0 +1,652 @@
+// libperch host side: the C ABI declared in include/perch.h.
+//
+// A context owns every device allocation it makes and charges each to its HBM
+// budget.  Meshes and observations are copied once and stay resident; scoring
+// calls launch the fused kernel (perch_kernels.cu) on the caller's stream or,
+// in synchronous mode, on the context's own stream with staging copies.
+#include "perch.h"
+#include "perch_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+struct MeshRec {
+    perch::DevMesh dm{};
+    void* verts = nullptr;
+    void* tris = nullptr;
+};
+
+struct SceneRec {
+    perch::DevScene ds{};
+    perch_params params{};
+    void* depth = nullptr;
+    void* labels = nullptr;
+    void* lab = nullptr;
+    void* pts = nullptr;
+    void* table = nullptr;
+};
+
+class DeviceGuard {
+public:
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev_ >= 0) cudaSetDevice(prev_);
+    }
+
+private:
+    int prev_ = -1;
+};
+
+}  // namespace
+
+struct perch_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    std::unordered_map<void*, size_t> allocs;
+    std::map<int32_t, MeshRec> meshes;
+    std::map<int32_t, SceneRec> scenes;
+    int32_t next_id = 1;
+    std::string err;
+    cudaStream_t stream = nullptr;
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    int* d_err = nullptr;
+    unsigned long long* d_best_partial = nullptr;   // 3 words per block, 1024 blocks
+    unsigned* d_best_ticket = nullptr;
+    long long* d_best_index = nullptr;
+    int32_t* d_best_cost = nullptr;
+    perch::ScoreConfig cfg{256, 16384};
+};
+
+namespace {
+
+perch_status fail(perch_ctx* c, perch_status st, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+perch_status cuda_fail(perch_ctx* c, cudaError_t e, const char* what)
+{
+    cudaGetLastError();
+    return fail(c, PERCH_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+perch_status dalloc(perch_ctx* c, size_t bytes, void** p)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(c, PERCH_E_BUDGET, "allocation of %zu bytes exceeds the HBM budget (%llu of %llu used)",
+                    bytes, (unsigned long long)c->used, (unsigned long long)c->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, PERCH_E_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs[*p] = bytes;
+    c->used += bytes;
+    return PERCH_OK;
+}
+
+void dfree(perch_ctx* c, void* p)
+{
+    if (!p) return;
+    auto it = c->allocs.find(p);
+    if (it != c->allocs.end()) {
+        c->used -= it->second;
+        c->allocs.erase(it);
+    }
+    cudaFree(p);
+}
+
+perch_status ensure_stage(perch_ctx* c, size_t bytes)
+{
+    if (c->stage_bytes >= bytes) return PERCH_OK;
+    dfree(c, c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    perch_status st = dalloc(c, want, &c->stage);
+    if (st == PERCH_OK) c->stage_bytes = want;
+    return st;
+}
+
+// Read and clear the device error word (synchronous).
+perch_status check_device_error(perch_ctx* c)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the device error word");
+    if (h == 0) return PERCH_OK;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+    return fail(c, PERCH_E_CUDA, "kernel invariant violated (flags 0x%x)", h);
+}
+
+bool finite(float x) { return std::isfinite(x); }
+
+uint32_t next_pow2(uint64_t x)
+{
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return (uint32_t)p;
+}
+
+perch_status clip_roi(perch_ctx* c, const SceneRec& s, const int32_t* roi, int out[4])
+{
+    int W = s.ds.W, H = s.ds.H;
+    if (!roi) {
+        out[0] = 0; out[1] = 0; out[2] = W; out[3] = H;
+        return PERCH_OK;
+    }
+    out[0] = std::max(0, roi[0]);
+    out[1] = std::max(0, roi[1]);
+    out[2] = std::min(W, roi[2]);
+    out[3] = std::min(H, roi[3]);
+    if (out[2] < out[0]) out[2] = out[0];
+    if (out[3] < out[1]) out[3] = out[1];
+    (void)c;
+    return PERCH_OK;
+}
+
+int mark_words_for(const SceneRec& s, int label, const int roi[4])
+{
+    long long bits = label >= 0 ? (long long)(roi[2] - roi[0]) * (roi[3] - roi[1])
+                                : (long long)s.ds.W * s.ds.H;
+    return (int)(((bits + 31) / 32 + 2) & ~1ll);   // even: keeps the later 8-byte arrays aligned
+}
+
+// Fit the z-buffer into the opt-in shared memory limit of the device.
+perch_status fit_config(perch_ctx* c, int mark_words, perch::ScoreConfig* cfg)
+{
+    int max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (max_optin <= 0) max_optin = 48 * 1024;
+    *cfg = c->cfg;
+    while (perch::score_smem_bytes(*cfg, mark_words) > (size_t)max_optin && cfg->zcap_words > 1024)
+        cfg->zcap_words /= 2;
+    if (perch::score_smem_bytes(*cfg, mark_words) > (size_t)max_optin)
+        return fail(c, PERCH_E_INVALID, "admissible-set bitset (%d words) does not fit in shared memory",
+                    mark_words);
+    return PERCH_OK;
+}
+
+perch::ScoreArgs make_args(perch_ctx* c, const SceneRec& s, const MeshRec& m, int label,
+                           const int roi[4], const float* poses, int32_t* costs, long long n,
+                           const perch::ScoreConfig& cfg, int mark_words)
+{
+    perch::ScoreArgs a{};
+    a.sc = s.ds;
+    a.m = m.dm;
+    a.label = label;
+    for (int i = 0; i < 4; ++i) a.roi[i] = roi[i];
+    a.poses = poses;
+    a.costs = costs;
+    a.n = n;
+    a.zcap_words = cfg.zcap_words;
+    a.mark_words = mark_words;
+    a.dump = nullptr;
+    a.err = c->d_err;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+perch_status perch_default_params(perch_params* p)
+{
+    if (!p) return PERCH_E_INVALID;
+    p->delta_m = 0.01f;
+    p->tau_c = 12.5f;
+    p->color_check = 1;
+    p->stride = 1;
+    p->occ_margin_units = 100;
+    p->z_near_m = 0.05f;
+    p->jo_mode = 0;
+    return PERCH_OK;
+}
+
+perch_status perch_create(perch_ctx** out, int32_t device, uint64_t hbm_budget_bytes)
+{
+    if (!out) return PERCH_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+        cudaGetLastError();
+        return PERCH_E_CUDA;
+    }
+    if (device < 0 || device >= ndev) return PERCH_E_INVALID;
+    perch_ctx* c = new (std::nothrow) perch_ctx();
+    if (!c) return PERCH_E_NOMEM;
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    DeviceGuard g(device);
+    perch_status st = PERCH_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "cudaStreamCreate");
+    void* p = nullptr;
+    if (st == PERCH_OK && (st = dalloc(c, sizeof(int), &p)) == PERCH_OK) c->d_err = (int*)p;
+    if (st == PERCH_OK && (st = dalloc(c, sizeof(unsigned long long) * 3 * 1024, &p)) == PERCH_OK)
+        c->d_best_partial = (unsigned long long*)p;
+    if (st == PERCH_OK && (st = dalloc(c, 64, &p)) == PERCH_OK) {
+        c->d_best_ticket = (unsigned*)p;
+        c->d_best_index = (long long*)((char*)p + 16);
+        c->d_best_cost = (int32_t*)((char*)p + 32);
+    }
+    if (st == PERCH_OK) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        cudaMemsetAsync(c->d_best_ticket, 0, 64, c->stream);
+        if ((e = perch::init_device_tables(c->stream)) != cudaSuccess) st = cuda_fail(c, e, "init tables");
+    }
+    if (st == PERCH_OK && (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        st = cuda_fail(c, e, "perch_create");
+    if (st != PERCH_OK) {
+        perch_destroy(c);
+        return st;
+    }
+    *out = c;
+    return PERCH_OK;
+}
+
+perch_status perch_destroy(perch_ctx* c)
+{
+    if (!c) return PERCH_OK;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->allocs) cudaFree(kv.first);
+    c->allocs.clear();
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return PERCH_OK;
+}
+
+const char* perch_last_error(const perch_ctx* c)
+{
+    return c ? c->err.c_str() : "null context";
+}
+
+uint64_t perch_hbm_used(const perch_ctx* c)
+{
+    return c ? c->used : 0;
+}
+
+perch_status perch_load_mesh(perch_ctx* c, const float* verts_xyz, const uint8_t* rgb,
+                             int32_t n_verts, const int32_t* tris, int32_t n_tris,
+                             float vol_radius_m, float vol_height_m, int32_t* mesh_id)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (!verts_xyz || !rgb || !tris || !mesh_id || n_verts < 1 || n_tris < 1)
+        return fail(c, PERCH_E_INVALID, "perch_load_mesh: null pointer or empty mesh");
+    if (!finite(vol_radius_m) || !finite(vol_height_m) || vol_radius_m < 0 || vol_height_m < 0)
+        return fail(c, PERCH_E_INVALID, "perch_load_mesh: bad admissible cylinder");
+    std::vector<float> v4((size_t)n_verts * 4);
+    MeshRec rec;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int32_t i = 0; i < n_verts; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            float x = verts_xyz[3 * i + k];
+            if (!finite(x)) return fail(c, PERCH_E_INVALID, "perch_load_mesh: non-finite vertex %d", i);
+            v4[4 * i + k] = x;
+            lo[k] = std::min(lo[k], x);
+            hi[k] = std::max(hi[k], x);
+        }
+        uint32_t packed = (uint32_t)rgb[3 * i] | ((uint32_t)rgb[3 * i + 1] << 8) |
+                          ((uint32_t)rgb[3 * i + 2] << 16);
+        std::memcpy(&v4[4 * i + 3], &packed, 4);
+    }
+    std::vector<int32_t> t4((size_t)n_tris * 4);
+    for (int32_t i = 0; i < n_tris; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            int32_t x = tris[3 * i + k];
+            if (x < 0 || x >= n_verts)
+                return fail(c, PERCH_E_INVALID, "perch_load_mesh: triangle %d has index %d out of range", i, x);
+            t4[4 * i + k] = x;
+        }
+        t4[4 * i + 3] = 0;
+    }
+    DeviceGuard g(c->device);
+    perch_status st = dalloc(c, v4.size() * sizeof(float), &rec.verts);
+    if (st != PERCH_OK) return st;
+    if ((st = dalloc(c, t4.size() * sizeof(int32_t), &rec.tris)) != PERCH_OK) {
+        dfree(c, rec.verts);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(rec.verts, v4.data(), v4.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rec.tris, t4.data(), t4.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        dfree(c, rec.verts);
+        dfree(c, rec.tris);
+        return cuda_fail(c, e, "perch_load_mesh upload");
+    }
+    rec.dm.verts = (const float4*)rec.verts;
+    rec.dm.tris = (const int4*)rec.tris;
+    rec.dm.n_verts = n_verts;
+    rec.dm.n_tris = n_tris;
+    rec.dm.vol_r = vol_radius_m;
+    rec.dm.vol_h = vol_height_m;
+    for (int k = 0; k < 3; ++k) {
+        rec.dm.lo[k] = lo[k];
+        rec.dm.hi[k] = hi[k];
+    }
+    int32_t id = c->next_id++;
+    c->meshes[id] = rec;
+    *mesh_id = id;
+    return PERCH_OK;
+}
+
+perch_status perch_release_mesh(perch_ctx* c, int32_t mesh_id)
+{
+    if (!c) return PERCH_E_INVALID;
+    auto it = c->meshes.find(mesh_id);
+    if (it == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    dfree(c, it->second.verts);
+    dfree(c, it->second.tris);
+    c->meshes.erase(it);
+    return PERCH_OK;
+}
+
+perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const uint8_t* rgb,
+                                   const int32_t* labels, int32_t W, int32_t H, float fx,
+                                   float fy, float cx, float cy, const perch_params* params,
+                                   int32_t* scene_id)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (!depth || !rgb || !params || !scene_id)
+        return fail(c, PERCH_E_INVALID, "perch_set_observation: null pointer");
+    if (W < 1 || H < 1 || (long long)W * H > 466033)
+        return fail(c, PERCH_E_INVALID, "perch_set_observation: image %dx%d outside 1 <= W*H <= 466033", W, H);
+    if (!finite(fx) || !finite(fy) || !finite(cx) || !finite(cy) || fx <= 0 || fy <= 0)
+        return fail(c, PERCH_E_INVALID, "perch_set_observation: bad intrinsics");
+    const perch_params& p = *params;
+    if (!finite(p.delta_m) || p.delta_m < 1e-4f || p.delta_m > 1.0f || !finite(p.tau_c) || p.tau_c < 0 ||
+        (p.color_check != 0 && p.color_check != 1) || p.stride < 1 || p.occ_margin_units < 0 ||
+        !finite(p.z_near_m) || p.z_near_m <= 0 || p.jo_mode != 0)
+        return fail(c, PERCH_E_INVALID, "perch_set_observation: parameters out of range");
+    const float cell = p.delta_m * perch::kCellGrow;
+    const double zmax = 65535.0 / 10000.0;
+    double xmax = std::max(std::fabs(0.0 - cx), std::fabs(W - 1.0 - cx)) * zmax / fx;
+    double ymax = std::max(std::fabs(0.0 - cy), std::fabs(H - 1.0 - cy)) * zmax / fy;
+    double lim = perch::kMaxCellCoord * (double)cell * 0.99;
+    if (xmax > lim || ymax > lim || zmax > lim)
+        return fail(c, PERCH_E_INVALID, "perch_set_observation: delta too small for the field of view");
+
+    long long npx = (long long)W * H;
+    long long n_valid = 0;
+    for (long long i = 0; i < npx; ++i) {
+        int u = (int)(i % W), v = (int)(i / W);
+        if (depth[i] != 0 && u % p.stride == 0 && v % p.stride == 0) ++n_valid;
+    }
+    uint32_t cap = next_pow2(std::max<long long>(1024, 2 * n_valid));
+    uint32_t n_tiles = (cap + 1023) / 1024;
+
+    DeviceGuard g(c->device);
+    SceneRec s;
+    s.params = p;
+    perch_status st = PERCH_OK;
+    void *d_rgb = nullptr, *slot = nullptr, *keys = nullptr, *count = nullptr, *cursor = nullptr,
+         *start = nullptr, *nvalid = nullptr;
+    auto cleanup_scratch = [&]() {
+        dfree(c, d_rgb); dfree(c, slot); dfree(c, keys); dfree(c, count);
+        dfree(c, cursor); dfree(c, start); dfree(c, nvalid);
+    };
+    auto cleanup_scene = [&]() {
+        dfree(c, s.depth); dfree(c, s.labels); dfree(c, s.lab); dfree(c, s.pts); dfree(c, s.table);
+    };
+    if ((st = dalloc(c, npx * sizeof(uint16_t), &s.depth)) ||
+        (labels && (st = dalloc(c, npx * sizeof(int32_t), &s.labels))) ||
+        (st = dalloc(c, npx * sizeof(float4), &s.lab)) ||
+        (st = dalloc(c, std::max<long long>(1, n_valid) * sizeof(float4), &s.pts)) ||
+        (st = dalloc(c, (size_t)cap * sizeof(uint4), &s.table)) ||
+        (st = dalloc(c, npx * 3, &d_rgb)) || (st = dalloc(c, npx * sizeof(int32_t), &slot)) ||
+        (st = dalloc(c, (size_t)cap * 8, &keys)) || (st = dalloc(c, (size_t)cap * 4, &count)) ||
+        (st = dalloc(c, ((size_t)cap + n_tiles) * 4, &cursor)) ||
+        (st = dalloc(c, (size_t)cap * 4, &start)) || (st = dalloc(c, sizeof(int), &nvalid))) {
+        cleanup_scratch();
+        cleanup_scene();
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(s.depth, depth, npx * sizeof(uint16_t), cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(d_rgb, rgb, npx * 3, cudaMemcpyHostToDevice, c->stream);
+    if (!e && labels) e = cudaMemcpyAsync(s.labels, labels, npx * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    perch::DevScene& d = s.ds;
+    d.W = W; d.H = H; d.fx = fx; d.fy = fy; d.cx = cx; d.cy = cy;
+    d.delta = p.delta_m;
+    d.delta2 = p.delta_m * p.delta_m;
+    d.cell = cell;
+    d.tau_c = p.tau_c;
+    d.z_near = p.z_near_m;
+    d.color_check = p.color_check;
+    d.stride = p.stride;
+    d.occ_margin = p.occ_margin_units;
+    d.depth = (const uint16_t*)s.depth;
+    d.labels = (const int32_t*)s.labels;
+    d.lab = (const float4*)s.lab;
+    d.pts = (const float4*)s.pts;
+    d.table = (const uint4*)s.table;
+    d.table_mask = cap - 1;
+    d.n_pts = (int)n_valid;
+    perch::BuildBuffers b{};
+    b.slot_of_pixel = (int32_t*)slot;
+    b.keys = (unsigned long long*)keys;
+    b.count = (uint32_t*)count;
+    b.cursor = (uint32_t*)cursor;
+    b.start = (uint32_t*)start;
+    b.n_valid = (int*)nvalid;
+    b.lab = (float4*)s.lab;
+    b.pts = (float4*)s.pts;
+    b.table = (uint4*)s.table;
+    if (!e) e = perch::launch_build(d, b, cap, (const uint8_t*)d_rgb, c->d_err, c->stream);
+    int got = -1;
+    if (!e) e = cudaMemcpyAsync(&got, nvalid, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    cleanup_scratch();
+    if (e) {
+        cleanup_scene();
+        return cuda_fail(c, e, "perch_set_observation build");
+    }
+    if ((st = check_device_error(c)) != PERCH_OK || got != n_valid) {
+        cleanup_scene();
+        return st != PERCH_OK ? st : fail(c, PERCH_E_CUDA, "observation build counted %d of %lld points", got, n_valid);
+    }
+    int32_t id = c->next_id++;
+    c->scenes[id] = s;
+    *scene_id = id;
+    return PERCH_OK;
+}
+
+perch_status perch_release_scene(perch_ctx* c, int32_t scene_id)
+{
+    if (!c) return PERCH_E_INVALID;
+    auto it = c->scenes.find(scene_id);
+    if (it == c->scenes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown scene %d", scene_id);
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    SceneRec& s = it->second;
+    dfree(c, s.depth); dfree(c, s.labels); dfree(c, s.lab); dfree(c, s.pts); dfree(c, s.table);
+    c->scenes.erase(it);
+    return PERCH_OK;
+}
+
+static perch_status lookup(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t label,
+                           SceneRec** s, MeshRec** m)
+{
+    auto si = c->scenes.find(scene_id);
+    if (si == c->scenes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown scene %d", scene_id);
+    auto mi = c->meshes.find(mesh_id);
+    if (mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
+    if (label < -1) return fail(c, PERCH_E_INVALID, "label must be -1 or >= 0");
+    if (label >= 0 && !si->second.labels)
+        return fail(c, PERCH_E_INVALID, "label %d given but the observation has no labels", label);
+    *s = &si->second;
+    *m = &mi->second;
+    return PERCH_OK;
+}
+
+perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh_id,
+                                    int32_t label, const int32_t* roi, const float* poses,
+                                    int64_t n, int32_t* costs, void* cuda_stream)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (n < 0) return fail(c, PERCH_E_INVALID, "n < 0");
+    if (n == 0) return PERCH_OK;
+    if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
+    SceneRec* s;
+    MeshRec* m;
+    perch_status st = lookup(c, scene_id, mesh_id, label, &s, &m);
+    if (st != PERCH_OK) return st;
+    int r[4];
+    clip_roi(c, *s, roi, r);
+    int mw = mark_words_for(*s, label, r);
+    perch::ScoreConfig cfg;
+    if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
+    DeviceGuard g(c->device);
+    cudaError_t e;
+    if (cuda_stream) {
+        perch::ScoreArgs a = make_args(c, *s, *m, label, r, poses, costs, n, cfg, mw);
+        if ((e = perch::launch_score(a, cfg, (cudaStream_t)cuda_stream)) != cudaSuccess)
+            return cuda_fail(c, e, "perch_score_hypotheses launch");
+        return PERCH_OK;
+    }
+    const long long chunk = 1 << 20;
+    if ((st = ensure_stage(c, (size_t)std::min<long long>(n, chunk) * (48 + 8))) != PERCH_OK) return st;
+    float* d_poses = (float*)c->stage;
+    int32_t* d_costs = (int32_t*)((char*)c->stage + (size_t)std::min<long long>(n, chunk) * 48);
+    for (long long off = 0; off < n; off += chunk) {
+        long long k = std::min(chunk, n - off);
+        e = cudaMemcpyAsync(d_poses, poses + 12 * off, k * 48, cudaMemcpyHostToDevice, c->stream);
+        perch::ScoreArgs a = make_args(c, *s, *m, label, r, d_poses, d_costs, k, cfg, mw);
+        if (!e) e = perch::launch_score(a, cfg, c->stream);
+        if (!e) e = cudaMemcpyAsync(costs + 2 * off, d_costs, k * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (!e) e = cudaStreamSynchronize(c->stream);
+        if (e) return cuda_fail(c, e, "perch_score_hypotheses");
+    }
+    return check_device_error(c);
+}
+
+perch_status perch_best(perch_ctx* c, const int32_t* costs, const uint64_t* ids, int64_t n,
+                        int64_t* best_index, int32_t* best_cost, void* cuda_stream)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (!costs || !best_index || !best_cost) return fail(c, PERCH_E_INVALID, "null pointer");
+    if (n < 1 || n > 0x7FFFFFFFll) return fail(c, PERCH_E_INVALID, "n out of range");
+    DeviceGuard g(c->device);
+    perch::BestArgs a{};
+    a.n = n;
+    a.partial = c->d_best_partial;
+    a.ticket = c->d_best_ticket;
+    cudaError_t e;
+    if (cuda_stream) {
+        a.costs = costs;
+        a.ids = (const unsigned long long*)ids;
+        a.best_index = (long long*)best_index;
+        a.best_cost = best_cost;
+        if ((e = perch::launch_best(a, (cudaStream_t)cuda_stream)) != cudaSuccess)
+            return cuda_fail(c, e, "perch_best launch");
+        return PERCH_OK;
+    }
+    size_t need = (size_t)n * 8 + (ids ? (size_t)n * 8 : 0);
+    perch_status st = ensure_stage(c, need);
+    if (st != PERCH_OK) return st;
+    int32_t* d_costs = (int32_t*)c->stage;
+    unsigned long long* d_ids = ids ? (unsigned long long*)((char*)c->stage + (size_t)n * 8) : nullptr;
+    e = cudaMemcpyAsync(d_costs, costs, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
+    if (!e && ids) e = cudaMemcpyAsync(d_ids, ids, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
+    a.costs = d_costs;
+    a.ids = d_ids;
+    a.best_index = c->d_best_index;
+    a.best_cost = c->d_best_cost;
+    if (!e) e = perch::launch_best(a, c->stream);
+    long long bi = -1;
+    int32_t bc = 0;
+    if (!e) e = cudaMemcpyAsync(&bi, c->d_best_index, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(&bc, c->d_best_cost, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "perch_best");
+    *best_index = bi;
+    *best_cost = bc;
+    return PERCH_OK;
+}
+
+perch_status perch_set_launch_config(perch_ctx* c, int32_t threads, int32_t zbuf_words)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if ((threads != 128 && threads != 256 && threads != 512) || zbuf_words < 1024 || zbuf_words > 49152)
+        return fail(c, PERCH_E_INVALID, "launch config (%d threads, %d words) out of range", threads, zbuf_words);
+    c->cfg.threads = threads;
+    c->cfg.zcap_words = zbuf_words & ~1;
+    return PERCH_OK;
+}
+
+perch_status perch_debug_render_keys(perch_ctx* c, int32_t scene_id, int32_t mesh_id,
+                                     const int32_t* roi, const float* pose, uint64_t* keys)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (!pose || !keys) return fail(c, PERCH_E_INVALID, "null pose or keys");
+    SceneRec* s;
+    MeshRec* m;
+    perch_status st = lookup(c, scene_id, mesh_id, -1, &s, &m);
+    if (st != PERCH_OK) return st;
+    int r[4];
+    clip_roi(c, *s, roi, r);
+    int mw = mark_words_for(*s, -1, r);
+    perch::ScoreConfig cfg;
+    if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
+    DeviceGuard g(c->device);
+    size_t npx = (size_t)s->ds.W * s->ds.H;
+    void* dump = nullptr;
+    if ((st = dalloc(c, npx * 8, &dump)) != PERCH_OK) return st;
+    if ((st = ensure_stage(c, 64)) != PERCH_OK) {
+        dfree(c, dump);
+        return st;
+    }
+    float* d_pose = (float*)c->stage;
+    int32_t* d_cost = (int32_t*)((char*)c->stage + 48);
+    cudaError_t e = cudaMemsetAsync(dump, 0xFF, npx * 8, c->stream);
+    if (!e) e = cudaMemcpyAsync(d_pose, pose, 48, cudaMemcpyHostToDevice, c->stream);
+    perch::ScoreArgs a = make_args(c, *s, *m, -1, r, d_pose, d_cost, 1, cfg, mw);
+    a.dump = (unsigned long long*)dump;
+    if (!e) e = perch::launch_score(a, cfg, c->stream);
+    if (!e) e = cudaMemcpyAsync(keys, dump, npx * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    dfree(c, dump);
+    if (e) return cuda_fail(c, e, "perch_debug_render_keys");
+    return check_device_error(c);
+}
+
+}  // extern "C"

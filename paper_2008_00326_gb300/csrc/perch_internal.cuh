@@ -1,0 +1,99 @@
+// Internal types shared by the host API (perch_api.cu) and the kernels
+// (perch_kernels.cu) of libperch.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace perch {
+
+constexpr uint64_t kEmptyKey = ~0ull;          // empty hash slot / empty z-buffer word
+constexpr int kCellBias = 1 << 20;             // cell coordinates packed as 21-bit fields
+constexpr float kCellGrow = 1.0f + 1.0f / 64.0f;  // hash cell edge = delta * kCellGrow
+constexpr double kMaxCellCoord = 1.0e5;        // |coordinate / cell| bound for exact probing
+
+// Device-resident observation (read-only during scoring).
+struct DevScene {
+    int W, H;
+    float fx, fy, cx, cy;
+    float delta, delta2, cell, tau_c, z_near;
+    int color_check, stride, occ_margin;
+    const uint16_t* depth;    // H*W
+    const int32_t* labels;    // H*W or nullptr
+    const float4* lab;        // H*W: (L, a, b, 0)
+    const float4* pts;        // n_pts, grouped by hash cell: (x, y, z, pixel index bits)
+    const uint4* table;       // hash slots: (key lo, key hi, start, count)
+    uint32_t table_mask;
+    int n_pts;
+};
+
+// Device-resident mesh.
+struct DevMesh {
+    const float4* verts;      // (x, y, z, rgb packed in the low 24 bits of w's bit pattern)
+    const int4* tris;         // (a, b, c, 0)
+    int n_verts, n_tris;
+    float vol_r, vol_h;
+    float lo[3], hi[3];       // object-frame bounding box of the vertices
+};
+
+// One scoring launch: n hypotheses of one mesh against one scene.
+struct ScoreArgs {
+    DevScene sc;
+    DevMesh m;
+    int label;                // -1: cylinder V(O); >= 0: label V(O)
+    int roi[4];               // clipped to the image, half-open
+    const float* poses;       // n*12
+    int32_t* costs;           // n*2
+    long long n;
+    int zcap_words;           // z-buffer capacity in 32-bit words
+    int mark_words;           // marks bitset capacity in 32-bit words
+    unsigned long long* dump; // debug: W*H 64-bit keys, or nullptr
+    int* err;                 // device error word (bit flags)
+};
+
+// Error bits written by kernels into the context's error word.
+enum : int { kErrKeyRange = 1, kErrMarkCap = 2, kErrHashFull = 4 };
+
+// Launch configuration of the scoring kernel (chosen by the host; the
+// autotuner searches over these).
+struct ScoreConfig {
+    int threads;              // 128, 256 or 512
+    int zcap_words;           // z-buffer words (32-bit keys: pixels; 64-bit: half)
+};
+
+size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words);
+cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, cudaStream_t s);
+
+// Observation build (voxel hash over I).
+struct BuildBuffers {
+    // scratch (freed after the build)
+    int32_t* slot_of_pixel;   // H*W
+    unsigned long long* keys; // table capacity
+    uint32_t* count;          // table capacity
+    uint32_t* cursor;         // table capacity
+    uint32_t* start;          // table capacity
+    int* n_valid;             // 1
+    // outputs (owned by the scene)
+    float4* lab;              // H*W
+    float4* pts;              // n_points capacity (H*W)
+    uint4* table;             // table capacity
+};
+cudaError_t launch_build(const DevScene& sc, const BuildBuffers& b, uint32_t table_cap,
+                         const uint8_t* rgb_dev, int* err, cudaStream_t s);
+
+// Argmin of J = J_o + J_r (ties to the lowest id / index).
+struct BestArgs {
+    const int32_t* costs;
+    const unsigned long long* ids;  // or nullptr
+    long long n;
+    long long* best_index;
+    int32_t* best_cost;
+    unsigned long long* partial;    // scratch: 2 words per block
+    unsigned int* ticket;           // scratch: 1 word, zero on entry, zero on exit
+};
+int best_blocks(long long n);
+cudaError_t launch_best(const BestArgs& a, cudaStream_t s);
+
+cudaError_t init_device_tables(cudaStream_t s);
+
+}  // namespace perch

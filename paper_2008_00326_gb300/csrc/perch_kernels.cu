@@ -1,0 +1,922 @@
+// libperch kernels for sm_103a: observation build (back-projection, CIELAB,
+// voxel hash over I), the fused per-hypothesis scorer (fixed-point raster with
+// an atomicMin z-buffer in shared memory, resolve with occluder removal and
+// image-space down-sampling, warp-cooperative 27-cell radius search,
+// CIEDE2000 check, J_r / J_o counts) and the warp-shuffle argmin.
+//
+// Bit-exactness: every step whose result decides an integer (snapping,
+// coverage, depth, back-projection, squared distances, the cylinder test) is
+// written with explicit round-to-nearest single-precision intrinsics
+// (__fadd_rn, __fmul_rn, __fdiv_rn) and the file is compiled with -fmad=false,
+// so no multiply-add is contracted.  Edge functions are exact int32.
+#include "perch_internal.cuh"
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace perch {
+
+// ---------------------------------------------------------------------------
+// colour: sRGB -> CIELAB (D65) and CIEDE2000 (Sec. IV-B, Eq. 4), binary32
+// ---------------------------------------------------------------------------
+
+__device__ float g_srgb_lin[256];   // sRGB decoding of each 8-bit code, filled at start-up
+
+__global__ void k_init_tables()
+{
+    int i = threadIdx.x;
+    if (i < 256) {
+        float c = __fdiv_rn((float)i, 255.0f);
+        g_srgb_lin[i] = (c <= 0.04045f) ? __fdiv_rn(c, 12.92f)
+                                        : powf(__fdiv_rn(__fadd_rn(c, 0.055f), 1.055f), 2.4f);
+    }
+}
+
+cudaError_t init_device_tables(cudaStream_t s)
+{
+    k_init_tables<<<1, 256, 0, s>>>();
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ float cie_f(float t)
+{
+    // cube root above (6/29)^3, the linear toe below it
+    return (t > 0.0088564517f) ? cbrtf(t) : (t * 903.29630f + 16.0f) / 116.0f;
+}
+
+__device__ __forceinline__ float3 srgb8_to_lab(uint32_t r8, uint32_t g8, uint32_t b8)
+{
+    float r = g_srgb_lin[r8], g = g_srgb_lin[g8], b = g_srgb_lin[b8];
+    float x = 0.4124564f * r + 0.3575761f * g + 0.1804375f * b;
+    float y = 0.2126729f * r + 0.7151522f * g + 0.0721750f * b;
+    float z = 0.0193339f * r + 0.1191920f * g + 0.9503041f * b;
+    float fx = cie_f(x / 0.95047f), fy = cie_f(y), fz = cie_f(z / 1.08883f);
+    return make_float3(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz));
+}
+
+// CIEDE2000 with kL = kC = kH = 1, angles in degrees.
+__device__ float ciede2000(float3 p, float3 q)
+{
+    const float kRad = 0.017453292519943295f;
+    const float k25p7 = 6103515625.0f;
+    float c1 = sqrtf(p.y * p.y + p.z * p.z);
+    float c2 = sqrtf(q.y * q.y + q.z * q.z);
+    float cm = 0.5f * (c1 + c2);
+    float cm2 = cm * cm, cm7 = cm2 * cm2 * cm2 * cm;
+    float g = 0.5f * (1.0f - sqrtf(cm7 / (cm7 + k25p7)));
+    float ap1 = p.y * (1.0f + g), ap2 = q.y * (1.0f + g);
+    float cp1 = sqrtf(ap1 * ap1 + p.z * p.z), cp2 = sqrtf(ap2 * ap2 + q.z * q.z);
+    float hp1 = (ap1 == 0.0f && p.z == 0.0f) ? 0.0f : atan2f(p.z, ap1) / kRad;
+    float hp2 = (ap2 == 0.0f && q.z == 0.0f) ? 0.0f : atan2f(q.z, ap2) / kRad;
+    if (hp1 < 0.0f) hp1 += 360.0f;
+    if (hp2 < 0.0f) hp2 += 360.0f;
+    float prod = cp1 * cp2;
+    float dh = 0.0f, hm;
+    if (prod == 0.0f) {
+        hm = hp1 + hp2;
+    } else {
+        dh = hp2 - hp1;
+        if (dh > 180.0f) dh -= 360.0f;
+        else if (dh < -180.0f) dh += 360.0f;
+        float s = hp1 + hp2;
+        if (fabsf(hp1 - hp2) <= 180.0f) hm = 0.5f * s;
+        else hm = (s < 360.0f) ? 0.5f * (s + 360.0f) : 0.5f * (s - 360.0f);
+    }
+    float dL = q.x - p.x;
+    float dC = cp2 - cp1;
+    float dH = 2.0f * sqrtf(prod) * sinf(0.5f * dh * kRad);
+    float lm = 0.5f * (p.x + q.x) - 50.0f;
+    float lm2 = lm * lm;
+    float cpm = 0.5f * (cp1 + cp2);
+    float t = 1.0f - 0.17f * cosf((hm - 30.0f) * kRad) + 0.24f * cosf(2.0f * hm * kRad)
+              + 0.32f * cosf((3.0f * hm + 6.0f) * kRad) - 0.20f * cosf((4.0f * hm - 63.0f) * kRad);
+    float e = (hm - 275.0f) / 25.0f;
+    float dtheta = 30.0f * expf(-e * e);
+    float cpm2 = cpm * cpm, cpm7 = cpm2 * cpm2 * cpm2 * cpm;
+    float rc = 2.0f * sqrtf(cpm7 / (cpm7 + k25p7));
+    float sl = 1.0f + 0.015f * lm2 / sqrtf(20.0f + lm2);
+    float sc = 1.0f + 0.045f * cpm;
+    float sh = 1.0f + 0.015f * cpm * t;
+    float rt = -sinf(2.0f * dtheta * kRad) * rc;
+    float a = dL / sl, b = dC / sc, c = dH / sh;
+    return sqrtf(a * a + b * b + c * c + rt * b * c);
+}
+
+// ---------------------------------------------------------------------------
+// geometry helpers (exact op order)
+// ---------------------------------------------------------------------------
+
+// Back-projection of pixel (u,v) at integer depth d (0.1 mm units), Sec. IV-A.
+__device__ __forceinline__ float3 back_project(const DevScene& sc, int u, int v, unsigned d)
+{
+    float z = __fdiv_rn(__uint2float_rn(d), 10000.0f);
+    float x = __fdiv_rn(__fmul_rn(__fsub_rn(__int2float_rn(u), sc.cx), z), sc.fx);
+    float y = __fdiv_rn(__fmul_rn(__fsub_rn(__int2float_rn(v), sc.cy), z), sc.fy);
+    return make_float3(x, y, z);
+}
+
+__device__ __forceinline__ int cell_coord(float x, float cell)
+{
+    return __float2int_rd(__fdiv_rn(x, cell));
+}
+
+__device__ __forceinline__ unsigned long long cell_key(int cx, int cy, int cz)
+{
+    return ((unsigned long long)((unsigned)(cx + kCellBias) & 0x1FFFFFu) << 42) |
+           ((unsigned long long)((unsigned)(cy + kCellBias) & 0x1FFFFFu) << 21) |
+           (unsigned long long)((unsigned)(cz + kCellBias) & 0x1FFFFFu);
+}
+
+__device__ __forceinline__ uint32_t hash_slot(unsigned long long k, uint32_t mask)
+{
+    k ^= k >> 31;
+    k *= 0x7fb5d329728ea185ull;
+    k ^= k >> 27;
+    k *= 0x81dadef4bc2dd44dull;
+    k ^= k >> 33;
+    return (uint32_t)k & mask;
+}
+
+// ---------------------------------------------------------------------------
+// observation build: per-pixel CIELAB, cloud I, voxel hash (cell = delta*(1+1/64))
+// ---------------------------------------------------------------------------
+
+__global__ void k_obs_insert(DevScene sc, const uint8_t* __restrict__ rgb, float4* lab,
+                             int32_t* slot_of_pixel, unsigned long long* keys, uint32_t* count,
+                             uint32_t mask, int* n_valid, int* err)
+{
+    int npx = sc.W * sc.H;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npx) return;
+    int u = i % sc.W, v = i / sc.W;
+    float3 L = srgb8_to_lab(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
+    lab[i] = make_float4(L.x, L.y, L.z, 0.0f);
+    unsigned d = sc.depth[i];
+    int slot = -1;
+    if (d != 0 && u % sc.stride == 0 && v % sc.stride == 0) {
+        float3 p = back_project(sc, u, v, d);
+        unsigned long long k = cell_key(cell_coord(p.x, sc.cell), cell_coord(p.y, sc.cell),
+                                        cell_coord(p.z, sc.cell));
+        uint32_t h = hash_slot(k, mask);
+        for (uint32_t probe = 0; probe <= mask; ++probe) {
+            unsigned long long prev = atomicCAS(&keys[h], kEmptyKey, k);
+            if (prev == kEmptyKey || prev == k) {
+                slot = (int)h;
+                break;
+            }
+            h = (h + 1) & mask;
+        }
+        if (slot < 0) atomicOr(err, kErrHashFull);
+        else atomicAdd(&count[slot], 1u);
+        atomicAdd(n_valid, 1);
+    }
+    slot_of_pixel[i] = slot;
+}
+
+// Exclusive scan of count[0..n) into start[], in tiles of 1024 (one block per
+// tile), then a second pass over the tile sums, then the offsets.
+__device__ __forceinline__ uint32_t block_incl_scan_1024(uint32_t x, uint32_t* warp_sums)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = warp_sums[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    if (w > 0) x += warp_sums[w - 1];
+    return x;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* count, uint32_t* start,
+                                                    uint32_t* tile_sums, uint32_t n)
+{
+    __shared__ uint32_t ws[32];
+    uint32_t i = blockIdx.x * 1024u + threadIdx.x;
+    uint32_t x = i < n ? count[i] : 0u;
+    uint32_t incl = block_incl_scan_1024(x, ws);
+    if (i < n) start[i] = incl - x;
+    if (threadIdx.x == 1023) tile_sums[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(uint32_t* tile_sums, uint32_t n_tiles)
+{
+    // n_tiles <= 1024 * k; sequential over chunks of 1024
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < n_tiles; base += 1024) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t x = i < n_tiles ? tile_sums[i] : 0u;
+        uint32_t incl = block_incl_scan_1024(x, ws);
+        uint32_t c = carry;
+        if (i < n_tiles) tile_sums[i] = c + incl - x;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void k_finish_table(const unsigned long long* keys, const uint32_t* count,
+                               uint32_t* start, const uint32_t* tile_offsets, uint4* table,
+                               uint32_t n)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t s = start[i] + tile_offsets[i >> 10];
+    start[i] = s;
+    unsigned long long k = keys[i];
+    table[i] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), s, k == kEmptyKey ? 0u : count[i]);
+}
+
+__global__ void k_obs_scatter(DevScene sc, const int32_t* slot_of_pixel, const uint32_t* start,
+                              uint32_t* cursor, float4* pts)
+{
+    int npx = sc.W * sc.H;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npx) return;
+    int slot = slot_of_pixel[i];
+    if (slot < 0) return;
+    int u = i % sc.W, v = i / sc.W;
+    float3 p = back_project(sc, u, v, sc.depth[i]);
+    uint32_t pos = start[slot] + atomicAdd(&cursor[slot], 1u);
+    pts[pos] = make_float4(p.x, p.y, p.z, __int_as_float(i));
+}
+
+cudaError_t launch_build(const DevScene& sc, const BuildBuffers& b, uint32_t cap,
+                         const uint8_t* rgb_dev, int* err, cudaStream_t s)
+{
+    int npx = sc.W * sc.H;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.keys, 0xFF, sizeof(unsigned long long) * cap, s))) return e;
+    if ((e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * cap, s))) return e;
+    if ((e = cudaMemsetAsync(b.cursor, 0, sizeof(uint32_t) * cap, s))) return e;
+    if ((e = cudaMemsetAsync(b.n_valid, 0, sizeof(int), s))) return e;
+    int blocks = (npx + 255) / 256;
+    k_obs_insert<<<blocks, 256, 0, s>>>(sc, rgb_dev, b.lab, b.slot_of_pixel, b.keys, b.count,
+                                        cap - 1, b.n_valid, err);
+    uint32_t n_tiles = (cap + 1023) / 1024;
+    // tile sums live after the cursor array's use: reuse `cursor` tail is unsafe, so
+    // place them in the upper part of slot storage-free scratch: the `start` array
+    // holds per-slot offsets, the tile sums go to cursor[cap - n_tiles ..] before the
+    // cursors are needed -- instead keep it simple and use a dedicated region:
+    uint32_t* tile_sums = b.cursor + cap;   // BuildBuffers::cursor has cap + n_tiles words
+    k_scan_tiles<<<n_tiles, 1024, 0, s>>>(b.count, b.start, tile_sums, cap);
+    k_scan_sums<<<1, 1024, 0, s>>>(tile_sums, n_tiles);
+    k_finish_table<<<(cap + 255) / 256, 256, 0, s>>>(b.keys, b.count, b.start, tile_sums, b.table,
+                                                     cap);
+    k_obs_scatter<<<blocks, 256, 0, s>>>(sc, b.slot_of_pixel, b.start, b.cursor, b.pts);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// scoring kernel
+// ---------------------------------------------------------------------------
+
+constexpr int kQueueCap = 64;     // large-triangle queue entries per tile
+constexpr int kBigArea = 48;      // pixel-box area above which a warp rasterises the triangle
+
+struct TriSetup {
+    int x[3], y[3];               // snapped positions, 1/16 px
+    float iz[3];                  // 1/Z
+    int vid[3];                   // mesh vertex ids after the orientation swap
+    int A;                        // doubled area > 0
+};
+
+struct BigTri {                   // queued large triangle (64 bytes)
+    int x[3], y[3];
+    float iz[3];
+    int A, tri;
+    int u0, v0, u1, v1;
+    int pad;
+};
+
+__device__ __forceinline__ int edge_fn(int ax, int ay, int bx, int by, int px, int py)
+{
+    return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+__device__ __forceinline__ bool owns(int dx, int dy)
+{
+    return dy > 0 || (dy == 0 && dx < 0);
+}
+
+__device__ __forceinline__ int floor16(int x) { return x >> 4; }         // arithmetic shift
+__device__ __forceinline__ int ceil16(int x) { return -((-x) >> 4); }
+
+// Triangle set-up at a pose: transform, near/guard-band cull, projection,
+// 4-bit snap, orientation.  Returns false if culled or degenerate.
+__device__ __forceinline__ bool setup_triangle(const DevScene& sc, const DevMesh& m,
+                                               const float* P, int t, TriSetup& o)
+{
+    int4 tv = __ldg(&m.tris[t]);
+    int vids[3] = {tv.x, tv.y, tv.z};
+    const float gx0 = (float)(-16 * sc.W), gx1 = (float)(32 * sc.W);
+    const float gy0 = (float)(-16 * sc.H), gy1 = (float)(32 * sc.H);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float4 v = __ldg(&m.verts[vids[k]]);
+        float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P[0], v.x), __fmul_rn(P[1], v.y)),
+                                      __fmul_rn(P[2], v.z)), P[3]);
+        float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P[4], v.x), __fmul_rn(P[5], v.y)),
+                                      __fmul_rn(P[6], v.z)), P[7]);
+        float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P[8], v.x), __fmul_rn(P[9], v.y)),
+                                      __fmul_rn(P[10], v.z)), P[11]);
+        if (!(Z >= sc.z_near)) return false;
+        float px = __fadd_rn(__fmul_rn(sc.fx, __fdiv_rn(X, Z)), sc.cx);
+        float py = __fadd_rn(__fmul_rn(sc.fy, __fdiv_rn(Y, Z)), sc.cy);
+        float sx = __fmul_rn(px, 16.0f), sy = __fmul_rn(py, 16.0f);
+        if (!(sx >= gx0) || !(sx < gx1) || !(sy >= gy0) || !(sy < gy1)) return false;
+        o.x[k] = __float2int_rn(sx);
+        o.y[k] = __float2int_rn(sy);
+        o.iz[k] = __fdiv_rn(1.0f, Z);
+        o.vid[k] = vids[k];
+    }
+    int A = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], o.x[2], o.y[2]);
+    if (A == 0) return false;
+    if (A < 0) {
+        int tx = o.x[1], ty = o.y[1], tvid = o.vid[1];
+        float ti = o.iz[1];
+        o.x[1] = o.x[2]; o.y[1] = o.y[2]; o.iz[1] = o.iz[2]; o.vid[1] = o.vid[2];
+        o.x[2] = tx; o.y[2] = ty; o.iz[2] = ti; o.vid[2] = tvid;
+        A = -A;
+    }
+    o.A = A;
+    return true;
+}
+
+// Depth of a covered sample from the edge values (perspective-correct 1/Z).
+// Returns false if the depth falls outside [1, 2^32-1].
+__device__ __forceinline__ bool sample_depth(int w0, int w1, int w2, const float* iz, int A,
+                                             unsigned& d)
+{
+    float num = __fadd_rn(__fadd_rn(__fmul_rn(__int2float_rn(w0), iz[0]),
+                                    __fmul_rn(__int2float_rn(w1), iz[1])),
+                          __fmul_rn(__int2float_rn(w2), iz[2]));
+    float izp = __fdiv_rn(num, __int2float_rn(A));
+    float z = __fdiv_rn(1.0f, izp);
+    float dz = __fmul_rn(z, 10000.0f);
+    if (!(dz < 4294967296.0f)) return false;
+    long long dd = __float2ll_rn(dz);
+    if (dd < 1 || dd > 0xFFFFFFFFll) return false;
+    d = (unsigned)dd;
+    return true;
+}
+
+template <bool K32>
+__device__ __forceinline__ void zmin(uint32_t* zbuf, int idx, unsigned d, int tri, int* err)
+{
+    if (K32) {
+        if (d > 0xFFFFu) {
+            atomicOr(err, kErrKeyRange);
+            return;
+        }
+        atomicMin(&zbuf[idx], (d << 16) | (unsigned)tri);
+    } else {
+        unsigned long long* z64 = reinterpret_cast<unsigned long long*>(zbuf);
+        atomicMin(&z64[idx], ((unsigned long long)d << 32) | (unsigned)tri);
+    }
+}
+
+// Rasterise the pixel box [u0,u1] x [v0,v1] of a set-up triangle, sequentially.
+template <bool K32>
+__device__ void raster_box(const int* x, const int* y, const float* iz, int A, int tri, int u0,
+                           int v0, int u1, int v1, int tu0, int tv0, int tw, uint32_t* zbuf,
+                           int* err)
+{
+    const bool o0 = owns(x[2] - x[1], y[2] - y[1]);
+    const bool o1 = owns(x[0] - x[2], y[0] - y[2]);
+    const bool o2 = owns(x[1] - x[0], y[1] - y[0]);
+    const int s0 = -16 * (y[2] - y[1]), s1 = -16 * (y[0] - y[2]), s2 = -16 * (y[1] - y[0]);
+    for (int v = v0; v <= v1; ++v) {
+        int sy = 16 * v, sx = 16 * u0;
+        int w0 = edge_fn(x[1], y[1], x[2], y[2], sx, sy);
+        int w1 = edge_fn(x[2], y[2], x[0], y[0], sx, sy);
+        int w2 = edge_fn(x[0], y[0], x[1], y[1], sx, sy);
+        for (int u = u0; u <= u1; ++u) {
+            bool cov = (w0 > 0 || (w0 == 0 && o0)) && (w1 > 0 || (w1 == 0 && o1)) &&
+                       (w2 > 0 || (w2 == 0 && o2));
+            if (cov) {
+                unsigned d;
+                if (sample_depth(w0, w1, w2, iz, A, d))
+                    zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, tri, err);
+            }
+            w0 += s0;
+            w1 += s1;
+            w2 += s2;
+        }
+    }
+}
+
+// Warp-cooperative 27-cell radius search around q: the nearest observed point
+// with squared distance <= delta^2 (ties to the lowest pixel index), packed as
+// (d2 bits << 32) | pixel, or kEmptyKey.  All 32 lanes must call it.
+__device__ __forceinline__ unsigned long long probe_nn(const DevScene& sc, float qx, float qy,
+                                                       float qz, int2* wscr, int lane)
+{
+    int cx = cell_coord(qx, sc.cell), cy = cell_coord(qy, sc.cell), cz = cell_coord(qz, sc.cell);
+    uint32_t start = 0, cnt = 0;
+    if (lane < 27) {
+        int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+        unsigned long long key = cell_key(cx + dx, cy + dy, cz + dz);
+        uint32_t h = hash_slot(key, sc.table_mask);
+        for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
+            uint4 e = __ldg(&sc.table[h]);
+            unsigned long long k = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
+            if (k == key) {
+                start = e.z;
+                cnt = e.w;
+                break;
+            }
+            if (k == kEmptyKey) break;
+            h = (h + 1) & sc.table_mask;
+        }
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane < 27) wscr[lane] = make_int2((int)start, (int)(incl - cnt));
+    if (lane == 27) wscr[27] = make_int2(0, (int)total);
+    __syncwarp();
+    unsigned long long best = kEmptyKey;
+    int r = 0;
+    for (uint32_t k = lane; k < total; k += 32) {
+        while ((uint32_t)wscr[r + 1].y <= k) ++r;
+        int2 e = wscr[r];
+        float4 p = __ldg(&sc.pts[e.x + (int)(k - (uint32_t)e.y)]);
+        float dx = __fsub_rn(qx, p.x), dy = __fsub_rn(qy, p.y), dz = __fsub_rn(qz, p.z);
+        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        if (d2 <= sc.delta2) {
+            unsigned long long key =
+                ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(p.w);
+            best = key < best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other < best ? other : best;
+    }
+    __syncwarp();
+    return best;
+}
+
+// Conservative pixel box of an object-frame box [lo,hi] at pose P (2 px
+// margin), clipped to [cu0,cu1) x [cv0,cv1).  Falls back to the clip box
+// when a corner is not in front of the camera.  Also returns the largest Z.
+__device__ void project_box(const DevScene& sc, const float* P, const float* lo, const float* hi,
+                            int cu0, int cv0, int cu1, int cv1, int* box, float* zmax)
+{
+    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f, zm = -3.0e38f;
+    bool ok = true;
+    for (int c = 0; c < 8; ++c) {
+        float x = (c & 1) ? hi[0] : lo[0];
+        float y = (c & 2) ? hi[1] : lo[1];
+        float z = (c & 4) ? hi[2] : lo[2];
+        float X = P[0] * x + P[1] * y + P[2] * z + P[3];
+        float Y = P[4] * x + P[5] * y + P[6] * z + P[7];
+        float Z = P[8] * x + P[9] * y + P[10] * z + P[11];
+        zm = fmaxf(zm, Z);
+        if (!(Z > 1e-4f)) {
+            ok = false;
+            continue;
+        }
+        float u = sc.fx * (X / Z) + sc.cx, v = sc.fy * (Y / Z) + sc.cy;
+        umin = fminf(umin, u); umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+    }
+    *zmax = zm;
+    if (!ok || !(umax - umin < 1.0e7f) || !(vmax - vmin < 1.0e7f)) {
+        box[0] = cu0; box[1] = cv0; box[2] = cu1; box[3] = cv1;
+        return;
+    }
+    int u0 = (int)floorf(fmaxf(umin, -1.0e7f)) - 2, u1 = (int)ceilf(fminf(umax, 1.0e7f)) + 3;
+    int v0 = (int)floorf(fmaxf(vmin, -1.0e7f)) - 2, v1 = (int)ceilf(fminf(vmax, 1.0e7f)) + 3;
+    box[0] = max(u0, cu0); box[1] = max(v0, cv0);
+    box[2] = min(u1, cu1); box[3] = min(v1, cv1);
+    if (box[2] < box[0]) box[2] = box[0];
+    if (box[3] < box[1]) box[3] = box[1];
+}
+
+template <int NT, bool K32>
+__device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox, uint32_t* zbuf,
+                            uint32_t* marks, BigTri* queue, int2* wscr_all, int* s_qn,
+                            const int* vbox, int& jr_local)
+{
+    const DevScene& sc = a.sc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int2* wscr = wscr_all + warp * 28;
+    const int s = sc.stride;
+    const int rw = rbox[2] - rbox[0], rh = rbox[3] - rbox[1];
+    if (rw <= 0 || rh <= 0) return;
+    const int cap_px = K32 ? a.zcap_words : a.zcap_words / 2;
+    const int tw = min(rw, cap_px);
+    const int th = max(1, cap_px / tw);
+    const uint32_t empty32 = 0xFFFFFFFFu;
+    const int vw = vbox[2] - vbox[0];
+    for (int tv0 = rbox[1]; tv0 < rbox[3]; tv0 += th) {
+        for (int tu0 = rbox[0]; tu0 < rbox[2]; tu0 += tw) {
+            const int tu1 = min(tu0 + tw, rbox[2]), tv1 = min(tv0 + th, rbox[3]);
+            const int tpx = tw * (tv1 - tv0);
+            const int words = K32 ? tpx : 2 * tpx;
+            for (int i = threadIdx.x; i < words; i += NT) zbuf[i] = empty32;
+            if (threadIdx.x == 0) *s_qn = 0;
+            __syncthreads();
+            // ---- raster: one thread per triangle, large ones queued for a warp
+            for (int t = threadIdx.x; t < a.m.n_tris; t += NT) {
+                TriSetup o;
+                if (!setup_triangle(sc, a.m, P, t, o)) continue;
+                int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
+                int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
+                int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
+                int v0 = max(ceil16(ymin), tv0), v1 = min(floor16(ymax), tv1 - 1);
+                if (u0 > u1 || v0 > v1) continue;
+                int area = (u1 - u0 + 1) * (v1 - v0 + 1);
+                if (area > kBigArea) {
+                    int q = atomicAdd(s_qn, 1);
+                    if (q < kQueueCap) {
+                        BigTri& b = queue[q];
+                        for (int k = 0; k < 3; ++k) { b.x[k] = o.x[k]; b.y[k] = o.y[k]; b.iz[k] = o.iz[k]; }
+                        b.A = o.A; b.tri = t; b.u0 = u0; b.v0 = v0; b.u1 = u1; b.v1 = v1;
+                        continue;
+                    }
+                }
+                raster_box<K32>(o.x, o.y, o.iz, o.A, t, u0, v0, u1, v1, tu0, tv0, tw, zbuf, a.err);
+            }
+            __syncthreads();
+            const int nq = min(*s_qn, kQueueCap);
+            for (int e = warp; e < nq; e += NT / 32) {
+                const BigTri& b = queue[e];
+                const int bw = b.u1 - b.u0 + 1, area = bw * (b.v1 - b.v0 + 1);
+                const bool o0 = owns(b.x[2] - b.x[1], b.y[2] - b.y[1]);
+                const bool o1 = owns(b.x[0] - b.x[2], b.y[0] - b.y[2]);
+                const bool o2 = owns(b.x[1] - b.x[0], b.y[1] - b.y[0]);
+                for (int k = lane; k < area; k += 32) {
+                    int u = b.u0 + k % bw, v = b.v0 + k / bw;
+                    int sx = 16 * u, sy = 16 * v;
+                    int w0 = edge_fn(b.x[1], b.y[1], b.x[2], b.y[2], sx, sy);
+                    int w1 = edge_fn(b.x[2], b.y[2], b.x[0], b.y[0], sx, sy);
+                    int w2 = edge_fn(b.x[0], b.y[0], b.x[1], b.y[1], sx, sy);
+                    bool cov = (w0 > 0 || (w0 == 0 && o0)) && (w1 > 0 || (w1 == 0 && o1)) &&
+                               (w2 > 0 || (w2 == 0 && o2));
+                    unsigned d;
+                    if (cov && sample_depth(w0, w1, w2, b.iz, b.A, d))
+                        zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, b.tri, a.err);
+                }
+            }
+            __syncthreads();
+            if (a.dump) {
+                for (int i = threadIdx.x; i < tpx; i += NT) {
+                    int u = tu0 + i % tw, v = tv0 + i / tw;
+                    if (u >= tu1) continue;
+                    unsigned long long k;
+                    if (K32) {
+                        uint32_t w = zbuf[i];
+                        k = (w == empty32) ? kEmptyKey
+                                           : (((unsigned long long)(w >> 16) << 32) | (w & 0xFFFFu));
+                    } else {
+                        k = reinterpret_cast<unsigned long long*>(zbuf)[i];
+                    }
+                    a.dump[(size_t)v * sc.W + u] = k;
+                }
+            }
+            // ---- resolve + radius search over the stride lattice of the tile
+            const int us0 = ((tu0 + s - 1) / s) * s, vs0 = ((tv0 + s - 1) / s) * s;
+            const int nu = us0 < tu1 ? (tu1 - 1 - us0) / s + 1 : 0;
+            const int nv = vs0 < tv1 ? (tv1 - 1 - vs0) / s + 1 : 0;
+            const int total = nu * nv;
+            for (int base = warp * 32; base < total; base += NT) {
+                int k = base + lane;
+                bool kept = false;
+                float qx = 0.f, qy = 0.f, qz = 0.f;
+                uint32_t crgb = 0;
+                if (k < total) {
+                    int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
+                    int zi = (v - tv0) * tw + (u - tu0);
+                    unsigned d = 0;
+                    int tri = -1;
+                    if (K32) {
+                        uint32_t w = zbuf[zi];
+                        if (w != empty32) { d = w >> 16; tri = (int)(w & 0xFFFFu); }
+                    } else {
+                        unsigned long long w = reinterpret_cast<unsigned long long*>(zbuf)[zi];
+                        if (w != kEmptyKey) { d = (unsigned)(w >> 32); tri = (int)(uint32_t)w; }
+                    }
+                    if (tri >= 0) {
+                        int pix = v * sc.W + u;
+                        unsigned dobs = __ldg(&sc.depth[pix]);
+                        bool occluded = dobs > 0 && (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
+                                        (a.label < 0 || __ldg(&sc.labels[pix]) != a.label);
+                        if (!occluded) {
+                            TriSetup o;
+                            setup_triangle(sc, a.m, P, tri, o);
+                            int sx = 16 * u, sy = 16 * v;
+                            long long w0 = edge_fn(o.x[1], o.y[1], o.x[2], o.y[2], sx, sy);
+                            long long w1 = edge_fn(o.x[2], o.y[2], o.x[0], o.y[0], sx, sy);
+                            long long w2 = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], sx, sy);
+                            uint32_t c0 = __float_as_uint(__ldg(&a.m.verts[o.vid[0]].w));
+                            uint32_t c1 = __float_as_uint(__ldg(&a.m.verts[o.vid[1]].w));
+                            uint32_t c2 = __float_as_uint(__ldg(&a.m.verts[o.vid[2]].w));
+                            long long half = o.A / 2;
+#pragma unroll
+                            for (int ch = 0; ch < 3; ++ch) {
+                                long long num = w0 * ((c0 >> (8 * ch)) & 255) + w1 * ((c1 >> (8 * ch)) & 255) +
+                                                w2 * ((c2 >> (8 * ch)) & 255) + half;
+                                crgb |= (uint32_t)(num / o.A) << (8 * ch);
+                            }
+                            float3 q = back_project(sc, u, v, d);
+                            qx = q.x; qy = q.y; qz = q.z;
+                            kept = true;
+                        }
+                    }
+                }
+                unsigned ballot = __ballot_sync(0xffffffffu, kept);
+                unsigned long long mine = kEmptyKey;
+                while (ballot) {
+                    int i = __ffs(ballot) - 1;
+                    ballot &= ballot - 1;
+                    float bx = __shfl_sync(0xffffffffu, qx, i);
+                    float by = __shfl_sync(0xffffffffu, qy, i);
+                    float bz = __shfl_sync(0xffffffffu, qz, i);
+                    unsigned long long r = probe_nn(sc, bx, by, bz, wscr, lane);
+                    if (lane == i) mine = r;
+                }
+                if (kept) {
+                    bool explained = mine != kEmptyKey;
+                    int pnn = (int)(uint32_t)mine;
+                    if (explained && sc.color_check) {
+                        float4 lp = __ldg(&sc.lab[pnn]);
+                        float3 lq = srgb8_to_lab(crgb & 255, (crgb >> 8) & 255, (crgb >> 16) & 255);
+                        if (ciede2000(lq, make_float3(lp.x, lp.y, lp.z)) > sc.tau_c) explained = false;
+                    }
+                    if (!explained) {
+                        ++jr_local;
+                    } else {
+                        int pu = pnn % sc.W, pv = pnn / sc.W;
+                        if (pu >= vbox[0] && pu < vbox[2] && pv >= vbox[1] && pv < vbox[3]) {
+                            int bit = (pv - vbox[1]) * vw + (pu - vbox[0]);
+                            atomicOr(&marks[bit >> 5], 1u << (bit & 31));
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_score(ScoreArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float s_pose[12];
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_qn;
+    __shared__ int s_red[3][NT / 32];
+
+    const long long h = blockIdx.x;
+    if (h >= a.n) return;
+    if (threadIdx.x < 12) s_pose[threadIdx.x] = a.poses[h * 12 + threadIdx.x];
+    __syncthreads();
+    const DevScene& sc = a.sc;
+    if (threadIdx.x == 0) {
+        float zmax;
+        project_box(sc, s_pose, a.m.lo, a.m.hi, a.roi[0], a.roi[1], a.roi[2], a.roi[3], s_rbox, &zmax);
+        s_k32 = (a.m.n_tris <= 65535 && zmax < 6.5f) ? 1 : 0;
+        if (a.label >= 0) {
+            s_vbox[0] = a.roi[0]; s_vbox[1] = a.roi[1]; s_vbox[2] = a.roi[2]; s_vbox[3] = a.roi[3];
+        } else {
+            float lo[3] = {-a.m.vol_r, -a.m.vol_r, 0.0f}, hi[3] = {a.m.vol_r, a.m.vol_r, a.m.vol_h};
+            float zv;
+            project_box(sc, s_pose, lo, hi, 0, 0, sc.W, sc.H, s_vbox, &zv);
+        }
+        long long bits = (long long)(s_vbox[2] - s_vbox[0]) * (s_vbox[3] - s_vbox[1]);
+        if (bits > 32ll * a.mark_words) {
+            atomicOr(a.err, kErrMarkCap);
+            s_vbox[2] = s_vbox[0];
+            s_vbox[3] = s_vbox[1];
+        }
+    }
+    __syncthreads();
+    uint32_t* zbuf = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* marks = zbuf + a.zcap_words;
+    BigTri* queue = reinterpret_cast<BigTri*>(marks + a.mark_words);
+    int2* wscr = reinterpret_cast<int2*>(queue + kQueueCap);
+
+    const int vw = s_vbox[2] - s_vbox[0], vh = s_vbox[3] - s_vbox[1];
+    const int mwords = (vw * vh + 31) / 32;
+    for (int i = threadIdx.x; i < mwords; i += NT) marks[i] = 0u;
+    __syncthreads();
+
+    int jr = 0;
+    if (s_k32)
+        score_tiles<NT, true>(a, s_pose, s_rbox, zbuf, marks, queue, wscr, &s_qn, s_vbox, jr);
+    else
+        score_tiles<NT, false>(a, s_pose, s_rbox, zbuf, marks, queue, wscr, &s_qn, s_vbox, jr);
+
+    // ---- J_o over the admissible set V(h)
+    int n_in = 0, n_marked = 0;
+    const int s = sc.stride;
+    const int us0 = ((s_vbox[0] + s - 1) / s) * s, vs0 = ((s_vbox[1] + s - 1) / s) * s;
+    const int nu = us0 < s_vbox[2] ? (s_vbox[2] - 1 - us0) / s + 1 : 0;
+    const int nv = vs0 < s_vbox[3] ? (s_vbox[3] - 1 - vs0) / s + 1 : 0;
+    const float* P = s_pose;
+    const float rr = __fmul_rn(a.m.vol_r, a.m.vol_r);
+    for (int k = threadIdx.x; k < nu * nv; k += NT) {
+        int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
+        int pix = v * sc.W + u;
+        unsigned d = __ldg(&sc.depth[pix]);
+        if (d == 0) continue;
+        bool in;
+        if (a.label >= 0) {
+            in = __ldg(&sc.labels[pix]) == a.label;
+        } else {
+            float3 p = back_project(sc, u, v, d);
+            float e0 = __fsub_rn(p.x, P[3]), e1 = __fsub_rn(p.y, P[7]), e2 = __fsub_rn(p.z, P[11]);
+            float q0 = __fadd_rn(__fadd_rn(__fmul_rn(P[0], e0), __fmul_rn(P[4], e1)), __fmul_rn(P[8], e2));
+            float q1 = __fadd_rn(__fadd_rn(__fmul_rn(P[1], e0), __fmul_rn(P[5], e1)), __fmul_rn(P[9], e2));
+            float q2 = __fadd_rn(__fadd_rn(__fmul_rn(P[2], e0), __fmul_rn(P[6], e1)), __fmul_rn(P[10], e2));
+            in = __fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)) <= rr && q2 >= 0.0f && q2 <= a.m.vol_h;
+        }
+        if (in) {
+            ++n_in;
+            int bit = (v - s_vbox[1]) * vw + (u - s_vbox[0]);
+            n_marked += (marks[bit >> 5] >> (bit & 31)) & 1u;
+        }
+    }
+    // ---- warp-shuffle reduction of (J_r, |I cap V|, marked)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        jr += __shfl_xor_sync(0xffffffffu, jr, o);
+        n_in += __shfl_xor_sync(0xffffffffu, n_in, o);
+        n_marked += __shfl_xor_sync(0xffffffffu, n_marked, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s_red[0][warp] = jr; s_red[1][warp] = n_in; s_red[2][warp] = n_marked; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int x = lane < NT / 32 ? s_red[0][lane] : 0;
+        int y = lane < NT / 32 ? s_red[1][lane] : 0;
+        int z = lane < NT / 32 ? s_red[2][lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+        }
+        if (lane == 0) {
+            a.costs[2 * h] = y - z;
+            a.costs[2 * h + 1] = x;
+        }
+    }
+}
+
+size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
+{
+    return sizeof(uint32_t) * (size_t)(cfg.zcap_words + mark_words) + sizeof(BigTri) * kQueueCap +
+           sizeof(int2) * 28 * (cfg.threads / 32);
+}
+
+template <int NT>
+static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, cudaStream_t s)
+{
+    size_t smem = score_smem_bytes(cfg, a.mark_words);
+    cudaError_t e = cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long kMaxGrid = 0x7FFFFFFFll;
+    ScoreArgs b = a;
+    for (long long off = 0; off < a.n; off += kMaxGrid) {
+        long long cnt = a.n - off < kMaxGrid ? a.n - off : kMaxGrid;
+        b.poses = a.poses + 12 * off;
+        b.costs = a.costs + 2 * off;
+        b.n = cnt;
+        k_score<NT><<<(unsigned)cnt, NT, smem, s>>>(b);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, cudaStream_t s)
+{
+    if (a.n <= 0) return cudaSuccess;
+    switch (cfg.threads) {
+    case 128: return launch_score_nt<128>(a, cfg, s);
+    case 512: return launch_score_nt<512>(a, cfg, s);
+    default: return launch_score_nt<256>(a, cfg, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// argmin of J = J_o + J_r (warp shuffles, then the last block reduces the partials)
+// ---------------------------------------------------------------------------
+
+constexpr int kBestThreads = 256;
+
+struct BestKey {
+    unsigned long long hi;   // (J << 32) | 0
+    unsigned long long id;   // caller id or index
+    long long idx;
+};
+
+__device__ __forceinline__ bool best_less(const BestKey& x, const BestKey& y)
+{
+    if (x.hi != y.hi) return x.hi < y.hi;
+    if (x.id != y.id) return x.id < y.id;
+    return x.idx < y.idx;
+}
+
+__device__ __forceinline__ BestKey shfl_best(const BestKey& k, int o)
+{
+    BestKey r;
+    r.hi = __shfl_xor_sync(0xffffffffu, k.hi, o);
+    r.id = __shfl_xor_sync(0xffffffffu, k.id, o);
+    r.idx = __shfl_xor_sync(0xffffffffu, k.idx, o);
+    return r;
+}
+
+__device__ BestKey block_best(BestKey k, BestKey* sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        BestKey t = shfl_best(k, o);
+        if (best_less(t, k)) k = t;
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = k;
+    __syncthreads();
+    if (w == 0) {
+        BestKey none = {~0ull, ~0ull, 0x7FFFFFFFFFFFFFFFll};
+        k = lane < kBestThreads / 32 ? sh[lane] : none;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            BestKey t = shfl_best(k, o);
+            if (best_less(t, k)) k = t;
+        }
+    }
+    return k;
+}
+
+__global__ void __launch_bounds__(kBestThreads) k_best(BestArgs a)
+{
+    __shared__ BestKey sh[kBestThreads / 32];
+    __shared__ bool last;
+    BestKey k = {~0ull, ~0ull, 0x7FFFFFFFFFFFFFFFll};
+    for (long long i = blockIdx.x * (long long)kBestThreads + threadIdx.x; i < a.n;
+         i += (long long)gridDim.x * kBestThreads) {
+        long long J = (long long)a.costs[2 * i] + a.costs[2 * i + 1];
+        BestKey c = {(unsigned long long)J << 32, a.ids ? a.ids[i] : (unsigned long long)i, i};
+        if (best_less(c, k)) k = c;
+    }
+    k = block_best(k, sh);
+    if (threadIdx.x == 0) {
+        a.partial[3 * blockIdx.x + 0] = k.hi;
+        a.partial[3 * blockIdx.x + 1] = k.id;
+        a.partial[3 * blockIdx.x + 2] = (unsigned long long)k.idx;
+        __threadfence();
+        unsigned t = atomicAdd(a.ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    BestKey m = {~0ull, ~0ull, 0x7FFFFFFFFFFFFFFFll};
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kBestThreads) {
+        BestKey c = {a.partial[3 * b], a.partial[3 * b + 1], (long long)a.partial[3 * b + 2]};
+        if (best_less(c, m)) m = c;
+    }
+    __syncthreads();
+    m = block_best(m, sh);
+    if (threadIdx.x == 0) {
+        *a.best_index = m.idx;
+        *a.best_cost = (int32_t)(m.hi >> 32);
+        *a.ticket = 0u;
+    }
+}
+
+int best_blocks(long long n)
+{
+    long long b = (n + kBestThreads - 1) / kBestThreads;
+    return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
+cudaError_t launch_best(const BestArgs& a, cudaStream_t s)
+{
+    k_best<<<best_blocks(a.n), kBestThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace perch

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libperch (include/perch.h), same names as the C ABI.
+
+Argument marshalling only: every step of the scoring path runs in the CUDA
+library.  Host-pointer (synchronous) calls take numpy arrays; device-pointer
+(asynchronous) calls take torch CUDA tensors plus a stream, and PyTorch is used
+for nothing but that device memory and the stream handle.  The module fails
+loudly when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+PERCH_OK = 0
+STATUS = {0: "PERCH_OK", -1: "PERCH_E_INVALID", -2: "PERCH_E_NOMEM", -3: "PERCH_E_BUDGET",
+          -4: "PERCH_E_NOTFOUND", -5: "PERCH_E_CUDA", -6: "PERCH_E_TIMEOUT", -7: "PERCH_E_BUSY"}
+
+# every function that include/perch.h declares
+EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_error",
+           "perch_hbm_used", "perch_load_mesh", "perch_release_mesh", "perch_set_observation",
+           "perch_release_scene", "perch_score_hypotheses", "perch_best", "perch_set_launch_config",
+           "perch_debug_render_keys")
+
+
+class PerchError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class perch_params(C.Structure):
+    _fields_ = [("delta_m", C.c_float), ("tau_c", C.c_float), ("color_check", C.c_int32),
+                ("stride", C.c_int32), ("occ_margin_units", C.c_int32), ("z_near_m", C.c_float),
+                ("jo_mode", C.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libperch.so (in-tree).  Raises if it is missing: build it first."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libperch.so not found at {path}; run __graft_entry__.build() "
+                           "(the scoring path has no CPU fallback)")
+    L = C.CDLL(path)
+    P, I32, I64, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    sig = {
+        "perch_default_params": ([P], I32),
+        "perch_create": ([P, I32, U64], I32),
+        "perch_destroy": ([P], I32),
+        "perch_last_error": ([P], C.c_char_p),
+        "perch_hbm_used": ([P], U64),
+        "perch_load_mesh": ([P, P, P, I32, P, I32, C.c_float, C.c_float, P], I32),
+        "perch_release_mesh": ([P, I32], I32),
+        "perch_set_observation": ([P, P, P, P, I32, I32, C.c_float, C.c_float, C.c_float,
+                                   C.c_float, P, P], I32),
+        "perch_release_scene": ([P, I32], I32),
+        "perch_score_hypotheses": ([P, I32, I32, I32, P, P, I64, P, P], I32),
+        "perch_best": ([P, P, P, I64, P, P, P], I32),
+        "perch_set_launch_config": ([P, I32, I32], I32),
+        "perch_debug_render_keys": ([P, I32, I32, P, P, P], I32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(ctx, st):
+    if st != PERCH_OK:
+        msg = load().perch_last_error(ctx)
+        raise PerchError(st, msg.decode() if msg else "")
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype)
+    return a, a.ctypes.data
+
+
+def _ptr_of(x):
+    """Device pointer of a torch CUDA tensor, or host pointer of a numpy array."""
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def perch_default_params(**over) -> perch_params:
+    p = perch_params()
+    load().perch_default_params(C.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def perch_create(device: int = 0, hbm_budget_bytes: int = 0):
+    ctx = C.c_void_p()
+    st = load().perch_create(C.byref(ctx), device, hbm_budget_bytes)
+    if st != PERCH_OK:
+        raise PerchError(st, "perch_create failed")
+    return ctx
+
+
+def perch_destroy(ctx):
+    _check(ctx, load().perch_destroy(ctx))
+
+
+def perch_last_error(ctx) -> str:
+    m = load().perch_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def perch_hbm_used(ctx) -> int:
+    return int(load().perch_hbm_used(ctx))
+
+
+def perch_load_mesh(ctx, verts, rgb, tris, vol_radius_m, vol_height_m) -> int:
+    v, pv = _host(verts, np.float32)
+    c, pc = _host(rgb, np.uint8)
+    t, pt = _host(tris, np.int32)
+    mid = C.c_int32()
+    _check(ctx, load().perch_load_mesh(ctx, pv, pc, v.shape[0], pt, t.shape[0], vol_radius_m,
+                                        vol_height_m, C.byref(mid)))
+    return mid.value
+
+
+def perch_release_mesh(ctx, mesh_id):
+    _check(ctx, load().perch_release_mesh(ctx, mesh_id))
+
+
+def perch_set_observation(ctx, depth, rgb, labels, fx, fy, cx, cy, params: perch_params) -> int:
+    d, pd = _host(depth, np.uint16)
+    c, pc = _host(rgb, np.uint8)
+    lab, pl = (None, None) if labels is None else _host(labels, np.int32)
+    H, W = d.shape
+    sid = C.c_int32()
+    _check(ctx, load().perch_set_observation(ctx, pd, pc, pl, W, H, fx, fy, cx, cy,
+                                              C.byref(params), C.byref(sid)))
+    return sid.value
+
+
+def perch_release_scene(ctx, scene_id):
+    _check(ctx, load().perch_release_scene(ctx, scene_id))
+
+
+def _roi(roi):
+    if roi is None:
+        return None, None
+    r = (C.c_int32 * 4)(*[int(x) for x in roi])
+    return r, C.cast(r, C.c_void_p)
+
+
+def perch_score_hypotheses(ctx, scene_id, mesh_id, label, roi, poses, costs=None, stream=None):
+    """Host mode (stream None): poses numpy (n,12) -> returns costs (n,2) int32.
+    Device mode: poses and costs torch CUDA tensors, stream a torch.cuda.Stream or
+    raw handle; enqueues and returns costs."""
+    keep, proi = _roi(roi)
+    if stream is None:
+        p, pp = _host(poses, np.float32)
+        n = p.size // 12
+        out = np.empty((n, 2), np.int32) if costs is None else costs
+        _check(ctx, load().perch_score_hypotheses(ctx, scene_id, mesh_id, label, proi, pp, n,
+                                                   out.ctypes.data, None))
+        return out
+    n = poses.numel() // 12
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(ctx, load().perch_score_hypotheses(ctx, scene_id, mesh_id, label, proi,
+                                               _ptr_of(poses), n, _ptr_of(costs), handle))
+    return costs
+
+
+def perch_best(ctx, costs, ids=None, stream=None, out_index=None, out_cost=None):
+    """Host mode: costs numpy (n,2) -> (best_index, best_cost).  Device mode:
+    costs/ids/out_index/out_cost torch CUDA tensors, result written on `stream`."""
+    if stream is None:
+        c, pc = _host(costs, np.int32)
+        n = c.size // 2
+        pi = None
+        if ids is not None:
+            ids_a, pi = _host(ids, np.uint64)
+        bi = C.c_int64()
+        bc = C.c_int32()
+        _check(ctx, load().perch_best(ctx, pc, pi, n, C.byref(bi), C.byref(bc), None))
+        return bi.value, bc.value
+    n = costs.numel() // 2
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(ctx, load().perch_best(ctx, _ptr_of(costs), None if ids is None else _ptr_of(ids), n,
+                                   _ptr_of(out_index), _ptr_of(out_cost), handle))
+
+
+def perch_set_launch_config(ctx, threads, zbuf_words):
+    _check(ctx, load().perch_set_launch_config(ctx, threads, zbuf_words))
+
+
+def perch_debug_render_keys(ctx, scene_id, mesh_id, roi, pose, W, H):
+    keep, proi = _roi(roi)
+    p, pp = _host(pose, np.float32)
+    keys = np.empty((H, W), np.uint64)
+    _check(ctx, load().perch_debug_render_keys(ctx, scene_id, mesh_id, proi, pp, keys.ctypes.data))
+    return keys
+
+
+class Context:
+    """Owning wrapper: a perch context plus the meshes and scenes loaded into it."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        self.ctx = perch_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.ctx is not None:
+            perch_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_mesh(self, mesh):
+        return perch_load_mesh(self.ctx, mesh.verts, mesh.rgb, mesh.tris, mesh.vol_radius,
+                               mesh.vol_height)
+
+    def set_observation(self, scene, **over):
+        p = scene.params
+        params = perch_default_params(delta_m=p.delta_m, tau_c=p.tau_c, color_check=p.color_check,
+                                      stride=p.stride, occ_margin_units=p.occ_margin_units,
+                                      z_near_m=p.z_near_m, jo_mode=p.jo_mode)
+        for k, v in over.items():
+            setattr(params, k, v)
+        return perch_set_observation(self.ctx, scene.depth, scene.rgb, scene.labels, scene.fx,
+                                     scene.fy, scene.cx, scene.cy, params)
+
+    def score(self, scene_id, mesh_id, label, roi, poses, costs=None, stream=None):
+        return perch_score_hypotheses(self.ctx, scene_id, mesh_id, label, roi, poses, costs, stream)
+
+    def best(self, costs, ids=None, **kw):
+        return perch_best(self.ctx, costs, ids, **kw)
+
+    def set_launch_config(self, threads, zbuf_words):
+        perch_set_launch_config(self.ctx, threads, zbuf_words)
+
+    def render_keys(self, scene_id, mesh_id, roi, pose, W, H):
+        return perch_debug_render_keys(self.ctx, scene_id, mesh_id, roi, pose, W, H)
+
+    @property
+    def hbm_used(self):
+        return perch_hbm_used(self.ctx)
+
+    def last_error(self):
+        return perch_last_error(self.ctx)

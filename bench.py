@@ -1,0 +1,353 @@
+"""Benchmark: hypotheses rendered+scored per second on the 3-object tabletop workload.
+
+One step = the whole hot path over one batch: the three objects' 29,584 pose
+hypotheses each (88,752 in all) are rendered, back-projected, occluder-culled,
+radius-searched and colour-checked against the 640x480 observation, and the
+per-object argmin is taken -- three perch_score_hypotheses calls and three
+perch_best calls through the C ABI.
+
+value : device-timed throughput with poses resident in HBM (CUDA events on the
+        launching stream, L2 flushed between steps by a 512 MiB write).
+e2e   : the same metric through the public API with HOST buffers: pinned poses
+        copied in and costs + argmin read back inside the timed region.
+roofline : the scoring kernel, bound by FP32 ALU issue (distance tests);
+        algorithmic work = oracle-counted 27-cell candidates x 8 FP32 ops.
+cpu_baseline : the plain C oracle on a bounded sample of the same workload.
+
+N > 1 (torchrun): every rank scores its own copy of the batch (independent
+problems, weak scaling, no data-path collective); value = all ranks' hypotheses
+/ the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hypotheses rendered+scored/s"
+UNIT = "hypotheses/s"
+FP32_OPS_PER_TEST = 8      # 3 sub, 3 mul, 2 add per squared distance
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid-half", type=int, default=21, help="positions per axis = 2*g+1")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def _workload(grid_half):
+    from paper_2008_00326_gb300 import scenes
+    sc = scenes.tabletop_3obj(grid_half=grid_half)
+    desc = (f"tabletop_3obj: 640x480 RGB-D, ellipsoid 20k + 2 same-shape cylinders 10k tris, "
+            f"{len(sc.requests)}x{len(sc.requests[0].poses)} 3-DoF hypotheses "
+            f"({2 * grid_half + 1}^2 positions x 16 yaws), colour check on, 20% occluder pixels")
+    return sc, desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[3 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sc, seconds, rng_seed=0):
+    """The oracle, as it stands, on a bounded random sample of the workload."""
+    from oracle import oracle as O
+    threads = O.num_threads()
+    rng = np.random.default_rng(rng_seed)
+    per = max(1, threads)
+    total_h, total_t, work = 0, 0.0, []
+    deadline = time.perf_counter() + seconds
+    rounds = 0
+    while True:
+        for req in sc.requests:
+            pick = rng.choice(len(req.poses), per, replace=False)
+            osc = O.OracleScene.from_scene(sc)
+            om = O.OracleMesh.from_mesh(sc.meshes[req.mesh_index])
+            t0 = time.perf_counter()
+            _, _, w = O.score(osc, om, req.poses[pick], label=req.label, roi=req.roi, with_work=True)
+            total_t += time.perf_counter() - t0
+            total_h += len(pick)
+            work.append(w)
+        rounds += 1
+        if time.perf_counter() >= deadline:
+            break
+    work = np.concatenate(work)
+    return {"value": total_h / total_t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{total_h} random hypotheses ({rounds} rounds x {per} per object) of the same "
+                      f"workload, brute-force nearest neighbours, {total_t:.1f} s"}, work
+
+
+def reference_arm(a):
+    """--impl reference: the oracle timed as the reference arm (host cores)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    sc, desc = _workload(a.grid_half)
+    threads = O.num_threads()
+    rng = np.random.default_rng(7)
+    per = max(1, threads)
+    oscs = [O.OracleScene.from_scene(sc) for _ in sc.requests]
+    oms = [O.OracleMesh.from_mesh(sc.meshes[r.mesh_index]) for r in sc.requests]
+
+    def step():
+        n = 0
+        for k, req in enumerate(sc.requests):
+            pick = rng.choice(len(req.poses), per, replace=False)
+            O.score(oscs[k], oms[k], req.poses[pick], label=req.label, roi=req.roi)
+            n += len(pick)
+        return n
+
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    n = sum(step() for _ in range(a.steps))
+    dt = time.perf_counter() - t0
+    v = n / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * dt / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": desc, "sample_per_step": f"{per} hypotheses per object"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{per} random hypotheses per object per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return reference_arm(a)
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2008_00326_gb300 import build, perch as P
+    build.build()
+    sc, desc = _workload(a.grid_half)
+    ctx = P.Context(local)
+    sid = ctx.set_observation(sc)
+    mids = [ctx.load_mesh(m) for m in sc.meshes]
+    reqs = sc.requests
+    n_step = sum(len(r.poses) for r in reqs)
+    stream = torch.cuda.Stream(dev)
+    d_poses = [torch.from_numpy(r.poses).to(dev) for r in reqs]
+    d_costs = [torch.empty((len(r.poses), 2), dtype=torch.int32, device=dev) for r in reqs]
+    d_bi = torch.empty(len(reqs), dtype=torch.int64, device=dev)
+    d_bc = torch.empty(len(reqs), dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step_device(ev_obj=None):
+        for k, r in enumerate(reqs):
+            P.perch_score_hypotheses(ctx.ctx, sid, mids[k], r.label, r.roi, d_poses[k], d_costs[k],
+                                     stream)
+            P.perch_best(ctx.ctx, d_costs[k], None, stream, d_bi[k:k + 1], d_bc[k:k + 1])
+            if ev_obj is not None:
+                ev_obj[k].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            step_device()
+    stream.synchronize()
+
+    # ---- device-timed steps (poses resident), per-object search latency
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, obj_lat = 0.0, []
+    score_ms = []
+    with torch.cuda.stream(stream):
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in reqs]
+            e0.record(stream)
+            step_device(evs)
+            stream.synchronize()
+            prev = e0
+            for ev in evs:
+                obj_lat.append(prev.elapsed_time(ev))
+                prev = ev
+            total_ms += e0.elapsed_time(evs[-1])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    # scoring-kernel-only timing (the dominant kernel), same stream
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, a.steps // 2)):
+            for k, r in enumerate(reqs):
+                flush.zero_()
+                s0 = torch.cuda.Event(enable_timing=True)
+                s1 = torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                P.perch_score_hypotheses(ctx.ctx, sid, mids[k], r.label, r.roi, d_poses[k],
+                                         d_costs[k], stream)
+                s1.record(stream)
+                stream.synchronize()
+                score_ms.append((k, s0.elapsed_time(s1)))
+    ms_step = total_ms / a.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n_step / (ms_step / 1000.0)
+
+    # ---- e2e through the public API with host buffers (pinned)
+    pinned = [torch.from_numpy(r.poses).pin_memory().numpy() for r in reqs]
+    host_costs = [torch.empty((len(r.poses), 2), dtype=torch.int32).pin_memory().numpy() for r in reqs]
+    e2e_steps = max(2, a.steps // 2)
+
+    def step_host():
+        out = []
+        for k, r in enumerate(reqs):
+            P.perch_score_hypotheses(ctx.ctx, sid, mids[k], r.label, r.roi, pinned[k], host_costs[k])
+            out.append(P.perch_best(ctx.ctx, host_costs[k]))
+        return out
+
+    step_host()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    e2e_ms = 1000.0 * (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = sum(p.nbytes for p in pinned) + sum(c.nbytes for c in host_costs)
+    d2h = sum(c.nbytes for c in host_costs) + len(reqs) * 12
+
+    if rank != 0:
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- CPU oracle baseline and the roofline's algorithmic work
+    cpu, work = (None, None)
+    if not a.no_cpu_baseline and world == 1:
+        cpu, work = cpu_baseline(sc, a.cpu_seconds)
+    roof = None
+    per_obj_ms = {}
+    for k, ms in score_ms:
+        per_obj_ms.setdefault(k, []).append(ms)
+    score_total_ms = sum(statistics.mean(v) for v in per_obj_ms.values())
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_ops = 152 * 128 * sm_max * 1e6
+    if work is not None:
+        cand_per_hyp = float(work[:, 5].mean())
+        ops = cand_per_hyp * n_step * FP32_OPS_PER_TEST
+        achieved = ops / (score_total_ms / 1000.0)
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                "kernel": "k_score (fused raster + resolve + 27-cell radius search + J_o)",
+                "work_per_hypothesis": {"cell_candidates": cand_per_hyp,
+                                        "kept_points": float(work[:, 4].mean()),
+                                        "fragments": float(work[:, 2].mean()),
+                                        "tri_setups": float(work[:, 0].mean())},
+                "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock)"}
+    lat = sorted(obj_lat)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "hypotheses_per_step": n_step, "l2": "flushed between steps (512 MiB write)",
+                   "launch": {"threads": 256, "zbuf_words": 16384}},
+        "latency_ms": {"search_p50": lat[len(lat) // 2], "search_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "what": "one object's 29,584-hypothesis search (score + argmin), device-timed"},
+        "e2e": {"value": world * n_step / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": a.steps * 2 * len(reqs),
+        "clocks": clk,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "kernel_ms_per_step": score_total_ms,
+    }
+    print(json.dumps(out))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

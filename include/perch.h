@@ -165,6 +165,30 @@ PERCH_API perch_status perch_score_hypotheses(perch_ctx *ctx, int32_t scene_id, 
 PERCH_API perch_status perch_best(perch_ctx *ctx, const int32_t *costs, const uint64_t *ids, int64_t n,
                         int64_t *best_index, int32_t *best_cost, void *cuda_stream);
 
+/* The same argmin as perch_best, for callers that cannot allocate device
+ * memory -- for example a serving process that reserves all of its HBM at
+ * start-up and may not call cudaMalloc afterwards (an allocation can
+ * synchronise the device and stall every other stream), or a host framework
+ * whose allocator owns the device memory.  Such callers cannot create a
+ * perch_ctx, so this call takes none.  The paper has no counterpart; it is an
+ * interface for these callers only.
+ *   costs (n*2 int32), ids (n uint64 or NULL), best_index (int64) and
+ *   best_cost (int32) are DEVICE pointers on the current CUDA device; the work
+ *   is enqueued on cuda_stream (NULL: the default stream) and the result is
+ *   written when the stream reaches it.
+ *   1 <= n <= 2^31-1, otherwise PERCH_E_INVALID; PERCH_E_CUDA if a CUDA call
+ *   fails.
+ * It allocates nothing.  Its scratch (the kernel's per-block partial results
+ * and completion ticket, 24.8 KB for at most 1024 blocks) is a static device
+ * array that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (for instance on
+ * two streams at once) race and must be ordered by the caller. */
+PERCH_API perch_status perch_best_noalloc(const int32_t *costs, const uint64_t *ids, int64_t n,
+                                          int64_t *best_index, int32_t *best_cost,
+                                          void *cuda_stream);
+
 /* Launch shape of the scoring kernel for this context: threads per block (128,
  * 256 or 512) and the capacity of the shared-memory z-buffer in 32-bit words
  * (1024 <= zbuf_words <= 49152; a 32-bit key per pixel when the mesh has fewer

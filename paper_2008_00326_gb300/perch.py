@@ -25,7 +25,7 @@ STATUS = {0: "PERCH_OK", -1: "PERCH_E_INVALID", -2: "PERCH_E_NOMEM", -3: "PERCH_
 EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_error",
            "perch_hbm_used", "perch_load_mesh", "perch_release_mesh", "perch_set_observation",
            "perch_release_scene", "perch_score_hypotheses", "perch_best", "perch_set_launch_config",
-           "perch_debug_render_keys")
+           "perch_debug_render_keys", "perch_best_noalloc")
 
 
 class PerchError(RuntimeError):
@@ -69,6 +69,7 @@ def load(path: str | None = None):
         "perch_best": ([P, P, P, I64, P, P, P], I32),
         "perch_set_launch_config": ([P, I32, I32], I32),
         "perch_debug_render_keys": ([P, I32, I32, P, P, P], I32),
+        "perch_best_noalloc": ([P, P, I64, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -197,6 +198,16 @@ def perch_best(ctx, costs, ids=None, stream=None, out_index=None, out_cost=None)
     handle = getattr(stream, "cuda_stream", stream)
     _check(ctx, load().perch_best(ctx, _ptr_of(costs), None if ids is None else _ptr_of(ids), n,
                                    _ptr_of(out_index), _ptr_of(out_cost), handle))
+
+
+def perch_best_noalloc(costs, ids, out_index, out_cost, stream=None):
+    """Argmin without a context or any allocation: torch CUDA tensors in and out."""
+    n = costs.numel() // 2
+    handle = getattr(stream, "cuda_stream", stream)
+    st = load().perch_best_noalloc(_ptr_of(costs), None if ids is None else _ptr_of(ids), n,
+                                   _ptr_of(out_index), _ptr_of(out_cost), handle)
+    if st != PERCH_OK:
+        raise PerchError(st, "perch_best_noalloc failed")
 
 
 def perch_set_launch_config(ctx, threads, zbuf_words):

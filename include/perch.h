@@ -190,13 +190,17 @@ PERCH_API perch_status perch_best_noalloc(const int32_t *costs, const uint64_t *
                                           void *cuda_stream);
 
 /* Launch shape of the scoring kernel for this context: threads per block (128,
- * 256 or 512) and the capacity of the shared-memory z-buffer in 32-bit words
+ * 256 or 512), the capacity of the shared-memory z-buffer in 32-bit words
  * (1024 <= zbuf_words <= 49152; a 32-bit key per pixel when the mesh has fewer
  * than 65536 triangles and the hypothesis lies within 6.5 m, else a 64-bit key
- * per pixel).  Pixel boxes larger than the z-buffer are processed in tiles.
- * Results do not depend on this choice; only speed does.  The autotuner of
+ * per pixel), and the capacity in bits of the bitset that marks nearest
+ * neighbours inside the admissible box (1024 <= mark_bits <= 2^22, 0 = the
+ * default 65536).  Pixel boxes larger than the z-buffer are processed in
+ * tiles, admissible boxes larger than the bitset in row bands.  Results do not
+ * depend on these choices; only speed and shared memory do.  The autotuner of
  * the batched form calls it.  PERCH_E_INVALID outside the ranges. */
-PERCH_API perch_status perch_set_launch_config(perch_ctx *ctx, int32_t threads, int32_t zbuf_words);
+PERCH_API perch_status perch_set_launch_config(perch_ctx *ctx, int32_t threads, int32_t zbuf_words,
+                                               int32_t mark_bits);
 
 /* Debug view of the rasteriser used by perch_score_hypotheses: the z-buffer of
  * one pose as 64-bit keys (depth << 32) | triangle id, 0xFFFFFFFFFFFFFFFF where

@@ -70,7 +70,7 @@ struct perch_ctx {
     unsigned* d_best_ticket = nullptr;
     long long* d_best_index = nullptr;
     int32_t* d_best_cost = nullptr;
-    perch::ScoreConfig cfg{256, 16384};
+    perch::ScoreConfig cfg{256, 8192, 1 << 16};
 };
 
 namespace {
@@ -174,10 +174,18 @@ perch_status clip_roi(perch_ctx* c, const SceneRec& s, const int32_t* roi, int o
     return PERCH_OK;
 }
 
-int mark_words_for(const SceneRec& s, int label, const int roi[4])
+// Capacity of the shared-memory bitset that marks nearest neighbours inside
+// the admissible box.  Boxes larger than this are processed in row bands (each
+// band repeats the render and search), so the capacity only trades shared
+// memory against that rare repetition.  At least one image row always fits.
+constexpr int kMarkBitsDefault = 1 << 16;
+
+int mark_words_for(const SceneRec& s, int label, const int roi[4], int cap_bits)
 {
     long long bits = label >= 0 ? (long long)(roi[2] - roi[0]) * (roi[3] - roi[1])
                                 : (long long)s.ds.W * s.ds.H;
+    bits = std::min<long long>(bits, cap_bits);
+    bits = std::max<long long>(bits, s.ds.W);
     return (int)(((bits + 31) / 32 + 2) & ~1ll);   // even: keeps the later 8-byte arrays aligned
 }
 
@@ -529,7 +537,7 @@ perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh
     if (st != PERCH_OK) return st;
     int r[4];
     clip_roi(c, *s, roi, r);
-    int mw = mark_words_for(*s, label, r);
+    int mw = mark_words_for(*s, label, r, c->cfg.mark_bits);
     perch::ScoreConfig cfg;
     if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
     DeviceGuard g(c->device);
@@ -601,14 +609,19 @@ perch_status perch_best(perch_ctx* c, const int32_t* costs, const uint64_t* ids,
     return PERCH_OK;
 }
 
-perch_status perch_set_launch_config(perch_ctx* c, int32_t threads, int32_t zbuf_words)
+perch_status perch_set_launch_config(perch_ctx* c, int32_t threads, int32_t zbuf_words,
+                                     int32_t mark_bits)
 {
     if (!c) return PERCH_E_INVALID;
     c->err.clear();
-    if ((threads != 128 && threads != 256 && threads != 512) || zbuf_words < 1024 || zbuf_words > 49152)
-        return fail(c, PERCH_E_INVALID, "launch config (%d threads, %d words) out of range", threads, zbuf_words);
+    if (mark_bits == 0) mark_bits = kMarkBitsDefault;
+    if ((threads != 128 && threads != 256 && threads != 512) || zbuf_words < 1024 ||
+        zbuf_words > 49152 || mark_bits < 1024 || mark_bits > (1 << 22))
+        return fail(c, PERCH_E_INVALID, "launch config (%d threads, %d words, %d bits) out of range",
+                    threads, zbuf_words, mark_bits);
     c->cfg.threads = threads;
     c->cfg.zcap_words = zbuf_words & ~1;
+    c->cfg.mark_bits = mark_bits;
     return PERCH_OK;
 }
 
@@ -624,7 +637,7 @@ perch_status perch_debug_render_keys(perch_ctx* c, int32_t scene_id, int32_t mes
     if (st != PERCH_OK) return st;
     int r[4];
     clip_roi(c, *s, roi, r);
-    int mw = mark_words_for(*s, -1, r);
+    int mw = mark_words_for(*s, -1, r, c->cfg.mark_bits);
     perch::ScoreConfig cfg;
     if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
     DeviceGuard g(c->device);

@@ -59,6 +59,7 @@ enum : int { kErrKeyRange = 1, kErrMarkCap = 2, kErrHashFull = 4 };
 struct ScoreConfig {
     int threads;              // 128, 256 or 512
     int zcap_words;           // z-buffer words (32-bit keys: pixels; 64-bit: half)
+    int mark_bits;            // admissible-box bitset capacity in bits
 };
 
 size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words);

@@ -418,13 +418,22 @@ __device__ void raster_box(const int* x, const int* y, const float* iz, int A, i
     }
 }
 
-// Warp-cooperative 27-cell radius search around q: the nearest observed point
-// with squared distance <= delta^2 (ties to the lowest pixel index), packed as
-// (d2 bits << 32) | pixel, or kEmptyKey.  All 32 lanes must call it.
-__device__ __forceinline__ unsigned long long probe_nn(const DevScene& sc, float qx, float qy,
-                                                       float qz, int2* wscr, int lane)
+// ---- resolve queue and per-warp cell groups -------------------------------
+
+constexpr int kKeptCap = 1024;    // kept rendered points buffered per round
+constexpr int kGroups = 8;        // distinct query cells looked up per warp round
+
+struct KeptPoint {                // a rendered point of R \ C waiting for its radius search
+    float x, y, z;
+    uint32_t rgb;                 // interpolated colour, r | g << 8 | b << 16
+};
+
+// Warp-cooperative lookup of the 27 cells around cell (cx,cy,cz): lane j < 27
+// probes neighbour j; the non-empty (start, count) runs are compacted into
+// runs[0..n) in neighbour order.  Returns n (same value in every lane).
+__device__ __forceinline__ int lookup_27(const DevScene& sc, int cx, int cy, int cz, int2* runs,
+                                         int lane)
 {
-    int cx = cell_coord(qx, sc.cell), cy = cell_coord(qy, sc.cell), cz = cell_coord(qz, sc.cell);
     uint32_t start = 0, cnt = 0;
     if (lane < 27) {
         int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
@@ -442,36 +451,76 @@ __device__ __forceinline__ unsigned long long probe_nn(const DevScene& sc, float
             h = (h + 1) & sc.table_mask;
         }
     }
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (lane < 27) wscr[lane] = make_int2((int)start, (int)(incl - cnt));
-    if (lane == 27) wscr[27] = make_int2(0, (int)total);
-    __syncwarp();
+    unsigned nonempty = __ballot_sync(0xffffffffu, cnt != 0);
+    if (cnt != 0) runs[__popc(nonempty & ((1u << lane) - 1u))] = make_int2((int)start, (int)cnt);
+    return __popc(nonempty);
+}
+
+// Nearest observed point within delta of q over the given runs of the cell-
+// grouped cloud: min of (d2 bits << 32 | pixel), i.e. smallest FP32 squared
+// distance, ties to the lowest pixel index; kEmptyKey if none.
+__device__ __forceinline__ unsigned long long scan_runs(const DevScene& sc, float qx, float qy,
+                                                        float qz, const int2* runs, int nruns)
+{
     unsigned long long best = kEmptyKey;
-    int r = 0;
-    for (uint32_t k = lane; k < total; k += 32) {
-        while ((uint32_t)wscr[r + 1].y <= k) ++r;
-        int2 e = wscr[r];
-        float4 p = __ldg(&sc.pts[e.x + (int)(k - (uint32_t)e.y)]);
-        float dx = __fsub_rn(qx, p.x), dy = __fsub_rn(qy, p.y), dz = __fsub_rn(qz, p.z);
-        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        if (d2 <= sc.delta2) {
-            unsigned long long key =
-                ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(p.w);
-            best = key < best ? key : best;
+    for (int r = 0; r < nruns; ++r) {
+        const int2 run = runs[r];
+        const float4* p = sc.pts + run.x;
+        for (int i = 0; i < run.y; ++i) {
+            float4 c = __ldg(p + i);
+            float dx = __fsub_rn(qx, c.x), dy = __fsub_rn(qy, c.y), dz = __fsub_rn(qz, c.z);
+            float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            if (d2 <= sc.delta2) {
+                unsigned long long key =
+                    ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
+                best = key < best ? key : best;
+            }
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-        best = other < best ? other : best;
+    return best;
+}
+
+// Radius search for up to 32 queued points (one per lane; `valid` marks the
+// lanes holding one).  Lanes whose points fall in the same hash cell form a
+// group (__match_any_sync); each group's 27-cell neighbourhood is looked up
+// once, cooperatively, then every lane scans its group's candidates for its
+// own point.  All 32 lanes must call it.
+__device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float qx, float qy,
+                                          float qz, int2* wruns, int* wnr, int lane)
+{
+    int cx = 0, cy = 0, cz = 0;
+    unsigned long long key = kEmptyKey;
+    if (valid) {
+        cx = cell_coord(qx, sc.cell);
+        cy = cell_coord(qy, sc.cell);
+        cz = cell_coord(qz, sc.cell);
+        key = cell_key(cx, cy, cz);
     }
-    __syncwarp();
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(grp) - 1;
+    const unsigned leaders = __ballot_sync(0xffffffffu, valid && lane == leader);
+    const int my_g = __popc(leaders & ((1u << leader) - 1u));
+    unsigned long long best = kEmptyKey;
+    unsigned rest = leaders;
+    for (int g0 = 0; rest != 0; g0 += kGroups) {
+        int ng = 0;
+        while (rest != 0 && ng < kGroups) {
+            const int L = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int lx = __shfl_sync(0xffffffffu, cx, L);
+            const int ly = __shfl_sync(0xffffffffu, cy, L);
+            const int lz = __shfl_sync(0xffffffffu, cz, L);
+            const int n = lookup_27(sc, lx, ly, lz, wruns + 27 * ng, lane);
+            if (lane == 0) wnr[ng] = n;
+            ++ng;
+        }
+        __syncwarp();
+        if (valid && my_g >= g0 && my_g < g0 + ng) {
+            const int gi = my_g - g0;
+            best = scan_runs(sc, qx, qy, qz, wruns + 27 * gi, wnr[gi]);
+        }
+        __syncwarp();
+    }
     return best;
 }
 
@@ -512,14 +561,29 @@ __device__ void project_box(const DevScene& sc, const float* P, const float* lo,
     if (box[3] < box[1]) box[3] = box[1];
 }
 
+// Shared-memory carve-up of one scoring block.
+struct ScoreSmem {
+    uint32_t* zbuf;               // z-buffer tile (32- or 64-bit keys)
+    uint32_t* marks;              // admissible-set band bitset
+    BigTri* big;                  // large-triangle queue
+    KeptPoint* kept;              // resolve -> radius-search queue
+    int2* runs;                   // per warp: kGroups x 27 runs
+    int* nruns;                   // per warp: kGroups counts
+    int* n_big;
+    int* n_kept;
+};
+
+// Rasterise, resolve and radius-search the pixel box rbox in z-buffer tiles.
+// J_r is accumulated when count_jr; marks are set for nearest neighbours that
+// fall in rows [mv0, mv1) of the admissible box vbox.
 template <int NT, bool K32>
-__device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox, uint32_t* zbuf,
-                            uint32_t* marks, BigTri* queue, int2* wscr_all, int* s_qn,
-                            const int* vbox, int& jr_local)
+__device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox, const ScoreSmem& S,
+                            const int* vbox, int mv0, int mv1, bool count_jr, int& jr_local)
 {
     const DevScene& sc = a.sc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int2* wscr = wscr_all + warp * 28;
+    int2* wruns = S.runs + warp * kGroups * 27;
+    int* wnr = S.nruns + warp * kGroups;
     const int s = sc.stride;
     const int rw = rbox[2] - rbox[0], rh = rbox[3] - rbox[1];
     if (rw <= 0 || rh <= 0) return;
@@ -528,13 +592,14 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
     const int th = max(1, cap_px / tw);
     const uint32_t empty32 = 0xFFFFFFFFu;
     const int vw = vbox[2] - vbox[0];
+    uint32_t* zbuf = S.zbuf;
     for (int tv0 = rbox[1]; tv0 < rbox[3]; tv0 += th) {
         for (int tu0 = rbox[0]; tu0 < rbox[2]; tu0 += tw) {
             const int tu1 = min(tu0 + tw, rbox[2]), tv1 = min(tv0 + th, rbox[3]);
             const int tpx = tw * (tv1 - tv0);
             const int words = K32 ? tpx : 2 * tpx;
             for (int i = threadIdx.x; i < words; i += NT) zbuf[i] = empty32;
-            if (threadIdx.x == 0) *s_qn = 0;
+            if (threadIdx.x == 0) *S.n_big = 0;
             __syncthreads();
             // ---- raster: one thread per triangle, large ones queued for a warp
             for (int t = threadIdx.x; t < a.m.n_tris; t += NT) {
@@ -547,9 +612,9 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
                 if (u0 > u1 || v0 > v1) continue;
                 int area = (u1 - u0 + 1) * (v1 - v0 + 1);
                 if (area > kBigArea) {
-                    int q = atomicAdd(s_qn, 1);
+                    int q = atomicAdd(S.n_big, 1);
                     if (q < kQueueCap) {
-                        BigTri& b = queue[q];
+                        BigTri& b = S.big[q];
                         for (int k = 0; k < 3; ++k) { b.x[k] = o.x[k]; b.y[k] = o.y[k]; b.iz[k] = o.iz[k]; }
                         b.A = o.A; b.tri = t; b.u0 = u0; b.v0 = v0; b.u1 = u1; b.v1 = v1;
                         continue;
@@ -558,9 +623,9 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
                 raster_box<K32>(o.x, o.y, o.iz, o.A, t, u0, v0, u1, v1, tu0, tv0, tw, zbuf, a.err);
             }
             __syncthreads();
-            const int nq = min(*s_qn, kQueueCap);
+            const int nq = min(*S.n_big, kQueueCap);
             for (int e = warp; e < nq; e += NT / 32) {
-                const BigTri& b = queue[e];
+                const BigTri& b = S.big[e];
                 const int bw = b.u1 - b.u0 + 1, area = bw * (b.v1 - b.v0 + 1);
                 const bool o0 = owns(b.x[2] - b.x[1], b.y[2] - b.y[1]);
                 const bool o1 = owns(b.x[0] - b.x[2], b.y[0] - b.y[2]);
@@ -594,87 +659,94 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
                     a.dump[(size_t)v * sc.W + u] = k;
                 }
             }
-            // ---- resolve + radius search over the stride lattice of the tile
+            // ---- resolve the stride lattice of the tile in rounds of kKeptCap
+            // pixels; kept points are compacted into the queue, then searched
             const int us0 = ((tu0 + s - 1) / s) * s, vs0 = ((tv0 + s - 1) / s) * s;
             const int nu = us0 < tu1 ? (tu1 - 1 - us0) / s + 1 : 0;
             const int nv = vs0 < tv1 ? (tv1 - 1 - vs0) / s + 1 : 0;
             const int total = nu * nv;
-            for (int base = warp * 32; base < total; base += NT) {
-                int k = base + lane;
-                bool kept = false;
-                float qx = 0.f, qy = 0.f, qz = 0.f;
-                uint32_t crgb = 0;
-                if (k < total) {
-                    int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
-                    int zi = (v - tv0) * tw + (u - tu0);
-                    unsigned d = 0;
-                    int tri = -1;
-                    if (K32) {
-                        uint32_t w = zbuf[zi];
-                        if (w != empty32) { d = w >> 16; tri = (int)(w & 0xFFFFu); }
-                    } else {
-                        unsigned long long w = reinterpret_cast<unsigned long long*>(zbuf)[zi];
-                        if (w != kEmptyKey) { d = (unsigned)(w >> 32); tri = (int)(uint32_t)w; }
-                    }
-                    if (tri >= 0) {
-                        int pix = v * sc.W + u;
-                        unsigned dobs = __ldg(&sc.depth[pix]);
-                        bool occluded = dobs > 0 && (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
-                                        (a.label < 0 || __ldg(&sc.labels[pix]) != a.label);
-                        if (!occluded) {
-                            TriSetup o;
-                            setup_triangle(sc, a.m, P, tri, o);
-                            int sx = 16 * u, sy = 16 * v;
-                            long long w0 = edge_fn(o.x[1], o.y[1], o.x[2], o.y[2], sx, sy);
-                            long long w1 = edge_fn(o.x[2], o.y[2], o.x[0], o.y[0], sx, sy);
-                            long long w2 = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], sx, sy);
-                            uint32_t c0 = __float_as_uint(__ldg(&a.m.verts[o.vid[0]].w));
-                            uint32_t c1 = __float_as_uint(__ldg(&a.m.verts[o.vid[1]].w));
-                            uint32_t c2 = __float_as_uint(__ldg(&a.m.verts[o.vid[2]].w));
-                            long long half = o.A / 2;
+            for (int base = 0; base < total; base += kKeptCap) {
+                if (threadIdx.x == 0) *S.n_kept = 0;
+                __syncthreads();
+                const int end = min(base + kKeptCap, total);
+                for (int k0 = base + warp * 32; k0 < end; k0 += NT) {
+                    const int k = k0 + lane;
+                    bool kept = false;
+                    KeptPoint kp;
+                    if (k < end) {
+                        int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
+                        int zi = (v - tv0) * tw + (u - tu0);
+                        unsigned d = 0;
+                        int tri = -1;
+                        if (K32) {
+                            uint32_t w = zbuf[zi];
+                            if (w != empty32) { d = w >> 16; tri = (int)(w & 0xFFFFu); }
+                        } else {
+                            unsigned long long w = reinterpret_cast<unsigned long long*>(zbuf)[zi];
+                            if (w != kEmptyKey) { d = (unsigned)(w >> 32); tri = (int)(uint32_t)w; }
+                        }
+                        if (tri >= 0) {
+                            int pix = v * sc.W + u;
+                            unsigned dobs = __ldg(&sc.depth[pix]);
+                            bool occluded = dobs > 0 && (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
+                                            (a.label < 0 || __ldg(&sc.labels[pix]) != a.label);
+                            if (!occluded) {
+                                TriSetup o;
+                                setup_triangle(sc, a.m, P, tri, o);
+                                int sx = 16 * u, sy = 16 * v;
+                                long long w0 = edge_fn(o.x[1], o.y[1], o.x[2], o.y[2], sx, sy);
+                                long long w1 = edge_fn(o.x[2], o.y[2], o.x[0], o.y[0], sx, sy);
+                                long long w2 = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], sx, sy);
+                                uint32_t c0 = __float_as_uint(__ldg(&a.m.verts[o.vid[0]].w));
+                                uint32_t c1 = __float_as_uint(__ldg(&a.m.verts[o.vid[1]].w));
+                                uint32_t c2 = __float_as_uint(__ldg(&a.m.verts[o.vid[2]].w));
+                                long long half = o.A / 2;
+                                uint32_t crgb = 0;
 #pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) {
-                                long long num = w0 * ((c0 >> (8 * ch)) & 255) + w1 * ((c1 >> (8 * ch)) & 255) +
-                                                w2 * ((c2 >> (8 * ch)) & 255) + half;
-                                crgb |= (uint32_t)(num / o.A) << (8 * ch);
+                                for (int ch = 0; ch < 3; ++ch) {
+                                    long long num = w0 * ((c0 >> (8 * ch)) & 255) + w1 * ((c1 >> (8 * ch)) & 255) +
+                                                    w2 * ((c2 >> (8 * ch)) & 255) + half;
+                                    crgb |= (uint32_t)(num / o.A) << (8 * ch);
+                                }
+                                float3 q = back_project(sc, u, v, d);
+                                kp.x = q.x; kp.y = q.y; kp.z = q.z; kp.rgb = crgb;
+                                kept = true;
                             }
-                            float3 q = back_project(sc, u, v, d);
-                            qx = q.x; qy = q.y; qz = q.z;
-                            kept = true;
                         }
                     }
+                    const unsigned bal = __ballot_sync(0xffffffffu, kept);
+                    int slot = 0;
+                    if (lane == 0 && bal) slot = atomicAdd(S.n_kept, __popc(bal));
+                    slot = __shfl_sync(0xffffffffu, slot, 0);
+                    if (kept) S.kept[slot + __popc(bal & ((1u << lane) - 1u))] = kp;
                 }
-                unsigned ballot = __ballot_sync(0xffffffffu, kept);
-                unsigned long long mine = kEmptyKey;
-                while (ballot) {
-                    int i = __ffs(ballot) - 1;
-                    ballot &= ballot - 1;
-                    float bx = __shfl_sync(0xffffffffu, qx, i);
-                    float by = __shfl_sync(0xffffffffu, qy, i);
-                    float bz = __shfl_sync(0xffffffffu, qz, i);
-                    unsigned long long r = probe_nn(sc, bx, by, bz, wscr, lane);
-                    if (lane == i) mine = r;
-                }
-                if (kept) {
-                    bool explained = mine != kEmptyKey;
-                    int pnn = (int)(uint32_t)mine;
+                __syncthreads();
+                const int nk = *S.n_kept;
+                for (int b0 = warp * 32; b0 < nk; b0 += NT) {
+                    const bool valid = b0 + lane < nk;
+                    KeptPoint kp = {0.f, 0.f, 0.f, 0u};
+                    if (valid) kp = S.kept[b0 + lane];
+                    const unsigned long long nn = probe_batch(sc, valid, kp.x, kp.y, kp.z, wruns, wnr, lane);
+                    if (!valid) continue;
+                    bool explained = nn != kEmptyKey;
+                    const int pnn = (int)(uint32_t)nn;
                     if (explained && sc.color_check) {
                         float4 lp = __ldg(&sc.lab[pnn]);
-                        float3 lq = srgb8_to_lab(crgb & 255, (crgb >> 8) & 255, (crgb >> 16) & 255);
+                        float3 lq = srgb8_to_lab(kp.rgb & 255, (kp.rgb >> 8) & 255, (kp.rgb >> 16) & 255);
                         if (ciede2000(lq, make_float3(lp.x, lp.y, lp.z)) > sc.tau_c) explained = false;
                     }
                     if (!explained) {
-                        ++jr_local;
+                        if (count_jr) ++jr_local;
                     } else {
                         int pu = pnn % sc.W, pv = pnn / sc.W;
-                        if (pu >= vbox[0] && pu < vbox[2] && pv >= vbox[1] && pv < vbox[3]) {
-                            int bit = (pv - vbox[1]) * vw + (pu - vbox[0]);
-                            atomicOr(&marks[bit >> 5], 1u << (bit & 31));
+                        if (pu >= vbox[0] && pu < vbox[2] && pv >= mv0 && pv < mv1) {
+                            int bit = (pv - mv0) * vw + (pu - vbox[0]);
+                            atomicOr(&S.marks[bit >> 5], 1u << (bit & 31));
                         }
                     }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
 }
@@ -684,7 +756,7 @@ __global__ void __launch_bounds__(NT) k_score(ScoreArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
-    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_qn;
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_nbig, s_nkept;
     __shared__ int s_red[3][NT / 32];
 
     const long long h = blockIdx.x;
@@ -703,59 +775,65 @@ __global__ void __launch_bounds__(NT) k_score(ScoreArgs a)
             float zv;
             project_box(sc, s_pose, lo, hi, 0, 0, sc.W, sc.H, s_vbox, &zv);
         }
-        long long bits = (long long)(s_vbox[2] - s_vbox[0]) * (s_vbox[3] - s_vbox[1]);
-        if (bits > 32ll * a.mark_words) {
-            atomicOr(a.err, kErrMarkCap);
-            s_vbox[2] = s_vbox[0];
-            s_vbox[3] = s_vbox[1];
-        }
     }
     __syncthreads();
-    uint32_t* zbuf = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* marks = zbuf + a.zcap_words;
-    BigTri* queue = reinterpret_cast<BigTri*>(marks + a.mark_words);
-    int2* wscr = reinterpret_cast<int2*>(queue + kQueueCap);
+    ScoreSmem S;
+    S.zbuf = reinterpret_cast<uint32_t*>(smem);
+    S.marks = S.zbuf + a.zcap_words;
+    S.kept = reinterpret_cast<KeptPoint*>(S.marks + a.mark_words);
+    S.runs = reinterpret_cast<int2*>(S.kept + kKeptCap);
+    S.big = reinterpret_cast<BigTri*>(S.runs + (NT / 32) * kGroups * 27);
+    S.nruns = reinterpret_cast<int*>(S.big + kQueueCap);
+    S.n_big = &s_nbig;
+    S.n_kept = &s_nkept;
 
+    // The admissible box is handled in bands of rows that fit the marks
+    // bitset; each band repeats the render + search (J_r counted once).
     const int vw = s_vbox[2] - s_vbox[0], vh = s_vbox[3] - s_vbox[1];
-    const int mwords = (vw * vh + 31) / 32;
-    for (int i = threadIdx.x; i < mwords; i += NT) marks[i] = 0u;
-    __syncthreads();
-
-    int jr = 0;
-    if (s_k32)
-        score_tiles<NT, true>(a, s_pose, s_rbox, zbuf, marks, queue, wscr, &s_qn, s_vbox, jr);
-    else
-        score_tiles<NT, false>(a, s_pose, s_rbox, zbuf, marks, queue, wscr, &s_qn, s_vbox, jr);
-
-    // ---- J_o over the admissible set V(h)
-    int n_in = 0, n_marked = 0;
+    const int band_rows = vw > 0 ? max(1, (32 * a.mark_words) / vw) : 1;
+    const int n_bands = vh > 0 ? (vh + band_rows - 1) / band_rows : 1;
+    int jr = 0, n_in = 0, n_marked = 0;
     const int s = sc.stride;
-    const int us0 = ((s_vbox[0] + s - 1) / s) * s, vs0 = ((s_vbox[1] + s - 1) / s) * s;
-    const int nu = us0 < s_vbox[2] ? (s_vbox[2] - 1 - us0) / s + 1 : 0;
-    const int nv = vs0 < s_vbox[3] ? (s_vbox[3] - 1 - vs0) / s + 1 : 0;
     const float* P = s_pose;
     const float rr = __fmul_rn(a.m.vol_r, a.m.vol_r);
-    for (int k = threadIdx.x; k < nu * nv; k += NT) {
-        int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
-        int pix = v * sc.W + u;
-        unsigned d = __ldg(&sc.depth[pix]);
-        if (d == 0) continue;
-        bool in;
-        if (a.label >= 0) {
-            in = __ldg(&sc.labels[pix]) == a.label;
-        } else {
-            float3 p = back_project(sc, u, v, d);
-            float e0 = __fsub_rn(p.x, P[3]), e1 = __fsub_rn(p.y, P[7]), e2 = __fsub_rn(p.z, P[11]);
-            float q0 = __fadd_rn(__fadd_rn(__fmul_rn(P[0], e0), __fmul_rn(P[4], e1)), __fmul_rn(P[8], e2));
-            float q1 = __fadd_rn(__fadd_rn(__fmul_rn(P[1], e0), __fmul_rn(P[5], e1)), __fmul_rn(P[9], e2));
-            float q2 = __fadd_rn(__fadd_rn(__fmul_rn(P[2], e0), __fmul_rn(P[6], e1)), __fmul_rn(P[10], e2));
-            in = __fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)) <= rr && q2 >= 0.0f && q2 <= a.m.vol_h;
+    for (int band = 0; band < n_bands; ++band) {
+        const int mv0 = s_vbox[1] + band * band_rows;
+        const int mv1 = min(mv0 + band_rows, s_vbox[3]);
+        const int mwords = (vw * max(0, mv1 - mv0) + 31) / 32;
+        for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = 0u;
+        __syncthreads();
+        if (s_k32)
+            score_tiles<NT, true>(a, P, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+        else
+            score_tiles<NT, false>(a, P, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+        __syncthreads();
+        // ---- J_o over the admissible set V(h), rows [mv0, mv1)
+        const int us0 = ((s_vbox[0] + s - 1) / s) * s, vs0 = ((mv0 + s - 1) / s) * s;
+        const int nu = us0 < s_vbox[2] ? (s_vbox[2] - 1 - us0) / s + 1 : 0;
+        const int nv = vs0 < mv1 ? (mv1 - 1 - vs0) / s + 1 : 0;
+        for (int k = threadIdx.x; k < nu * nv; k += NT) {
+            int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
+            int pix = v * sc.W + u;
+            unsigned d = __ldg(&sc.depth[pix]);
+            if (d == 0) continue;
+            bool in;
+            if (a.label >= 0) {
+                in = __ldg(&sc.labels[pix]) == a.label;
+            } else {
+                float3 p = back_project(sc, u, v, d);
+                float e0 = __fsub_rn(p.x, P[3]), e1 = __fsub_rn(p.y, P[7]), e2 = __fsub_rn(p.z, P[11]);
+                float q0 = __fadd_rn(__fadd_rn(__fmul_rn(P[0], e0), __fmul_rn(P[4], e1)), __fmul_rn(P[8], e2));
+                float q1 = __fadd_rn(__fadd_rn(__fmul_rn(P[1], e0), __fmul_rn(P[5], e1)), __fmul_rn(P[9], e2));
+                float q2 = __fadd_rn(__fadd_rn(__fmul_rn(P[2], e0), __fmul_rn(P[6], e1)), __fmul_rn(P[10], e2));
+                in = __fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)) <= rr && q2 >= 0.0f && q2 <= a.m.vol_h;
+            }
+            if (in) {
+                ++n_in;
+                int bit = (v - mv0) * vw + (u - s_vbox[0]);
+                n_marked += (S.marks[bit >> 5] >> (bit & 31)) & 1u;
+            }
         }
-        if (in) {
-            ++n_in;
-            int bit = (v - s_vbox[1]) * vw + (u - s_vbox[0]);
-            n_marked += (marks[bit >> 5] >> (bit & 31)) & 1u;
-        }
+        __syncthreads();
     }
     // ---- warp-shuffle reduction of (J_r, |I cap V|, marked)
 #pragma unroll
@@ -786,8 +864,9 @@ __global__ void __launch_bounds__(NT) k_score(ScoreArgs a)
 
 size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
 {
-    return sizeof(uint32_t) * (size_t)(cfg.zcap_words + mark_words) + sizeof(BigTri) * kQueueCap +
-           sizeof(int2) * 28 * (cfg.threads / 32);
+    return sizeof(uint32_t) * (size_t)(cfg.zcap_words + mark_words) + sizeof(KeptPoint) * kKeptCap +
+           sizeof(int2) * (cfg.threads / 32) * kGroups * 27 + sizeof(BigTri) * kQueueCap +
+           sizeof(int) * (cfg.threads / 32) * kGroups;
 }
 
 template <int NT>

@@ -67,7 +67,7 @@ def load(path: str | None = None):
         "perch_release_scene": ([P, I32], I32),
         "perch_score_hypotheses": ([P, I32, I32, I32, P, P, I64, P, P], I32),
         "perch_best": ([P, P, P, I64, P, P, P], I32),
-        "perch_set_launch_config": ([P, I32, I32], I32),
+        "perch_set_launch_config": ([P, I32, I32, I32], I32),
         "perch_debug_render_keys": ([P, I32, I32, P, P, P], I32),
         "perch_best_noalloc": ([P, P, I64, P, P, P], I32),
     }
@@ -210,8 +210,8 @@ def perch_best_noalloc(costs, ids, out_index, out_cost, stream=None):
         raise PerchError(st, "perch_best_noalloc failed")
 
 
-def perch_set_launch_config(ctx, threads, zbuf_words):
-    _check(ctx, load().perch_set_launch_config(ctx, threads, zbuf_words))
+def perch_set_launch_config(ctx, threads, zbuf_words, mark_bits=0):
+    _check(ctx, load().perch_set_launch_config(ctx, threads, zbuf_words, mark_bits))
 
 
 def perch_debug_render_keys(ctx, scene_id, mesh_id, roi, pose, W, H):
@@ -265,8 +265,8 @@ class Context:
     def best(self, costs, ids=None, **kw):
         return perch_best(self.ctx, costs, ids, **kw)
 
-    def set_launch_config(self, threads, zbuf_words):
-        perch_set_launch_config(self.ctx, threads, zbuf_words)
+    def set_launch_config(self, threads, zbuf_words, mark_bits=0):
+        perch_set_launch_config(self.ctx, threads, zbuf_words, mark_bits)
 
     def render_keys(self, scene_id, mesh_id, roi, pose, W, H):
         return perch_debug_render_keys(self.ctx, scene_id, mesh_id, roi, pose, W, H)

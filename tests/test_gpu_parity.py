@@ -72,7 +72,7 @@ def test_key_buffers_bitexact(P, ctx, oracle, zbuf_words):
                     want, _ = oracle.render_keys(osc, om, pose, req.roi)
                     assert np.array_equal(got, want), (sc.name, int(np.sum(got != want)))
     finally:
-        ctx.set_launch_config(256, 16384)
+        ctx.set_launch_config(256, 8192)
 
 
 # ---------------------------------------------------------------------------
@@ -100,12 +100,14 @@ def test_small_colour_on_band(ctx, oracle):
     assert ctx.best(got) == oracle.best(want)
 
 
-@pytest.mark.parametrize("threads,zbuf_words", [(256, 16384), (128, 1024), (512, 2048)])
-def test_three_objects_reduced(ctx, oracle, threads, zbuf_words):
-    """3 objects, colour on, occluders; launch shapes that force z-buffer tiling."""
+@pytest.mark.parametrize("threads,zbuf_words,mark_bits",
+                         [(256, 8192, 0), (128, 1024, 1024), (512, 2048, 2048), (256, 16384, 0)])
+def test_three_objects_reduced(ctx, oracle, threads, zbuf_words, mark_bits):
+    """3 objects, colour on, occluders; launch shapes that force z-buffer tiles
+    and admissible-box bands."""
     sc = scenes.tabletop_3obj(W=320, H=240, grid_half=3, n_yaw=4, tri_scale=0.25)
     sid, mids = _load(ctx, sc)
-    ctx.set_launch_config(threads, zbuf_words)
+    ctx.set_launch_config(threads, zbuf_words, mark_bits)
     try:
         for req in sc.requests:
             got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
@@ -114,17 +116,23 @@ def test_three_objects_reduced(ctx, oracle, threads, zbuf_words):
             assert_within_band(got, want, band, f"3obj mesh {req.mesh_index}")
             assert ctx.best(got) == oracle.best(want)
     finally:
-        ctx.set_launch_config(256, 16384)
+        ctx.set_launch_config(256, 8192)
 
 
-def test_sixdof_reduced_labels(ctx, oracle):
+@pytest.mark.parametrize("mark_bits", [0, 1024])
+def test_sixdof_reduced_labels(ctx, oracle, mark_bits):
     sc = scenes.sixdof_5obj(n_hyp=24, W=320, H=240, tri_scale=0.1)
     sid, mids = _load(ctx, sc)
-    for req in sc.requests:
-        got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
-        want, band = oracle.score(*_oracle(oracle, sc, req), req.poses, label=req.label, roi=req.roi)
-        assert_within_band(got, want, band, f"6dof mesh {req.mesh_index}")
-        assert ctx.best(got) == oracle.best(want)
+    ctx.set_launch_config(256, 8192, mark_bits)
+    try:
+        for req in sc.requests:
+            got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
+            want, band = oracle.score(*_oracle(oracle, sc, req), req.poses, label=req.label,
+                                      roi=req.roi)
+            assert_within_band(got, want, band, f"6dof mesh {req.mesh_index}")
+            assert ctx.best(got) == oracle.best(want)
+    finally:
+        ctx.set_launch_config(256, 8192)
 
 
 @pytest.mark.parametrize("stride", [2, 3])

@@ -424,10 +424,10 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     s.params = p;
     perch_status st = PERCH_OK;
     void *d_rgb = nullptr, *slot = nullptr, *keys = nullptr, *count = nullptr, *cursor = nullptr,
-         *start = nullptr, *nvalid = nullptr;
+         *start = nullptr, *nvalid = nullptr, *big = nullptr;
     auto cleanup_scratch = [&]() {
         dfree(c, d_rgb); dfree(c, slot); dfree(c, keys); dfree(c, count);
-        dfree(c, cursor); dfree(c, start); dfree(c, nvalid);
+        dfree(c, cursor); dfree(c, start); dfree(c, nvalid); dfree(c, big);
     };
     auto cleanup_scene = [&]() {
         dfree(c, s.depth); dfree(c, s.labels); dfree(c, s.lab); dfree(c, s.pts); dfree(c, s.table);
@@ -436,11 +436,11 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
         (labels && (st = dalloc(c, npx * sizeof(int32_t), &s.labels))) ||
         (st = dalloc(c, npx * sizeof(float4), &s.lab)) ||
         (st = dalloc(c, std::max<long long>(1, n_valid) * sizeof(float4), &s.pts)) ||
-        (st = dalloc(c, (size_t)cap * sizeof(uint4), &s.table)) ||
+        (st = dalloc(c, (size_t)cap * sizeof(uint4), &big)) ||
         (st = dalloc(c, npx * 3, &d_rgb)) || (st = dalloc(c, npx * sizeof(int32_t), &slot)) ||
         (st = dalloc(c, (size_t)cap * 8, &keys)) || (st = dalloc(c, (size_t)cap * 4, &count)) ||
         (st = dalloc(c, ((size_t)cap + n_tiles) * 4, &cursor)) ||
-        (st = dalloc(c, (size_t)cap * 4, &start)) || (st = dalloc(c, sizeof(int), &nvalid))) {
+        (st = dalloc(c, (size_t)cap * 4, &start)) || (st = dalloc(c, 2 * sizeof(int), &nvalid))) {
         cleanup_scratch();
         cleanup_scene();
         return st;
@@ -462,7 +462,7 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     d.labels = (const int32_t*)s.labels;
     d.lab = (const float4*)s.lab;
     d.pts = (const float4*)s.pts;
-    d.table = (const uint4*)s.table;
+    d.table = (const uint4*)big;
     d.table_mask = cap - 1;
     d.n_pts = (int)n_valid;
     perch::BuildBuffers b{};
@@ -474,20 +474,41 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     b.n_valid = (int*)nvalid;
     b.lab = (float4*)s.lab;
     b.pts = (float4*)s.pts;
-    b.table = (uint4*)s.table;
+    b.table = (uint4*)big;
     if (!e) e = perch::launch_build(d, b, cap, (const uint8_t*)d_rgb, c->d_err, c->stream);
-    int got = -1;
-    if (!e) e = cudaMemcpyAsync(&got, nvalid, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    int got[2] = {-1, -1};
+    if (!e) e = cudaMemcpyAsync(got, nvalid, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) {
+        cleanup_scratch();
+        cleanup_scene();
+        return cuda_fail(c, e, "perch_set_observation build");
+    }
+    if ((st = check_device_error(c)) != PERCH_OK || got[0] != n_valid) {
+        cleanup_scratch();
+        cleanup_scene();
+        return st != PERCH_OK ? st : fail(c, PERCH_E_CUDA, "observation build counted %d of %lld points", got[0], n_valid);
+    }
+    // compact the hash table to twice its occupied cells
+    uint32_t cap_small = next_pow2(std::max<long long>(64, 2ll * got[1]));
+    if ((st = dalloc(c, (size_t)cap_small * sizeof(uint4), &s.table)) != PERCH_OK) {
+        cleanup_scratch();
+        cleanup_scene();
+        return st;
+    }
+    e = perch::launch_compact_table((const uint4*)big, cap, (uint4*)s.table, cap_small, c->d_err, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     cleanup_scratch();
     if (e) {
         cleanup_scene();
-        return cuda_fail(c, e, "perch_set_observation build");
+        return cuda_fail(c, e, "perch_set_observation table");
     }
-    if ((st = check_device_error(c)) != PERCH_OK || got != n_valid) {
+    if ((st = check_device_error(c)) != PERCH_OK) {
         cleanup_scene();
-        return st != PERCH_OK ? st : fail(c, PERCH_E_CUDA, "observation build counted %d of %lld points", got, n_valid);
+        return st;
     }
+    d.table = (const uint4*)s.table;
+    d.table_mask = cap_small - 1;
     int32_t id = c->next_id++;
     c->scenes[id] = s;
     *scene_id = id;

@@ -73,7 +73,7 @@ struct BuildBuffers {
     uint32_t* count;          // table capacity
     uint32_t* cursor;         // table capacity
     uint32_t* start;          // table capacity
-    int* n_valid;             // 1
+    int* n_valid;             // 2: valid points, occupied cells
     // outputs (owned by the scene)
     float4* lab;              // H*W
     float4* pts;              // n_points capacity (H*W)
@@ -81,6 +81,8 @@ struct BuildBuffers {
 };
 cudaError_t launch_build(const DevScene& sc, const BuildBuffers& b, uint32_t table_cap,
                          const uint8_t* rgb_dev, int* err, cudaStream_t s);
+cudaError_t launch_compact_table(const uint4* big, uint32_t cap_big, uint4* small, uint32_t cap_small,
+                                 int* err, cudaStream_t s);
 
 // Argmin of J = J_o + J_r (ties to the lowest id / index).
 struct BestArgs {

@@ -239,6 +239,51 @@ __global__ void k_finish_table(const unsigned long long* keys, const uint32_t* c
     table[i] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), s, k == kEmptyKey ? 0u : count[i]);
 }
 
+// Re-insert the occupied slots of the build table into a table sized for
+// them (twice the occupied count, rounded up to a power of two), so that the
+// lookups of the radius search touch a compact, cache-friendly array.
+__global__ void k_compact_table(const uint4* big, uint32_t cap_big, uint4* small, uint32_t mask,
+                                int* err)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap_big) return;
+    uint4 e = big[i];
+    unsigned long long k = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
+    if (k == kEmptyKey) return;
+    uint32_t h = hash_slot(k, mask);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&small[h]), kEmptyKey, k);
+        if (prev == kEmptyKey) {
+            small[h].z = e.z;
+            small[h].w = e.w;
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(err, kErrHashFull);
+}
+
+cudaError_t launch_compact_table(const uint4* big, uint32_t cap_big, uint4* small, uint32_t cap_small,
+                                 int* err, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(small, 0xFF, sizeof(uint4) * cap_small, s);
+    if (e != cudaSuccess) return e;
+    k_compact_table<<<(cap_big + 255) / 256, 256, 0, s>>>(big, cap_big, small, cap_small - 1, err);
+    return cudaGetLastError();
+}
+
+__global__ void k_count_cells(const uint4* table, uint32_t n, int* n_cells)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool occ = false;
+    if (i < n) {
+        uint4 e = table[i];
+        occ = !(e.x == 0xFFFFFFFFu && e.y == 0xFFFFFFFFu);
+    }
+    unsigned b = __ballot_sync(0xffffffffu, occ);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_cells, __popc(b));
+}
+
 __global__ void k_obs_scatter(DevScene sc, const int32_t* slot_of_pixel, const uint32_t* start,
                               uint32_t* cursor, float4* pts)
 {
@@ -261,21 +306,19 @@ cudaError_t launch_build(const DevScene& sc, const BuildBuffers& b, uint32_t cap
     if ((e = cudaMemsetAsync(b.keys, 0xFF, sizeof(unsigned long long) * cap, s))) return e;
     if ((e = cudaMemsetAsync(b.count, 0, sizeof(uint32_t) * cap, s))) return e;
     if ((e = cudaMemsetAsync(b.cursor, 0, sizeof(uint32_t) * cap, s))) return e;
-    if ((e = cudaMemsetAsync(b.n_valid, 0, sizeof(int), s))) return e;
+    if ((e = cudaMemsetAsync(b.n_valid, 0, 2 * sizeof(int), s))) return e;
     int blocks = (npx + 255) / 256;
     k_obs_insert<<<blocks, 256, 0, s>>>(sc, rgb_dev, b.lab, b.slot_of_pixel, b.keys, b.count,
                                         cap - 1, b.n_valid, err);
     uint32_t n_tiles = (cap + 1023) / 1024;
-    // tile sums live after the cursor array's use: reuse `cursor` tail is unsafe, so
-    // place them in the upper part of slot storage-free scratch: the `start` array
-    // holds per-slot offsets, the tile sums go to cursor[cap - n_tiles ..] before the
-    // cursors are needed -- instead keep it simple and use a dedicated region:
+    // the tile sums of the scan live just past the cursors
     uint32_t* tile_sums = b.cursor + cap;   // BuildBuffers::cursor has cap + n_tiles words
     k_scan_tiles<<<n_tiles, 1024, 0, s>>>(b.count, b.start, tile_sums, cap);
     k_scan_sums<<<1, 1024, 0, s>>>(tile_sums, n_tiles);
     k_finish_table<<<(cap + 255) / 256, 256, 0, s>>>(b.keys, b.count, b.start, tile_sums, b.table,
                                                      cap);
     k_obs_scatter<<<blocks, 256, 0, s>>>(sc, b.slot_of_pixel, b.start, b.cursor, b.pts);
+    k_count_cells<<<(cap + 255) / 256, 256, 0, s>>>(b.table, cap, b.n_valid + 1);
     return cudaGetLastError();
 }
 
@@ -421,39 +464,57 @@ __device__ void raster_box(const int* x, const int* y, const float* iz, int A, i
 // ---- resolve queue and per-warp cell groups -------------------------------
 
 constexpr int kKeptCap = 1024;    // kept rendered points buffered per round
-constexpr int kGroups = 8;        // distinct query cells looked up per warp round
+constexpr int kGroups = 4;        // distinct query cells looked up together per warp
 
 struct KeptPoint {                // a rendered point of R \ C waiting for its radius search
     float x, y, z;
     uint32_t rgb;                 // interpolated colour, r | g << 8 | b << 16
 };
 
-// Warp-cooperative lookup of the 27 cells around cell (cx,cy,cz): lane j < 27
-// probes neighbour j; the non-empty (start, count) runs are compacted into
-// runs[0..n) in neighbour order.  Returns n (same value in every lane).
-__device__ __forceinline__ int lookup_27(const DevScene& sc, int cx, int cy, int cz, int2* runs,
-                                         int lane)
+// Warp-cooperative lookup of the 27-cell neighbourhoods of up to kGroups
+// query cells at once: lane j < 27 probes neighbour j of every cell, issuing
+// all first-slot loads before resolving any (the table lives in L2, so the
+// loads overlap).  The non-empty (start, count) runs of cell g are compacted
+// into runs[27 g ..] in neighbour order and their number into nr[g].
+__device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, const int* gy,
+                                             const int* gz, int ng, int2* runs, int* nr, int lane)
 {
-    uint32_t start = 0, cnt = 0;
-    if (lane < 27) {
-        int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-        unsigned long long key = cell_key(cx + dx, cy + dy, cz + dz);
-        uint32_t h = hash_slot(key, sc.table_mask);
-        for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
-            uint4 e = __ldg(&sc.table[h]);
-            unsigned long long k = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
-            if (k == key) {
-                start = e.z;
-                cnt = e.w;
-                break;
-            }
-            if (k == kEmptyKey) break;
-            h = (h + 1) & sc.table_mask;
+    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    unsigned long long key[kGroups];
+    uint32_t h[kGroups];
+    uint4 e[kGroups];
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        if (g < ng && lane < 27) {
+            key[g] = cell_key(gx[g] + dx, gy[g] + dy, gz[g] + dz);
+            h[g] = hash_slot(key[g], sc.table_mask);
+            e[g] = __ldg(&sc.table[h[g]]);
         }
     }
-    unsigned nonempty = __ballot_sync(0xffffffffu, cnt != 0);
-    if (cnt != 0) runs[__popc(nonempty & ((1u << lane) - 1u))] = make_int2((int)start, (int)cnt);
-    return __popc(nonempty);
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        if (g >= ng) break;
+        uint32_t start = 0, cnt = 0;
+        if (lane < 27) {
+            uint4 x = e[g];
+            uint32_t slot = h[g];
+            for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
+                unsigned long long k = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+                if (k == key[g]) {
+                    start = x.z;
+                    cnt = x.w;
+                    break;
+                }
+                if (k == kEmptyKey) break;
+                slot = (slot + 1) & sc.table_mask;
+                x = __ldg(&sc.table[slot]);
+            }
+        }
+        const unsigned nonempty = __ballot_sync(0xffffffffu, cnt != 0);
+        if (cnt != 0)
+            runs[27 * g + __popc(nonempty & ((1u << lane) - 1u))] = make_int2((int)start, (int)cnt);
+        if (lane == 0) nr[g] = __popc(nonempty);
+    }
 }
 
 // Nearest observed point within delta of q over the given runs of the cell-
@@ -503,17 +564,21 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
     unsigned long long best = kEmptyKey;
     unsigned rest = leaders;
     for (int g0 = 0; rest != 0; g0 += kGroups) {
+        int gx[kGroups], gy[kGroups], gz[kGroups];
         int ng = 0;
-        while (rest != 0 && ng < kGroups) {
-            const int L = __ffs(rest) - 1;
-            rest &= rest - 1;
-            const int lx = __shfl_sync(0xffffffffu, cx, L);
-            const int ly = __shfl_sync(0xffffffffu, cy, L);
-            const int lz = __shfl_sync(0xffffffffu, cz, L);
-            const int n = lookup_27(sc, lx, ly, lz, wruns + 27 * ng, lane);
-            if (lane == 0) wnr[ng] = n;
-            ++ng;
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) {
+            gx[g] = gy[g] = gz[g] = 0;
+            if (rest != 0) {
+                const int L = __ffs(rest) - 1;
+                rest &= rest - 1;
+                gx[g] = __shfl_sync(0xffffffffu, cx, L);
+                gy[g] = __shfl_sync(0xffffffffu, cy, L);
+                gz[g] = __shfl_sync(0xffffffffu, cz, L);
+                ng = g + 1;
+            }
         }
+        lookup_cells(sc, gx, gy, gz, ng, wruns, wnr, lane);
         __syncwarp();
         if (valid && my_g >= g0 && my_g < g0 + ng) {
             const int gi = my_g - g0;
@@ -664,7 +729,10 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
             const int us0 = ((tu0 + s - 1) / s) * s, vs0 = ((tv0 + s - 1) / s) * s;
             const int nu = us0 < tu1 ? (tu1 - 1 - us0) / s + 1 : 0;
             const int nv = vs0 < tv1 ? (tv1 - 1 - vs0) / s + 1 : 0;
-            const int total = nu * nv;
+            // lattice pixels are visited in 8 x 4 blocks, one block per warp
+            // step, so that a warp's kept points are close together in space
+            const int nbx = (nu + 7) / 8, nby = (nv + 3) / 4;
+            const int total = nbx * nby * 32;
             for (int base = 0; base < total; base += kKeptCap) {
                 if (threadIdx.x == 0) *S.n_kept = 0;
                 __syncthreads();
@@ -673,8 +741,9 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
                     const int k = k0 + lane;
                     bool kept = false;
                     KeptPoint kp;
-                    if (k < end) {
-                        int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
+                    const int blk = k >> 5, lu = (blk % nbx) * 8 + (k & 7), lv = (blk / nbx) * 4 + ((k >> 3) & 3);
+                    if (k < end && lu < nu && lv < nv) {
+                        int u = us0 + lu * s, v = vs0 + lv * s;
                         int zi = (v - tv0) * tw + (u - tu0);
                         unsigned d = 0;
                         int tri = -1;
@@ -752,7 +821,7 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_score(ScoreArgs a)
+__global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];

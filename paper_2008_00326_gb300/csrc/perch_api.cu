@@ -489,8 +489,10 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
         cleanup_scene();
         return st != PERCH_OK ? st : fail(c, PERCH_E_CUDA, "observation build counted %d of %lld points", got[0], n_valid);
     }
-    // compact the hash table to twice its occupied cells
-    uint32_t cap_small = next_pow2(std::max<long long>(64, 2ll * got[1]));
+    // compact the hash table to eight times its occupied cells: most of the
+    // 27 lookups per query are misses, and a load factor of at most 1/8 ends
+    // nearly all of them at the first slot
+    uint32_t cap_small = next_pow2(std::max<long long>(64, 8ll * got[1]));
     if ((st = dalloc(c, (size_t)cap_small * sizeof(uint4), &s.table)) != PERCH_OK) {
         cleanup_scratch();
         cleanup_scene();

@@ -70,6 +70,10 @@ struct perch_ctx {
     unsigned* d_best_ticket = nullptr;
     long long* d_best_index = nullptr;
     int32_t* d_best_cost = nullptr;
+    unsigned* d_next = nullptr;            // hypothesis counter of the persistent scorer
+    void* vcache = nullptr;                // per-block vertex caches of the scorer
+    size_t vcache_bytes = 0;
+    cudaEvent_t ev_score = nullptr;        // end of the last scoring launch
     perch::ScoreConfig cfg{256, 8192, 1 << 16};
 };
 
@@ -204,6 +208,49 @@ perch_status fit_config(perch_ctx* c, int mark_words, perch::ScoreConfig* cfg)
     return PERCH_OK;
 }
 
+// Grid of the persistent scorer and its vertex-cache slots (one per block,
+// used when the snapped coordinates fit in int16, i.e. W, H <= 1023).  The
+// cache grows on demand; growing waits for every earlier scoring launch.
+perch_status prepare_score(perch_ctx* c, const SceneRec& s, const MeshRec& m,
+                           const perch::ScoreConfig& cfg, int mark_words, int* grid,
+                           unsigned long long** vc, long long* vstride)
+{
+    *grid = perch::score_grid(cfg, mark_words);
+    if (*grid <= 0) {
+        cudaGetLastError();
+        return fail(c, PERCH_E_CUDA, "scoring kernel does not fit on the device");
+    }
+    *vc = nullptr;
+    *vstride = 0;
+    if (s.ds.W > 1023 || s.ds.H > 1023) return PERCH_OK;
+    long long stride = ((long long)m.dm.n_verts + 31) / 32 * 32;
+    size_t need = (size_t)*grid * stride * sizeof(unsigned long long);
+    if (need > c->vcache_bytes) {
+        if (c->ev_score) cudaEventSynchronize(c->ev_score);
+        cudaStreamSynchronize(c->stream);
+        dfree(c, c->vcache);
+        c->vcache = nullptr;
+        c->vcache_bytes = 0;
+        perch_status st = dalloc(c, need, &c->vcache);
+        if (st != PERCH_OK) return st;
+        c->vcache_bytes = need;
+    }
+    *vc = (unsigned long long*)c->vcache;
+    *vstride = stride;
+    return PERCH_OK;
+}
+
+// Launch the scorer on stream st after every earlier scoring launch of this
+// context (they share the counter and the vertex caches).
+cudaError_t launch_ordered(perch_ctx* c, const perch::ScoreArgs& a, const perch::ScoreConfig& cfg,
+                           int grid, cudaStream_t st)
+{
+    cudaError_t e = cudaStreamWaitEvent(st, c->ev_score, 0);
+    if (e == cudaSuccess) e = perch::launch_score(a, cfg, grid, st);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_score, st);
+    return e;
+}
+
 perch::ScoreArgs make_args(perch_ctx* c, const SceneRec& s, const MeshRec& m, int label,
                            const int roi[4], const float* poses, int32_t* costs, long long n,
                            const perch::ScoreConfig& cfg, int mark_words)
@@ -220,6 +267,7 @@ perch::ScoreArgs make_args(perch_ctx* c, const SceneRec& s, const MeshRec& m, in
     a.mark_words = mark_words;
     a.dump = nullptr;
     a.err = c->d_err;
+    a.next = c->d_next;
     return a;
 }
 
@@ -266,7 +314,12 @@ perch_status perch_create(perch_ctx** out, int32_t device, uint64_t hbm_budget_b
         c->d_best_ticket = (unsigned*)p;
         c->d_best_index = (long long*)((char*)p + 16);
         c->d_best_cost = (int32_t*)((char*)p + 32);
+        c->d_next = (unsigned*)((char*)p + 48);
     }
+    if (st == PERCH_OK && (e = cudaEventCreateWithFlags(&c->ev_score, cudaEventDisableTiming)) != cudaSuccess)
+        st = cuda_fail(c, e, "cudaEventCreate");
+    if (st == PERCH_OK && (e = cudaEventRecord(c->ev_score, c->stream)) != cudaSuccess)
+        st = cuda_fail(c, e, "cudaEventRecord");
     if (st == PERCH_OK) {
         cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
         cudaMemsetAsync(c->d_best_ticket, 0, 64, c->stream);
@@ -287,8 +340,10 @@ perch_status perch_destroy(perch_ctx* c)
     if (!c) return PERCH_OK;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->ev_score) cudaEventSynchronize(c->ev_score);
     for (auto& kv : c->allocs) cudaFree(kv.first);
     c->allocs.clear();
+    if (c->ev_score) cudaEventDestroy(c->ev_score);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return PERCH_OK;
@@ -565,9 +620,15 @@ perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh
     if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
     DeviceGuard g(c->device);
     cudaError_t e;
+    int grid;
+    unsigned long long* vc;
+    long long vstride;
+    if ((st = prepare_score(c, *s, *m, cfg, mw, &grid, &vc, &vstride)) != PERCH_OK) return st;
     if (cuda_stream) {
         perch::ScoreArgs a = make_args(c, *s, *m, label, r, poses, costs, n, cfg, mw);
-        if ((e = perch::launch_score(a, cfg, (cudaStream_t)cuda_stream)) != cudaSuccess)
+        a.vcache = vc;
+        a.vstride = vstride;
+        if ((e = launch_ordered(c, a, cfg, grid, (cudaStream_t)cuda_stream)) != cudaSuccess)
             return cuda_fail(c, e, "perch_score_hypotheses launch");
         return PERCH_OK;
     }
@@ -579,7 +640,9 @@ perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh
         long long k = std::min(chunk, n - off);
         e = cudaMemcpyAsync(d_poses, poses + 12 * off, k * 48, cudaMemcpyHostToDevice, c->stream);
         perch::ScoreArgs a = make_args(c, *s, *m, label, r, d_poses, d_costs, k, cfg, mw);
-        if (!e) e = perch::launch_score(a, cfg, c->stream);
+        a.vcache = vc;
+        a.vstride = vstride;
+        if (!e) e = launch_ordered(c, a, cfg, grid, c->stream);
         if (!e) e = cudaMemcpyAsync(costs + 2 * off, d_costs, k * 8, cudaMemcpyDeviceToHost, c->stream);
         if (!e) e = cudaStreamSynchronize(c->stream);
         if (e) return cuda_fail(c, e, "perch_score_hypotheses");
@@ -675,9 +738,18 @@ perch_status perch_debug_render_keys(perch_ctx* c, int32_t scene_id, int32_t mes
     int32_t* d_cost = (int32_t*)((char*)c->stage + 48);
     cudaError_t e = cudaMemsetAsync(dump, 0xFF, npx * 8, c->stream);
     if (!e) e = cudaMemcpyAsync(d_pose, pose, 48, cudaMemcpyHostToDevice, c->stream);
+    int grid;
+    unsigned long long* vc;
+    long long vstride;
+    if ((st = prepare_score(c, *s, *m, cfg, mw, &grid, &vc, &vstride)) != PERCH_OK) {
+        dfree(c, dump);
+        return st;
+    }
     perch::ScoreArgs a = make_args(c, *s, *m, -1, r, d_pose, d_cost, 1, cfg, mw);
     a.dump = (unsigned long long*)dump;
-    if (!e) e = perch::launch_score(a, cfg, c->stream);
+    a.vcache = vc;
+    a.vstride = vstride;
+    if (!e) e = launch_ordered(c, a, cfg, grid, c->stream);
     if (!e) e = cudaMemcpyAsync(keys, dump, npx * 8, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     dfree(c, dump);

@@ -49,6 +49,9 @@ struct ScoreArgs {
     int mark_words;           // marks bitset capacity in 32-bit words
     unsigned long long* dump; // debug: W*H 64-bit keys, or nullptr
     int* err;                 // device error word (bit flags)
+    unsigned* next;           // hypothesis counter, zeroed by the launcher
+    unsigned long long* vcache;  // per-block vertex cache slots, or nullptr
+    long long vstride;        // vertices per slot
 };
 
 // Error bits written by kernels into the context's error word.
@@ -63,7 +66,9 @@ struct ScoreConfig {
 };
 
 size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words);
-cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, cudaStream_t s);
+// Blocks of the persistent scoring kernel that fit on the device at once.
+int score_grid(const ScoreConfig& cfg, int mark_words);
+cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s);
 
 // Observation build (voxel hash over I).
 struct BuildBuffers {

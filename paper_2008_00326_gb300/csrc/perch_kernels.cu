@@ -629,21 +629,95 @@ __device__ void project_box(const DevScene& sc, const float* P, const float* lo,
 // Shared-memory carve-up of one scoring block.
 struct ScoreSmem {
     uint32_t* zbuf;               // z-buffer tile (32- or 64-bit keys)
-    uint32_t* marks;              // admissible-set band bitset
+    uint32_t* marks;              // admissible-band bitset
     BigTri* big;                  // large-triangle queue
     KeptPoint* kept;              // resolve -> radius-search queue
     int2* runs;                   // per warp: kGroups x 27 runs
     int* nruns;                   // per warp: kGroups counts
     int* n_big;
     int* n_kept;
+    int* next_batch;
 };
+
+// ---- per-hypothesis vertex cache (one slot of global scratch per block) ----
+//
+// Each vertex is transformed, projected and snapped once per hypothesis and
+// kept as (x16 : int16, y16 : int16, 1/Z : float); a vertex that fails the
+// near-plane or guard-band test is stored with x16 = -32768, which culls every
+// triangle that uses it.  Used when 32 W and 32 H fit in int16.
+constexpr int kCulledX = -32768;
+
+__device__ __forceinline__ void vertex_pass(const DevScene& sc, const DevMesh& m, const float* P,
+                                            unsigned long long* vc, int nt)
+{
+    const float gx0 = (float)(-16 * sc.W), gx1 = (float)(32 * sc.W);
+    const float gy0 = (float)(-16 * sc.H), gy1 = (float)(32 * sc.H);
+    for (int i = threadIdx.x; i < m.n_verts; i += nt) {
+        float4 v = __ldg(&m.verts[i]);
+        float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P[0], v.x), __fmul_rn(P[1], v.y)),
+                                      __fmul_rn(P[2], v.z)), P[3]);
+        float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P[4], v.x), __fmul_rn(P[5], v.y)),
+                                      __fmul_rn(P[6], v.z)), P[7]);
+        float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P[8], v.x), __fmul_rn(P[9], v.y)),
+                                      __fmul_rn(P[10], v.z)), P[11]);
+        unsigned long long rec = (unsigned long long)(uint16_t)kCulledX;
+        if (Z >= sc.z_near) {
+            float sx = __fmul_rn(__fadd_rn(__fmul_rn(sc.fx, __fdiv_rn(X, Z)), sc.cx), 16.0f);
+            float sy = __fmul_rn(__fadd_rn(__fmul_rn(sc.fy, __fdiv_rn(Y, Z)), sc.cy), 16.0f);
+            if (sx >= gx0 && sx < gx1 && sy >= gy0 && sy < gy1) {
+                uint32_t xs = (uint16_t)(int16_t)__float2int_rn(sx);
+                uint32_t ys = (uint16_t)(int16_t)__float2int_rn(sy);
+                rec = (unsigned long long)(xs | (ys << 16)) |
+                      ((unsigned long long)__float_as_uint(__fdiv_rn(1.0f, Z)) << 32);
+            }
+        }
+        vc[i] = rec;
+    }
+}
+
+__device__ __forceinline__ bool setup_cached(const DevMesh& m, const unsigned long long* vc, int t,
+                                             TriSetup& o)
+{
+    int4 tv = __ldg(&m.tris[t]);
+    int vids[3] = {tv.x, tv.y, tv.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        unsigned long long r = vc[vids[k]];
+        int xs = (int16_t)(uint16_t)(r & 0xFFFFu);
+        if (xs == kCulledX) return false;
+        o.x[k] = xs;
+        o.y[k] = (int16_t)(uint16_t)((r >> 16) & 0xFFFFu);
+        o.iz[k] = __uint_as_float((uint32_t)(r >> 32));
+        o.vid[k] = vids[k];
+    }
+    int A = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], o.x[2], o.y[2]);
+    if (A == 0) return false;
+    if (A < 0) {
+        int tx = o.x[1], ty = o.y[1], tvid = o.vid[1];
+        float ti = o.iz[1];
+        o.x[1] = o.x[2]; o.y[1] = o.y[2]; o.iz[1] = o.iz[2]; o.vid[1] = o.vid[2];
+        o.x[2] = tx; o.y[2] = ty; o.iz[2] = ti; o.vid[2] = tvid;
+        A = -A;
+    }
+    o.A = A;
+    return true;
+}
+
+template <bool VC>
+__device__ __forceinline__ bool get_triangle(const DevScene& sc, const DevMesh& m, const float* P,
+                                             const unsigned long long* vc, int t, TriSetup& o)
+{
+    if (VC) return setup_cached(m, vc, t, o);
+    return setup_triangle(sc, m, P, t, o);
+}
 
 // Rasterise, resolve and radius-search the pixel box rbox in z-buffer tiles.
 // J_r is accumulated when count_jr; marks are set for nearest neighbours that
 // fall in rows [mv0, mv1) of the admissible box vbox.
-template <int NT, bool K32>
-__device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox, const ScoreSmem& S,
-                            const int* vbox, int mv0, int mv1, bool count_jr, int& jr_local)
+template <int NT, bool K32, bool VC>
+__device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned long long* vc,
+                            const int* rbox, const ScoreSmem& S, const int* vbox, int mv0, int mv1,
+                            bool count_jr, int& jr_local)
 {
     const DevScene& sc = a.sc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -669,7 +743,7 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
             // ---- raster: one thread per triangle, large ones queued for a warp
             for (int t = threadIdx.x; t < a.m.n_tris; t += NT) {
                 TriSetup o;
-                if (!setup_triangle(sc, a.m, P, t, o)) continue;
+                if (!get_triangle<VC>(sc, a.m, P, vc, t, o)) continue;
                 int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
                 int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
                 int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
@@ -725,16 +799,16 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
                 }
             }
             // ---- resolve the stride lattice of the tile in rounds of kKeptCap
-            // pixels; kept points are compacted into the queue, then searched
+            // pixels; kept points are compacted into the queue, then searched.
+            // Lattice pixels are visited in 8 x 4 blocks, one block per warp
+            // step, so that a warp's kept points are close together in space.
             const int us0 = ((tu0 + s - 1) / s) * s, vs0 = ((tv0 + s - 1) / s) * s;
             const int nu = us0 < tu1 ? (tu1 - 1 - us0) / s + 1 : 0;
             const int nv = vs0 < tv1 ? (tv1 - 1 - vs0) / s + 1 : 0;
-            // lattice pixels are visited in 8 x 4 blocks, one block per warp
-            // step, so that a warp's kept points are close together in space
             const int nbx = (nu + 7) / 8, nby = (nv + 3) / 4;
             const int total = nbx * nby * 32;
             for (int base = 0; base < total; base += kKeptCap) {
-                if (threadIdx.x == 0) *S.n_kept = 0;
+                if (threadIdx.x == 0) { *S.n_kept = 0; *S.next_batch = 0; }
                 __syncthreads();
                 const int end = min(base + kKeptCap, total);
                 for (int k0 = base + warp * 32; k0 < end; k0 += NT) {
@@ -761,7 +835,7 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
                                             (a.label < 0 || __ldg(&sc.labels[pix]) != a.label);
                             if (!occluded) {
                                 TriSetup o;
-                                setup_triangle(sc, a.m, P, tri, o);
+                                get_triangle<VC>(sc, a.m, P, vc, tri, o);
                                 int sx = 16 * u, sy = 16 * v;
                                 long long w0 = edge_fn(o.x[1], o.y[1], o.x[2], o.y[2], sx, sy);
                                 long long w1 = edge_fn(o.x[2], o.y[2], o.x[0], o.y[0], sx, sy);
@@ -790,8 +864,13 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
                     if (kept) S.kept[slot + __popc(bal & ((1u << lane) - 1u))] = kp;
                 }
                 __syncthreads();
+                // warps take batches of 32 queued points as they become free
                 const int nk = *S.n_kept;
-                for (int b0 = warp * 32; b0 < nk; b0 += NT) {
+                for (;;) {
+                    int b0 = 0;
+                    if (lane == 0) b0 = atomicAdd(S.next_batch, 32);
+                    b0 = __shfl_sync(0xffffffffu, b0, 0);
+                    if (b0 >= nk) break;
                     const bool valid = b0 + lane < nk;
                     KeptPoint kp = {0.f, 0.f, 0.f, 0u};
                     if (valid) kp = S.kept[b0 + lane];
@@ -820,23 +899,19 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const int* rbox,
     }
 }
 
+// Score hypothesis h (one block).  Writes costs[2h] = J_o, costs[2h+1] = J_r.
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
+__device__ void score_one(const ScoreArgs& a, long long h, const ScoreSmem& S, float* s_pose,
+                          int* s_rbox, int* s_vbox, int* s_k32, int (*s_red)[NT / 32],
+                          unsigned long long* vc)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float s_pose[12];
-    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_nbig, s_nkept;
-    __shared__ int s_red[3][NT / 32];
-
-    const long long h = blockIdx.x;
-    if (h >= a.n) return;
+    const DevScene& sc = a.sc;
     if (threadIdx.x < 12) s_pose[threadIdx.x] = a.poses[h * 12 + threadIdx.x];
     __syncthreads();
-    const DevScene& sc = a.sc;
     if (threadIdx.x == 0) {
         float zmax;
         project_box(sc, s_pose, a.m.lo, a.m.hi, a.roi[0], a.roi[1], a.roi[2], a.roi[3], s_rbox, &zmax);
-        s_k32 = (a.m.n_tris <= 65535 && zmax < 6.5f) ? 1 : 0;
+        *s_k32 = (a.m.n_tris <= 65535 && zmax < 6.5f) ? 1 : 0;
         if (a.label >= 0) {
             s_vbox[0] = a.roi[0]; s_vbox[1] = a.roi[1]; s_vbox[2] = a.roi[2]; s_vbox[3] = a.roi[3];
         } else {
@@ -845,16 +920,9 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
             project_box(sc, s_pose, lo, hi, 0, 0, sc.W, sc.H, s_vbox, &zv);
         }
     }
+    const bool use_vc = vc != nullptr;
+    if (use_vc) vertex_pass(sc, a.m, s_pose, vc, NT);
     __syncthreads();
-    ScoreSmem S;
-    S.zbuf = reinterpret_cast<uint32_t*>(smem);
-    S.marks = S.zbuf + a.zcap_words;
-    S.kept = reinterpret_cast<KeptPoint*>(S.marks + a.mark_words);
-    S.runs = reinterpret_cast<int2*>(S.kept + kKeptCap);
-    S.big = reinterpret_cast<BigTri*>(S.runs + (NT / 32) * kGroups * 27);
-    S.nruns = reinterpret_cast<int*>(S.big + kQueueCap);
-    S.n_big = &s_nbig;
-    S.n_kept = &s_nkept;
 
     // The admissible box is handled in bands of rows that fit the marks
     // bitset; each band repeats the render + search (J_r counted once).
@@ -871,10 +939,13 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
         const int mwords = (vw * max(0, mv1 - mv0) + 31) / 32;
         for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = 0u;
         __syncthreads();
-        if (s_k32)
-            score_tiles<NT, true>(a, P, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-        else
-            score_tiles<NT, false>(a, P, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+        if (*s_k32) {
+            if (use_vc) score_tiles<NT, true, true>(a, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, true, false>(a, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+        } else {
+            if (use_vc) score_tiles<NT, false, true>(a, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, false, false>(a, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+        }
         __syncthreads();
         // ---- J_o over the admissible set V(h), rows [mv0, mv1)
         const int us0 = ((s_vbox[0] + s - 1) / s) * s, vs0 = ((mv0 + s - 1) / s) * s;
@@ -929,6 +1000,37 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
             a.costs[2 * h + 1] = x;
         }
     }
+    __syncthreads();
+}
+
+// Persistent scoring kernel: each block repeatedly takes the next hypothesis
+// index from a device counter (zero at launch) and scores it.
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float s_pose[12];
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_nbig, s_nkept, s_next, s_h;
+    __shared__ int s_red[3][NT / 32];
+
+    ScoreSmem S;
+    S.zbuf = reinterpret_cast<uint32_t*>(smem);
+    S.marks = S.zbuf + a.zcap_words;
+    S.kept = reinterpret_cast<KeptPoint*>(S.marks + a.mark_words);
+    S.runs = reinterpret_cast<int2*>(S.kept + kKeptCap);
+    S.big = reinterpret_cast<BigTri*>(S.runs + (NT / 32) * kGroups * 27);
+    S.nruns = reinterpret_cast<int*>(S.big + kQueueCap);
+    S.n_big = &s_nbig;
+    S.n_kept = &s_nkept;
+    S.next_batch = &s_next;
+    unsigned long long* vc = a.vcache ? a.vcache + (size_t)blockIdx.x * a.vstride : nullptr;
+    for (;;) {
+        if (threadIdx.x == 0) s_h = (int)atomicAdd(a.next, 1u);
+        __syncthreads();
+        const long long h = s_h;
+        if (h >= a.n) break;
+        score_one<NT>(a, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+    }
 }
 
 size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
@@ -939,32 +1041,58 @@ size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
 }
 
 template <int NT>
-static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, cudaStream_t s)
+static int score_grid_nt(size_t smem)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT>, NT, smem) != cudaSuccess)
+        return -1;
+    return max(1, per) * max(1, sms);
+}
+
+int score_grid(const ScoreConfig& cfg, int mark_words)
+{
+    size_t smem = score_smem_bytes(cfg, mark_words);
+    switch (cfg.threads) {
+    case 128: return score_grid_nt<128>(smem);
+    case 512: return score_grid_nt<512>(smem);
+    default: return score_grid_nt<256>(smem);
+    }
+}
+
+template <int NT>
+static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s)
 {
     size_t smem = score_smem_bytes(cfg, a.mark_words);
     cudaError_t e = cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const long long kMaxGrid = 0x7FFFFFFFll;
+    const long long kMaxPerLaunch = 0x7FFFFFFFll;
     ScoreArgs b = a;
-    for (long long off = 0; off < a.n; off += kMaxGrid) {
-        long long cnt = a.n - off < kMaxGrid ? a.n - off : kMaxGrid;
+    for (long long off = 0; off < a.n; off += kMaxPerLaunch) {
+        long long cnt = a.n - off < kMaxPerLaunch ? a.n - off : kMaxPerLaunch;
         b.poses = a.poses + 12 * off;
         b.costs = a.costs + 2 * off;
         b.n = cnt;
-        k_score<NT><<<(unsigned)cnt, NT, smem, s>>>(b);
+        if ((e = cudaMemsetAsync(a.next, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+        int g = (int)(cnt < grid ? cnt : grid);
+        k_score<NT><<<g, NT, smem, s>>>(b);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, cudaStream_t s)
+cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
     switch (cfg.threads) {
-    case 128: return launch_score_nt<128>(a, cfg, s);
-    case 512: return launch_score_nt<512>(a, cfg, s);
-    default: return launch_score_nt<256>(a, cfg, s);
+    case 128: return launch_score_nt<128>(a, cfg, grid, s);
+    case 512: return launch_score_nt<512>(a, cfg, grid, s);
+    default: return launch_score_nt<256>(a, cfg, grid, s);
     }
 }
 

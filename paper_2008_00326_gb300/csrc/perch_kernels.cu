@@ -471,13 +471,24 @@ struct KeptPoint {                // a rendered point of R \ C waiting for its r
     uint32_t rgb;                 // interpolated colour, r | g << 8 | b << 16
 };
 
+// Per-warp scratch of the radius search (shared memory).
+struct WarpProbe {
+    int2 runs[kGroups][27];       // per group: non-empty runs as (start - first pair index, end pair index)
+    int total[kGroups];           // per group: candidates in its 27 cells
+    unsigned mask[kGroups];       // per group: lanes whose query lies in the group's cell
+    unsigned char qlist[kGroups][32];  // per group: the lanes of its queries, in lane order
+    float4 q[32];                 // query of each lane
+    unsigned long long best[32];  // nearest-neighbour key of each lane's query
+};
+
 // Warp-cooperative lookup of the 27-cell neighbourhoods of up to kGroups
 // query cells at once: lane j < 27 probes neighbour j of every cell, issuing
 // all first-slot loads before resolving any (the table lives in L2, so the
-// loads overlap).  The non-empty (start, count) runs of cell g are compacted
-// into runs[27 g ..] in neighbour order and their number into nr[g].
+// loads overlap).  Group g's non-empty runs are stored in neighbour order with
+// a running candidate count so that candidate i of the group is point
+// runs[r].x + i for the first run r with i < runs[r].y.
 __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, const int* gy,
-                                             const int* gz, int ng, int2* runs, int* nr, int lane)
+                                             const int* gz, int ng, WarpProbe& W, int lane)
 {
     const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
     unsigned long long key[kGroups];
@@ -510,44 +521,32 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
                 x = __ldg(&sc.table[slot]);
             }
         }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
         const unsigned nonempty = __ballot_sync(0xffffffffu, cnt != 0);
         if (cnt != 0)
-            runs[27 * g + __popc(nonempty & ((1u << lane) - 1u))] = make_int2((int)start, (int)cnt);
-        if (lane == 0) nr[g] = __popc(nonempty);
+            W.runs[g][__popc(nonempty & ((1u << lane) - 1u))] =
+                make_int2((int)start - (int)(incl - cnt), (int)incl);
+        if (lane == 26) W.total[g] = (int)incl;
     }
-}
-
-// Nearest observed point within delta of q over the given runs of the cell-
-// grouped cloud: min of (d2 bits << 32 | pixel), i.e. smallest FP32 squared
-// distance, ties to the lowest pixel index; kEmptyKey if none.
-__device__ __forceinline__ unsigned long long scan_runs(const DevScene& sc, float qx, float qy,
-                                                        float qz, const int2* runs, int nruns)
-{
-    unsigned long long best = kEmptyKey;
-    for (int r = 0; r < nruns; ++r) {
-        const int2 run = runs[r];
-        const float4* p = sc.pts + run.x;
-        for (int i = 0; i < run.y; ++i) {
-            float4 c = __ldg(p + i);
-            float dx = __fsub_rn(qx, c.x), dy = __fsub_rn(qy, c.y), dz = __fsub_rn(qz, c.z);
-            float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            if (d2 <= sc.delta2) {
-                unsigned long long key =
-                    ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
-                best = key < best ? key : best;
-            }
-        }
-    }
-    return best;
 }
 
 // Radius search for up to 32 queued points (one per lane; `valid` marks the
 // lanes holding one).  Lanes whose points fall in the same hash cell form a
 // group (__match_any_sync); each group's 27-cell neighbourhood is looked up
-// once, cooperatively, then every lane scans its group's candidates for its
-// own point.  All 32 lanes must call it.
+// once, cooperatively.  The group's (query, candidate) pairs are then spread
+// evenly over the 32 lanes -- consecutive lanes take consecutive queries of
+// the same candidate -- and each pair within delta folds (d2 bits, pixel)
+// into its query's minimum with a shared-memory atomicMin.  Returns the
+// lane's own result: the nearest observed point within delta (smallest FP32
+// squared distance, ties to the lowest pixel index) or kEmptyKey.  All 32
+// lanes must call it.
 __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float qx, float qy,
-                                          float qz, int2* wruns, int* wnr, int lane)
+                                          float qz, WarpProbe& W, int lane)
 {
     int cx = 0, cy = 0, cz = 0;
     unsigned long long key = kEmptyKey;
@@ -557,11 +556,13 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
         cz = cell_coord(qz, sc.cell);
         key = cell_key(cx, cy, cz);
     }
+    W.q[lane] = make_float4(qx, qy, qz, 0.0f);
+    W.best[lane] = kEmptyKey;
     const unsigned grp = __match_any_sync(0xffffffffu, key);
     const int leader = __ffs(grp) - 1;
     const unsigned leaders = __ballot_sync(0xffffffffu, valid && lane == leader);
     const int my_g = __popc(leaders & ((1u << leader) - 1u));
-    unsigned long long best = kEmptyKey;
+    const int my_pos = __popc(grp & ((1u << lane) - 1u));
     unsigned rest = leaders;
     for (int g0 = 0; rest != 0; g0 += kGroups) {
         int gx[kGroups], gy[kGroups], gz[kGroups];
@@ -575,18 +576,38 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
                 gx[g] = __shfl_sync(0xffffffffu, cx, L);
                 gy[g] = __shfl_sync(0xffffffffu, cy, L);
                 gz[g] = __shfl_sync(0xffffffffu, cz, L);
+                const unsigned m = __shfl_sync(0xffffffffu, grp, L);
+                if (lane == 0) W.mask[g] = m;
                 ng = g + 1;
             }
         }
-        lookup_cells(sc, gx, gy, gz, ng, wruns, wnr, lane);
+        if (valid && my_g >= g0 && my_g < g0 + kGroups) W.qlist[my_g - g0][my_pos] = (unsigned char)lane;
+        lookup_cells(sc, gx, gy, gz, ng, W, lane);
         __syncwarp();
-        if (valid && my_g >= g0 && my_g < g0 + ng) {
-            const int gi = my_g - g0;
-            best = scan_runs(sc, qx, qy, qz, wruns + 27 * gi, wnr[gi]);
+        for (int g = 0; g < ng; ++g) {
+            const int T = W.total[g];
+            if (T == 0) continue;
+            const int G = __popc(W.mask[g]);
+            const int P = G * T;
+            const int dq = 32 % G, dc = 32 / G;
+            int qi = lane % G, ci = lane / G, r = 0;
+            for (int p = lane; p < P; p += 32) {
+                while (W.runs[g][r].y <= ci) ++r;
+                const float4 c = __ldg(&sc.pts[W.runs[g][r].x + ci]);
+                const int ql = W.qlist[g][qi];
+                const float4 q = W.q[ql];
+                float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
+                float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+                if (d2 <= sc.delta2)
+                    atomicMin(&W.best[ql], ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w));
+                qi += dq;
+                ci += dc;
+                if (qi >= G) { qi -= G; ++ci; }
+            }
         }
         __syncwarp();
     }
-    return best;
+    return W.best[lane];
 }
 
 // Conservative pixel box of an object-frame box [lo,hi] at pose P (2 px
@@ -632,8 +653,7 @@ struct ScoreSmem {
     uint32_t* marks;              // admissible-band bitset
     BigTri* big;                  // large-triangle queue
     KeptPoint* kept;              // resolve -> radius-search queue
-    int2* runs;                   // per warp: kGroups x 27 runs
-    int* nruns;                   // per warp: kGroups counts
+    WarpProbe* probe;             // per warp scratch of the radius search
     int* n_big;
     int* n_kept;
     int* next_batch;
@@ -721,8 +741,7 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
 {
     const DevScene& sc = a.sc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int2* wruns = S.runs + warp * kGroups * 27;
-    int* wnr = S.nruns + warp * kGroups;
+    WarpProbe& WP = S.probe[warp];
     const int s = sc.stride;
     const int rw = rbox[2] - rbox[0], rh = rbox[3] - rbox[1];
     if (rw <= 0 || rh <= 0) return;
@@ -874,7 +893,7 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
                     const bool valid = b0 + lane < nk;
                     KeptPoint kp = {0.f, 0.f, 0.f, 0u};
                     if (valid) kp = S.kept[b0 + lane];
-                    const unsigned long long nn = probe_batch(sc, valid, kp.x, kp.y, kp.z, wruns, wnr, lane);
+                    const unsigned long long nn = probe_batch(sc, valid, kp.x, kp.y, kp.z, WP, lane);
                     if (!valid) continue;
                     bool explained = nn != kEmptyKey;
                     const int pnn = (int)(uint32_t)nn;
@@ -1017,9 +1036,8 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.zbuf = reinterpret_cast<uint32_t*>(smem);
     S.marks = S.zbuf + a.zcap_words;
     S.kept = reinterpret_cast<KeptPoint*>(S.marks + a.mark_words);
-    S.runs = reinterpret_cast<int2*>(S.kept + kKeptCap);
-    S.big = reinterpret_cast<BigTri*>(S.runs + (NT / 32) * kGroups * 27);
-    S.nruns = reinterpret_cast<int*>(S.big + kQueueCap);
+    S.probe = reinterpret_cast<WarpProbe*>(S.kept + kKeptCap);
+    S.big = reinterpret_cast<BigTri*>(S.probe + NT / 32);
     S.n_big = &s_nbig;
     S.n_kept = &s_nkept;
     S.next_batch = &s_next;
@@ -1036,8 +1054,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
 size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
 {
     return sizeof(uint32_t) * (size_t)(cfg.zcap_words + mark_words) + sizeof(KeptPoint) * kKeptCap +
-           sizeof(int2) * (cfg.threads / 32) * kGroups * 27 + sizeof(BigTri) * kQueueCap +
-           sizeof(int) * (cfg.threads / 32) * kGroups;
+           sizeof(WarpProbe) * (cfg.threads / 32) + sizeof(BigTri) * kQueueCap;
 }
 
 template <int NT>

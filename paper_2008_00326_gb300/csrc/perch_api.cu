@@ -706,7 +706,7 @@ perch_status perch_set_launch_config(perch_ctx* c, int32_t threads, int32_t zbuf
         return fail(c, PERCH_E_INVALID, "launch config (%d threads, %d words, %d bits) out of range",
                     threads, zbuf_words, mark_bits);
     c->cfg.threads = threads;
-    c->cfg.zcap_words = zbuf_words & ~1;
+    c->cfg.zcap_words = zbuf_words & ~3;
     c->cfg.mark_bits = mark_bits;
     return PERCH_OK;
 }

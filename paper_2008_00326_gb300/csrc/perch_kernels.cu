@@ -466,13 +466,13 @@ __device__ void raster_box(const int* x, const int* y, const float* iz, int A, i
 constexpr int kKeptCap = 1024;    // kept rendered points buffered per round
 constexpr int kGroups = 4;        // distinct query cells looked up together per warp
 
-struct KeptPoint {                // a rendered point of R \ C waiting for its radius search
+struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
     float x, y, z;
     uint32_t rgb;                 // interpolated colour, r | g << 8 | b << 16
 };
 
 // Per-warp scratch of the radius search (shared memory).
-struct WarpProbe {
+struct __align__(16) WarpProbe {
     int2 runs[kGroups][27];       // per group: non-empty runs as (start - first pair index, end pair index)
     int total[kGroups];           // per group: candidates in its 27 cells
     unsigned mask[kGroups];       // per group: lanes whose query lies in the group's cell
@@ -480,6 +480,9 @@ struct WarpProbe {
     float4 q[32];                 // query of each lane
     unsigned long long best[32];  // nearest-neighbour key of each lane's query
 };
+
+static_assert(sizeof(KeptPoint) == 16, "kept-point queue entries are 16 bytes");
+static_assert(sizeof(WarpProbe) % 16 == 0, "per-warp scratch keeps 16-byte alignment");
 
 // Warp-cooperative lookup of the 27-cell neighbourhoods of up to kGroups
 // query cells at once: lane j < 27 probes neighbour j of every cell, issuing
@@ -1022,6 +1025,26 @@ __device__ void score_one(const ScoreArgs& a, long long h, const ScoreSmem& S, f
     __syncthreads();
 }
 
+// Byte offsets of the dynamic shared-memory regions of a scoring block; every
+// region starts on a 16-byte boundary (the queues and the per-warp scratch
+// hold float4 and 64-bit fields).
+struct SmemLayout {
+    size_t marks, kept, probe, big, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline SmemLayout smem_layout(int zcap_words, int mark_words, int threads)
+{
+    SmemLayout L;
+    L.marks = align16(sizeof(uint32_t) * (size_t)zcap_words);
+    L.kept = align16(L.marks + sizeof(uint32_t) * (size_t)mark_words);
+    L.probe = align16(L.kept + sizeof(KeptPoint) * kKeptCap);
+    L.big = align16(L.probe + sizeof(WarpProbe) * (size_t)(threads / 32));
+    L.total = align16(L.big + sizeof(BigTri) * kQueueCap);
+    return L;
+}
+
 // Persistent scoring kernel: each block repeatedly takes the next hypothesis
 // index from a device counter (zero at launch) and scores it.
 template <int NT>
@@ -1032,12 +1055,13 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     __shared__ int s_rbox[4], s_vbox[4], s_k32, s_nbig, s_nkept, s_next, s_h;
     __shared__ int s_red[3][NT / 32];
 
+    SmemLayout L = smem_layout(a.zcap_words, a.mark_words, NT);
     ScoreSmem S;
     S.zbuf = reinterpret_cast<uint32_t*>(smem);
-    S.marks = S.zbuf + a.zcap_words;
-    S.kept = reinterpret_cast<KeptPoint*>(S.marks + a.mark_words);
-    S.probe = reinterpret_cast<WarpProbe*>(S.kept + kKeptCap);
-    S.big = reinterpret_cast<BigTri*>(S.probe + NT / 32);
+    S.marks = reinterpret_cast<uint32_t*>(smem + L.marks);
+    S.kept = reinterpret_cast<KeptPoint*>(smem + L.kept);
+    S.probe = reinterpret_cast<WarpProbe*>(smem + L.probe);
+    S.big = reinterpret_cast<BigTri*>(smem + L.big);
     S.n_big = &s_nbig;
     S.n_kept = &s_nkept;
     S.next_batch = &s_next;
@@ -1053,8 +1077,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
 
 size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
 {
-    return sizeof(uint32_t) * (size_t)(cfg.zcap_words + mark_words) + sizeof(KeptPoint) * kKeptCap +
-           sizeof(WarpProbe) * (cfg.threads / 32) + sizeof(BigTri) * kQueueCap;
+    return smem_layout(cfg.zcap_words, mark_words, cfg.threads).total;
 }
 
 template <int NT>

@@ -463,7 +463,7 @@ __device__ void raster_box(const int* x, const int* y, const float* iz, int A, i
 
 // ---- resolve queue and per-warp cell groups -------------------------------
 
-constexpr int kKeptCap = 1024;    // kept rendered points buffered per round
+constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
 constexpr int kGroups = 4;        // distinct query cells looked up together per warp
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
@@ -655,7 +655,7 @@ struct ScoreSmem {
     uint32_t* zbuf;               // z-buffer tile (32- or 64-bit keys)
     uint32_t* marks;              // admissible-band bitset
     BigTri* big;                  // large-triangle queue
-    KeptPoint* kept;              // resolve -> radius-search queue
+    KeptPoint* kept;              // per warp: resolve -> radius-search ring queue
     WarpProbe* probe;             // per warp scratch of the radius search
     int* n_big;
     int* n_kept;
@@ -760,7 +760,7 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
             const int tpx = tw * (tv1 - tv0);
             const int words = K32 ? tpx : 2 * tpx;
             for (int i = threadIdx.x; i < words; i += NT) zbuf[i] = empty32;
-            if (threadIdx.x == 0) *S.n_big = 0;
+            if (threadIdx.x == 0) { *S.n_big = 0; *S.next_batch = 0; }
             __syncthreads();
             // ---- raster: one thread per triangle, large ones queued for a warp
             for (int t = threadIdx.x; t < a.m.n_tris; t += NT) {
@@ -820,25 +820,28 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
                     a.dump[(size_t)v * sc.W + u] = k;
                 }
             }
-            // ---- resolve the stride lattice of the tile in rounds of kKeptCap
-            // pixels; kept points are compacted into the queue, then searched.
-            // Lattice pixels are visited in 8 x 4 blocks, one block per warp
-            // step, so that a warp's kept points are close together in space.
+            // ---- resolve + radius search.  The stride lattice of the tile is
+            // cut into 8 x 4 pixel blocks that warps take from a counter; a
+            // warp resolves a block (occluder test, colour, back-projection)
+            // and appends its kept points to its own queue, which it searches
+            // 32 at a time -- no block-wide barrier until the tile is done.
             const int us0 = ((tu0 + s - 1) / s) * s, vs0 = ((tv0 + s - 1) / s) * s;
             const int nu = us0 < tu1 ? (tu1 - 1 - us0) / s + 1 : 0;
             const int nv = vs0 < tv1 ? (tv1 - 1 - vs0) / s + 1 : 0;
             const int nbx = (nu + 7) / 8, nby = (nv + 3) / 4;
-            const int total = nbx * nby * 32;
-            for (int base = 0; base < total; base += kKeptCap) {
-                if (threadIdx.x == 0) { *S.n_kept = 0; *S.next_batch = 0; }
-                __syncthreads();
-                const int end = min(base + kKeptCap, total);
-                for (int k0 = base + warp * 32; k0 < end; k0 += NT) {
-                    const int k = k0 + lane;
+            const int nblocks = nbx * nby;
+            KeptPoint* wq = S.kept + warp * kWarpQueue;
+            int wq_head = 0, wq_count = 0;
+            for (;;) {
+                int blk = 0;
+                if (lane == 0) blk = atomicAdd(S.next_batch, 1);
+                blk = __shfl_sync(0xffffffffu, blk, 0);
+                const bool more = blk < nblocks;
+                if (more) {
                     bool kept = false;
                     KeptPoint kp;
-                    const int blk = k >> 5, lu = (blk % nbx) * 8 + (k & 7), lv = (blk / nbx) * 4 + ((k >> 3) & 3);
-                    if (k < end && lu < nu && lv < nv) {
+                    const int lu = (blk % nbx) * 8 + (lane & 7), lv = (blk / nbx) * 4 + (lane >> 3);
+                    if (lu < nu && lv < nv) {
                         int u = us0 + lu * s, v = vs0 + lv * s;
                         int zi = (v - tv0) * tw + (u - tu0);
                         unsigned d = 0;
@@ -880,43 +883,43 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, kept);
-                    int slot = 0;
-                    if (lane == 0 && bal) slot = atomicAdd(S.n_kept, __popc(bal));
-                    slot = __shfl_sync(0xffffffffu, slot, 0);
-                    if (kept) S.kept[slot + __popc(bal & ((1u << lane) - 1u))] = kp;
+                    if (kept) wq[(wq_head + wq_count + __popc(bal & ((1u << lane) - 1u))) % kWarpQueue] = kp;
+                    wq_count += __popc(bal);
                 }
-                __syncthreads();
-                // warps take batches of 32 queued points as they become free
-                const int nk = *S.n_kept;
-                for (;;) {
-                    int b0 = 0;
-                    if (lane == 0) b0 = atomicAdd(S.next_batch, 32);
-                    b0 = __shfl_sync(0xffffffffu, b0, 0);
-                    if (b0 >= nk) break;
-                    const bool valid = b0 + lane < nk;
-                    KeptPoint kp = {0.f, 0.f, 0.f, 0u};
-                    if (valid) kp = S.kept[b0 + lane];
-                    const unsigned long long nn = probe_batch(sc, valid, kp.x, kp.y, kp.z, WP, lane);
-                    if (!valid) continue;
-                    bool explained = nn != kEmptyKey;
-                    const int pnn = (int)(uint32_t)nn;
-                    if (explained && sc.color_check) {
-                        float4 lp = __ldg(&sc.lab[pnn]);
-                        float3 lq = srgb8_to_lab(kp.rgb & 255, (kp.rgb >> 8) & 255, (kp.rgb >> 16) & 255);
-                        if (ciede2000(lq, make_float3(lp.x, lp.y, lp.z)) > sc.tau_c) explained = false;
-                    }
-                    if (!explained) {
-                        if (count_jr) ++jr_local;
-                    } else {
-                        int pu = pnn % sc.W, pv = pnn / sc.W;
-                        if (pu >= vbox[0] && pu < vbox[2] && pv >= mv0 && pv < mv1) {
-                            int bit = (pv - mv0) * vw + (pu - vbox[0]);
-                            atomicOr(&S.marks[bit >> 5], 1u << (bit & 31));
+                // search a full batch, or what is left once the blocks run out
+                while (wq_count >= 32 || (!more && wq_count > 0)) {
+                    __syncwarp();
+                    const int nb = min(wq_count, 32);
+                    const bool valid = lane < nb;
+                    KeptPoint kq = {0.f, 0.f, 0.f, 0u};
+                    if (valid) kq = wq[(wq_head + lane) % kWarpQueue];
+                    wq_head = (wq_head + nb) % kWarpQueue;
+                    wq_count -= nb;
+                    const unsigned long long nn = probe_batch(sc, valid, kq.x, kq.y, kq.z, WP, lane);
+                    if (valid) {
+                        bool explained = nn != kEmptyKey;
+                        const int pnn = (int)(uint32_t)nn;
+                        if (explained && sc.color_check) {
+                            float4 lp = __ldg(&sc.lab[pnn]);
+                            float3 lq = srgb8_to_lab(kq.rgb & 255, (kq.rgb >> 8) & 255, (kq.rgb >> 16) & 255);
+                            if (ciede2000(lq, make_float3(lp.x, lp.y, lp.z)) > sc.tau_c) explained = false;
+                        }
+                        if (!explained) {
+                            if (count_jr) ++jr_local;
+                        } else {
+                            int pu = pnn % sc.W, pv = pnn / sc.W;
+                            if (pu >= vbox[0] && pu < vbox[2] && pv >= mv0 && pv < mv1) {
+                                int bit = (pv - mv0) * vw + (pu - vbox[0]);
+                                atomicOr(&S.marks[bit >> 5], 1u << (bit & 31));
+                            }
                         }
                     }
                 }
-                __syncthreads();
+                if (!more) break;
             }
+            __syncthreads();
+            if (threadIdx.x == 0) *S.next_batch = 0;
+            __syncthreads();
         }
     }
 }
@@ -1039,7 +1042,7 @@ __host__ __device__ inline SmemLayout smem_layout(int zcap_words, int mark_words
     SmemLayout L;
     L.marks = align16(sizeof(uint32_t) * (size_t)zcap_words);
     L.kept = align16(L.marks + sizeof(uint32_t) * (size_t)mark_words);
-    L.probe = align16(L.kept + sizeof(KeptPoint) * kKeptCap);
+    L.probe = align16(L.kept + sizeof(KeptPoint) * kWarpQueue * (size_t)(threads / 32));
     L.big = align16(L.probe + sizeof(WarpProbe) * (size_t)(threads / 32));
     L.total = align16(L.big + sizeof(BigTri) * kQueueCap);
     return L;

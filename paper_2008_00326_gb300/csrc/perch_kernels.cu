@@ -464,7 +464,7 @@ __device__ void raster_box(const int* x, const int* y, const float* iz, int A, i
 // ---- resolve queue and per-warp cell groups -------------------------------
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
-constexpr int kGroups = 4;        // distinct query cells looked up together per warp
+constexpr int kGroups = 2;        // distinct query cells looked up together per warp
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
     float x, y, z;
@@ -541,10 +541,10 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
 // Radius search for up to 32 queued points (one per lane; `valid` marks the
 // lanes holding one).  Lanes whose points fall in the same hash cell form a
 // group (__match_any_sync); each group's 27-cell neighbourhood is looked up
-// once, cooperatively.  The group's (query, candidate) pairs are then spread
-// evenly over the 32 lanes -- consecutive lanes take consecutive queries of
-// the same candidate -- and each pair within delta folds (d2 bits, pixel)
-// into its query's minimum with a shared-memory atomicMin.  Returns the
+// once, cooperatively.  The group's candidates are then tested by all 32
+// lanes: floor(32 / G) lanes per query (G = the group's queries) split the
+// candidate list, each keeps its minimum (d2 bits, pixel) in a register and
+// folds it into the query's result with one shared-memory atomicMin.  Returns the
 // lane's own result: the nearest observed point within delta (smallest FP32
 // squared distance, ties to the lowest pixel index) or kEmptyKey.  All 32
 // lanes must call it.
@@ -590,22 +590,27 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
         for (int g = 0; g < ng; ++g) {
             const int T = W.total[g];
             if (T == 0) continue;
+            // k = floor(32 / G) lanes per query; lane j of a query takes
+            // candidates j, j + k, ... and keeps its minimum in a register
             const int G = __popc(W.mask[g]);
-            const int P = G * T;
-            const int dq = 32 % G, dc = 32 / G;
-            int qi = lane % G, ci = lane / G, r = 0;
-            for (int p = lane; p < P; p += 32) {
-                while (W.runs[g][r].y <= ci) ++r;
-                const float4 c = __ldg(&sc.pts[W.runs[g][r].x + ci]);
-                const int ql = W.qlist[g][qi];
+            const int k = 32 / G;
+            if (lane < G * k) {
+                const int ql = W.qlist[g][lane / k];
                 const float4 q = W.q[ql];
-                float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
-                float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-                if (d2 <= sc.delta2)
-                    atomicMin(&W.best[ql], ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w));
-                qi += dq;
-                ci += dc;
-                if (qi >= G) { qi -= G; ++ci; }
+                unsigned long long local = kEmptyKey;
+                int r = 0;
+                for (int ci = lane % k; ci < T; ci += k) {
+                    while (W.runs[g][r].y <= ci) ++r;
+                    const float4 c = __ldg(&sc.pts[W.runs[g][r].x + ci]);
+                    float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
+                    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+                    if (d2 <= sc.delta2) {
+                        unsigned long long key =
+                            ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
+                        local = key < local ? key : local;
+                    }
+                }
+                if (local != kEmptyKey) atomicMin(&W.best[ql], local);
             }
         }
         __syncwarp();

@@ -464,7 +464,7 @@ __device__ void raster_box(const int* x, const int* y, const float* iz, int A, i
 // ---- resolve queue and per-warp cell groups -------------------------------
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
-constexpr int kGroups = 1;        // distinct query cells looked up together per warp
+constexpr int kGroups = 2;        // distinct query cells looked up together per warp
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
     float x, y, z;
@@ -599,32 +599,15 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
                 const float4 q = W.q[ql];
                 unsigned long long local = kEmptyKey;
                 int r = 0;
-                // four candidates per step: their loads are issued together
-                for (int ci = lane % k; ci < T; ci += 4 * k) {
-                    int idx[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int cu = ci + u * k;
-                        idx[u] = -1;
-                        if (cu < T) {
-                            while (W.runs[g][r].y <= cu) ++r;
-                            idx[u] = W.runs[g][r].x + cu;
-                        }
-                    }
-                    float4 c[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (idx[u] >= 0) c[u] = __ldg(&sc.pts[idx[u]]);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (idx[u] < 0) continue;
-                        float ex = __fsub_rn(q.x, c[u].x), ey = __fsub_rn(q.y, c[u].y), ez = __fsub_rn(q.z, c[u].z);
-                        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-                        if (d2 <= sc.delta2) {
-                            unsigned long long key =
-                                ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c[u].w);
-                            local = key < local ? key : local;
-                        }
+                for (int ci = lane % k; ci < T; ci += k) {
+                    while (W.runs[g][r].y <= ci) ++r;
+                    const float4 c = __ldg(&sc.pts[W.runs[g][r].x + ci]);
+                    float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
+                    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+                    if (d2 <= sc.delta2) {
+                        unsigned long long key =
+                            ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
+                        local = key < local ? key : local;
                     }
                 }
                 if (local != kEmptyKey) atomicMin(&W.best[ql], local);

@@ -464,7 +464,7 @@ __device__ void raster_box(const int* x, const int* y, const float* iz, int A, i
 // ---- resolve queue and per-warp cell groups -------------------------------
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
-constexpr int kGroups = 2;        // distinct query cells looked up together per warp
+constexpr int kGroups = 1;        // distinct query cells looked up together per warp
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
     float x, y, z;

@@ -33,7 +33,8 @@
  * Readings of the paper (it is silent on these): pixel centres at integer
  * coordinates; 4 sub-pixel bits; no clipping (triangles with a vertex nearer
  * than z_near or outside [-W,2W)x[-H,2H) are culled whole); two-sided
- * rasterisation; top-left style tie rule; perspective-correct 1/Z depth;
+ * rasterisation; top-left style tie rule; perspective-correct depth
+ * z = A / sum(w_i / Z_i);
  * nearest depth wins, then lowest triangle id; affine integer colour
  * interpolation; occluder margin m; nearest-neighbour ties to the lowest pixel
  * index; V(h) is the object's inscribed cylinder about its z axis, or
@@ -315,10 +316,10 @@ int or_render_keys(const or_scene *sc, const or_mesh *m, const float pose[12],
                 int64_t w[3];
                 if (!coverage(&o, u, v, w))
                     continue;
-                /* C4: perspective-correct depth from interpolated 1/Z */
+                /* C4: perspective-correct depth from interpolated 1/Z:
+                 * z = A / (w0/Z0 + w1/Z1 + w2/Z2), one division */
                 float num = ((float)w[0] * o.iz[0] + (float)w[1] * o.iz[1]) + (float)w[2] * o.iz[2];
-                float iz = num / (float)o.A;
-                float z = 1.0f / iz;
+                float z = (float)o.A / num;
                 float dz = z * 10000.0f;
                 if (!(dz < 4294967296.0f))
                     continue;

@@ -326,8 +326,6 @@ cudaError_t launch_build(const DevScene& sc, const BuildBuffers& b, uint32_t cap
 // scoring kernel
 // ---------------------------------------------------------------------------
 
-constexpr int kQueueCap = 64;     // large-triangle queue entries per tile
-constexpr int kBigArea = 48;      // pixel-box area above which a warp rasterises the triangle
 
 struct TriSetup {
     int x[3], y[3];               // snapped positions, 1/16 px
@@ -336,11 +334,12 @@ struct TriSetup {
     int A;                        // doubled area > 0
 };
 
-struct BigTri {                   // queued large triangle (64 bytes)
-    int x[3], y[3];
-    float iz[3];
-    int A, tri;
-    int u0, v0, u1, v1;
+struct TriStage {                 // a set-up triangle staged for its warp (64 bytes)
+    int x[3], y[3];               // snapped positions, 1/16 px
+    float iz[3];                  // 1/Z
+    int A, tri;                   // doubled area, triangle id
+    int u0, v0, bw;               // pixel box origin and width (in the tile)
+    int owns;                     // bit i: edge i owns samples lying on it
     int pad;
 };
 
@@ -398,7 +397,8 @@ __device__ __forceinline__ bool setup_triangle(const DevScene& sc, const DevMesh
     return true;
 }
 
-// Depth of a covered sample from the edge values (perspective-correct 1/Z).
+// Depth of a covered sample from the edge values (perspective-correct:
+// z = A / (w0/Z0 + w1/Z1 + w2/Z2), one division).
 // Returns false if the depth falls outside [1, 2^32-1].
 __device__ __forceinline__ bool sample_depth(int w0, int w1, int w2, const float* iz, int A,
                                              unsigned& d)
@@ -406,8 +406,7 @@ __device__ __forceinline__ bool sample_depth(int w0, int w1, int w2, const float
     float num = __fadd_rn(__fadd_rn(__fmul_rn(__int2float_rn(w0), iz[0]),
                                     __fmul_rn(__int2float_rn(w1), iz[1])),
                           __fmul_rn(__int2float_rn(w2), iz[2]));
-    float izp = __fdiv_rn(num, __int2float_rn(A));
-    float z = __fdiv_rn(1.0f, izp);
+    float z = __fdiv_rn(__int2float_rn(A), num);
     float dz = __fmul_rn(z, 10000.0f);
     if (!(dz < 4294967296.0f)) return false;
     long long dd = __float2ll_rn(dz);
@@ -431,36 +430,6 @@ __device__ __forceinline__ void zmin(uint32_t* zbuf, int idx, unsigned d, int tr
     }
 }
 
-// Rasterise the pixel box [u0,u1] x [v0,v1] of a set-up triangle, sequentially.
-template <bool K32>
-__device__ void raster_box(const int* x, const int* y, const float* iz, int A, int tri, int u0,
-                           int v0, int u1, int v1, int tu0, int tv0, int tw, uint32_t* zbuf,
-                           int* err)
-{
-    const bool o0 = owns(x[2] - x[1], y[2] - y[1]);
-    const bool o1 = owns(x[0] - x[2], y[0] - y[2]);
-    const bool o2 = owns(x[1] - x[0], y[1] - y[0]);
-    const int s0 = -16 * (y[2] - y[1]), s1 = -16 * (y[0] - y[2]), s2 = -16 * (y[1] - y[0]);
-    for (int v = v0; v <= v1; ++v) {
-        int sy = 16 * v, sx = 16 * u0;
-        int w0 = edge_fn(x[1], y[1], x[2], y[2], sx, sy);
-        int w1 = edge_fn(x[2], y[2], x[0], y[0], sx, sy);
-        int w2 = edge_fn(x[0], y[0], x[1], y[1], sx, sy);
-        for (int u = u0; u <= u1; ++u) {
-            bool cov = (w0 > 0 || (w0 == 0 && o0)) && (w1 > 0 || (w1 == 0 && o1)) &&
-                       (w2 > 0 || (w2 == 0 && o2));
-            if (cov) {
-                unsigned d;
-                if (sample_depth(w0, w1, w2, iz, A, d))
-                    zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, tri, err);
-            }
-            w0 += s0;
-            w1 += s1;
-            w2 += s2;
-        }
-    }
-}
-
 // ---- resolve queue and per-warp cell groups -------------------------------
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
@@ -481,7 +450,13 @@ struct __align__(16) WarpProbe {
     unsigned long long best[32];  // nearest-neighbour key of each lane's query
 };
 
+// Per-warp scratch: the radius search and the rasteriser's triangle stage
+// use the same bytes (the two phases are separated by block barriers).
+constexpr size_t kWarpScratch = sizeof(WarpProbe) > 32 * sizeof(TriStage) ? sizeof(WarpProbe)
+                                                                            : 32 * sizeof(TriStage);
 static_assert(sizeof(KeptPoint) == 16, "kept-point queue entries are 16 bytes");
+static_assert(sizeof(TriStage) == 64, "staged triangles are 64 bytes");
+static_assert(kWarpScratch % 16 == 0, "per-warp scratch keeps 16-byte alignment");
 static_assert(sizeof(WarpProbe) % 16 == 0, "per-warp scratch keeps 16-byte alignment");
 
 // Warp-cooperative lookup of the 27-cell neighbourhoods of up to kGroups
@@ -659,11 +634,9 @@ __device__ void project_box(const DevScene& sc, const float* P, const float* lo,
 struct ScoreSmem {
     uint32_t* zbuf;               // z-buffer tile (32- or 64-bit keys)
     uint32_t* marks;              // admissible-band bitset
-    BigTri* big;                  // large-triangle queue
     KeptPoint* kept;              // per warp: resolve -> radius-search ring queue
-    WarpProbe* probe;             // per warp scratch of the radius search
-    int* n_big;
-    int* n_kept;
+    WarpProbe* probe;             // per warp scratch of the radius search (aliases stage)
+    TriStage* stage;              // per warp 32 staged triangles (aliases probe)
     int* next_batch;
 };
 
@@ -749,7 +722,8 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
 {
     const DevScene& sc = a.sc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpProbe& WP = S.probe[warp];
+    WarpProbe& WP = *reinterpret_cast<WarpProbe*>(reinterpret_cast<char*>(S.probe) + warp * kWarpScratch);
+    TriStage* TS = reinterpret_cast<TriStage*>(reinterpret_cast<char*>(S.stage) + warp * kWarpScratch);
     const int s = sc.stride;
     const int rw = rbox[2] - rbox[0], rh = rbox[3] - rbox[1];
     if (rw <= 0 || rh <= 0) return;
@@ -765,49 +739,70 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
             const int tpx = tw * (tv1 - tv0);
             const int words = K32 ? tpx : 2 * tpx;
             for (int i = threadIdx.x; i < words; i += NT) zbuf[i] = empty32;
-            if (threadIdx.x == 0) { *S.n_big = 0; *S.next_batch = 0; }
+            if (threadIdx.x == 0) *S.next_batch = 0;
             __syncthreads();
-            // ---- raster: one thread per triangle, large ones queued for a warp
-            for (int t = threadIdx.x; t < a.m.n_tris; t += NT) {
+            // ---- raster: a warp sets up 32 triangles (one per lane), stages
+            // them in shared memory and spreads the pixels of their boxes
+            // evenly over its lanes (a prefix sum of the box areas, then a
+            // binary search per pixel for its triangle)
+            for (int base = warp * 32; base < a.m.n_tris; base += NT) {
+                const int t = base + lane;
+                int area = 0;
                 TriSetup o;
-                if (!get_triangle<VC>(sc, a.m, P, vc, t, o)) continue;
-                int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
-                int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
-                int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
-                int v0 = max(ceil16(ymin), tv0), v1 = min(floor16(ymax), tv1 - 1);
-                if (u0 > u1 || v0 > v1) continue;
-                int area = (u1 - u0 + 1) * (v1 - v0 + 1);
-                if (area > kBigArea) {
-                    int q = atomicAdd(S.n_big, 1);
-                    if (q < kQueueCap) {
-                        BigTri& b = S.big[q];
-                        for (int k = 0; k < 3; ++k) { b.x[k] = o.x[k]; b.y[k] = o.y[k]; b.iz[k] = o.iz[k]; }
-                        b.A = o.A; b.tri = t; b.u0 = u0; b.v0 = v0; b.u1 = u1; b.v1 = v1;
-                        continue;
+                if (t < a.m.n_tris && get_triangle<VC>(sc, a.m, P, vc, t, o)) {
+                    int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
+                    int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
+                    int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
+                    int v0 = max(ceil16(ymin), tv0), v1 = min(floor16(ymax), tv1 - 1);
+                    if (u0 <= u1 && v0 <= v1) {
+                        area = (u1 - u0 + 1) * (v1 - v0 + 1);
+                        TriStage& e = TS[lane];
+                        for (int k = 0; k < 3; ++k) { e.x[k] = o.x[k]; e.y[k] = o.y[k]; e.iz[k] = o.iz[k]; }
+                        e.A = o.A;
+                        e.tri = t;
+                        e.u0 = u0;
+                        e.v0 = v0;
+                        e.bw = u1 - u0 + 1;
+                        e.owns = (owns(o.x[2] - o.x[1], o.y[2] - o.y[1]) ? 1 : 0) |
+                                 (owns(o.x[0] - o.x[2], o.y[0] - o.y[2]) ? 2 : 0) |
+                                 (owns(o.x[1] - o.x[0], o.y[1] - o.y[0]) ? 4 : 0);
                     }
                 }
-                raster_box<K32>(o.x, o.y, o.iz, o.A, t, u0, v0, u1, v1, tu0, tv0, tw, zbuf, a.err);
-            }
-            __syncthreads();
-            const int nq = min(*S.n_big, kQueueCap);
-            for (int e = warp; e < nq; e += NT / 32) {
-                const BigTri& b = S.big[e];
-                const int bw = b.u1 - b.u0 + 1, area = bw * (b.v1 - b.v0 + 1);
-                const bool o0 = owns(b.x[2] - b.x[1], b.y[2] - b.y[1]);
-                const bool o1 = owns(b.x[0] - b.x[2], b.y[0] - b.y[2]);
-                const bool o2 = owns(b.x[1] - b.x[0], b.y[1] - b.y[0]);
-                for (int k = lane; k < area; k += 32) {
-                    int u = b.u0 + k % bw, v = b.v0 + k / bw;
-                    int sx = 16 * u, sy = 16 * v;
-                    int w0 = edge_fn(b.x[1], b.y[1], b.x[2], b.y[2], sx, sy);
-                    int w1 = edge_fn(b.x[2], b.y[2], b.x[0], b.y[0], sx, sy);
-                    int w2 = edge_fn(b.x[0], b.y[0], b.x[1], b.y[1], sx, sy);
-                    bool cov = (w0 > 0 || (w0 == 0 && o0)) && (w1 > 0 || (w1 == 0 && o1)) &&
-                               (w2 > 0 || (w2 == 0 && o2));
-                    unsigned d;
-                    if (cov && sample_depth(w0, w1, w2, b.iz, b.A, d))
-                        zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, b.tri, a.err);
+                int incl = area;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    int x = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += x;
                 }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                __syncwarp();
+                for (int f0 = 0; f0 < total; f0 += 32) {
+                    const int f = f0 + lane;
+                    // the triangle j whose pixel range holds f: incl[j-1] <= f < incl[j]
+                    int j = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+                        if (v <= f) j += step;
+                    }
+                    const int excl = __shfl_sync(0xffffffffu, incl, j > 0 ? j - 1 : 0);
+                    if (f >= total) continue;
+                    const TriStage& e = TS[j];
+                    const int local = f - (j > 0 ? excl : 0);
+                    const int dv = local / e.bw;
+                    const int u = e.u0 + (local - dv * e.bw), v = e.v0 + dv;
+                    const int sx = 16 * u, sy = 16 * v;
+                    const int w0 = edge_fn(e.x[1], e.y[1], e.x[2], e.y[2], sx, sy);
+                    const int w1 = edge_fn(e.x[2], e.y[2], e.x[0], e.y[0], sx, sy);
+                    const int w2 = edge_fn(e.x[0], e.y[0], e.x[1], e.y[1], sx, sy);
+                    const bool cov = (w0 > 0 || (w0 == 0 && (e.owns & 1))) &&
+                                     (w1 > 0 || (w1 == 0 && (e.owns & 2))) &&
+                                     (w2 > 0 || (w2 == 0 && (e.owns & 4)));
+                    unsigned d;
+                    if (cov && sample_depth(w0, w1, w2, e.iz, e.A, d))
+                        zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, e.tri, a.err);
+                }
+                __syncwarp();
             }
             __syncthreads();
             if (a.dump) {
@@ -1037,7 +1032,7 @@ __device__ void score_one(const ScoreArgs& a, long long h, const ScoreSmem& S, f
 // region starts on a 16-byte boundary (the queues and the per-warp scratch
 // hold float4 and 64-bit fields).
 struct SmemLayout {
-    size_t marks, kept, probe, big, total;
+    size_t marks, kept, probe, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -1048,8 +1043,7 @@ __host__ __device__ inline SmemLayout smem_layout(int zcap_words, int mark_words
     L.marks = align16(sizeof(uint32_t) * (size_t)zcap_words);
     L.kept = align16(L.marks + sizeof(uint32_t) * (size_t)mark_words);
     L.probe = align16(L.kept + sizeof(KeptPoint) * kWarpQueue * (size_t)(threads / 32));
-    L.big = align16(L.probe + sizeof(WarpProbe) * (size_t)(threads / 32));
-    L.total = align16(L.big + sizeof(BigTri) * kQueueCap);
+    L.total = align16(L.probe + kWarpScratch * (size_t)(threads / 32));
     return L;
 }
 
@@ -1060,7 +1054,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
-    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_nbig, s_nkept, s_next, s_h;
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_h;
     __shared__ int s_red[3][NT / 32];
 
     SmemLayout L = smem_layout(a.zcap_words, a.mark_words, NT);
@@ -1069,9 +1063,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.marks = reinterpret_cast<uint32_t*>(smem + L.marks);
     S.kept = reinterpret_cast<KeptPoint*>(smem + L.kept);
     S.probe = reinterpret_cast<WarpProbe*>(smem + L.probe);
-    S.big = reinterpret_cast<BigTri*>(smem + L.big);
-    S.n_big = &s_nbig;
-    S.n_kept = &s_nkept;
+    S.stage = reinterpret_cast<TriStage*>(smem + L.probe);
     S.next_batch = &s_next;
     unsigned long long* vc = a.vcache ? a.vcache + (size_t)blockIdx.x * a.vstride : nullptr;
     for (;;) {

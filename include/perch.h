@@ -202,6 +202,53 @@ PERCH_API perch_status perch_best_noalloc(const int32_t *costs, const uint64_t *
 PERCH_API perch_status perch_set_launch_config(perch_ctx *ctx, int32_t threads, int32_t zbuf_words,
                                                int32_t mark_bits);
 
+/* ---- batched form ----------------------------------------------------------
+ * Hypotheses of many (scene, mesh) searches scored by ONE persistent launch:
+ * every block of the scoring kernel takes the next hypothesis of the whole
+ * list from a device counter, so searches of very different sizes (objects,
+ * ROIs, hypothesis counts) share the GPU without per-search launches.  Each
+ * item is what perch_score_hypotheses takes (Sec. IV-A "Parallel Search":
+ * every object of every scene is searched independently). */
+typedef struct perch_work_item {
+    int32_t scene_id;
+    int32_t mesh_id;
+    int32_t label;            /* as in perch_score_hypotheses */
+    int32_t roi[4];           /* {u0,v0,u1,v1}; u1 <= u0 or v1 <= v0 means the whole image */
+    int64_t pose_offset;      /* index of the item's first hypothesis in the batch arrays */
+    int64_t n;                /* hypotheses of the item (>= 0) */
+} perch_work_item;
+
+/* Score all items of a batch.  poses holds 12 floats and costs 2 int32 per
+ * hypothesis; item i uses entries [pose_offset, pose_offset + n).  Items may
+ * not overlap.  cuda_stream NULL: HOST pointers, synchronous; otherwise DEVICE
+ * pointers enqueued on that stream.  items is a host array, copied by the call.
+ * The total number of hypotheses must stay below 2^32. */
+PERCH_API perch_status perch_score_batch(perch_ctx *ctx, const perch_work_item *items, int32_t n_items,
+                                         const float *poses, int32_t *costs, void *cuda_stream);
+
+/* A batch captured once as a CUDA graph (counter reset + persistent launch)
+ * and replayed: the item list, the device pose/cost arrays and the launch
+ * shape are fixed at creation; the caller refills the pose array between
+ * replays.  The graph owns its scratch, so replays of one graph must be
+ * ordered (one stream), while different graphs and the context may run
+ * concurrently.  poses/costs are DEVICE pointers. */
+typedef struct perch_batch_graph perch_batch_graph;
+PERCH_API perch_status perch_batch_graph_create(perch_ctx *ctx, const perch_work_item *items,
+                                                int32_t n_items, const float *poses,
+                                                int32_t *costs, perch_batch_graph **out);
+PERCH_API perch_status perch_batch_graph_launch(perch_batch_graph *g, void *cuda_stream);
+PERCH_API perch_status perch_batch_graph_destroy(perch_batch_graph *g);
+
+/* Autotuner: time the candidate launch shapes (threads per block x z-buffer
+ * words) on this batch (DEVICE poses/costs, results are overwritten), keep the
+ * fastest as the context's launch configuration and remember it for batches
+ * of the same class (largest ROI area and triangle count, each rounded to a
+ * power of two); a later call for a known class returns the remembered shape
+ * without timing.  *threads and *zbuf_words receive the choice. */
+PERCH_API perch_status perch_autotune(perch_ctx *ctx, const perch_work_item *items, int32_t n_items,
+                                      const float *poses, int32_t *costs, int32_t *threads,
+                                      int32_t *zbuf_words);
+
 /* Debug view of the rasteriser used by perch_score_hypotheses: the z-buffer of
  * one pose as 64-bit keys (depth << 32) | triangle id, 0xFFFFFFFFFFFFFFFF where
  * nothing is covered.  keys is a HOST buffer of W*H uint64 of the scene; the

@@ -35,6 +35,30 @@ struct SceneRec {
     void* table = nullptr;
 };
 
+// Everything one chain of scoring launches needs besides its inputs: the
+// hypothesis counter, the per-block vertex caches, and a small ring of
+// job-table uploads (pinned host staging + device table + an event each), so
+// that consecutive asynchronous launches need not wait for each other on the
+// host.  Launches that share a ScoreScratch are ordered on the GPU through
+// `last` (they share the counter and the caches).
+constexpr int kStageRing = 4;
+
+struct JobStage {
+    void* host = nullptr;          // pinned
+    void* dev = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;
+};
+
+struct ScoreScratch {
+    unsigned* next = nullptr;      // device counter
+    void* vcache = nullptr;
+    size_t vcache_bytes = 0;
+    JobStage stage[kStageRing];
+    int turn = 0;
+    cudaEvent_t last = nullptr;
+};
+
 class DeviceGuard {
 public:
     explicit DeviceGuard(int dev)
@@ -70,11 +94,18 @@ struct perch_ctx {
     unsigned* d_best_ticket = nullptr;
     long long* d_best_index = nullptr;
     int32_t* d_best_cost = nullptr;
-    unsigned* d_next = nullptr;            // hypothesis counter of the persistent scorer
-    void* vcache = nullptr;                // per-block vertex caches of the scorer
-    size_t vcache_bytes = 0;
-    cudaEvent_t ev_score = nullptr;        // end of the last scoring launch
+    ScoreScratch plain;                    // scratch of the context's own scoring launches
+    std::map<uint64_t, perch::ScoreConfig> tuned;   // autotuner results by batch class
     perch::ScoreConfig cfg{256, 8192, 1 << 16};
+};
+
+struct perch_batch_graph {
+    perch_ctx* ctx = nullptr;
+    unsigned* next = nullptr;              // the graph's own hypothesis counter
+    void* vcache = nullptr;                // and vertex caches
+    void* table = nullptr;                 // device job table (uploaded at creation)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -208,67 +239,149 @@ perch_status fit_config(perch_ctx* c, int mark_words, perch::ScoreConfig* cfg)
     return PERCH_OK;
 }
 
-// Grid of the persistent scorer and its vertex-cache slots (one per block,
-// used when the snapped coordinates fit in int16, i.e. W, H <= 1023).  The
-// cache grows on demand; growing waits for every earlier scoring launch.
-perch_status prepare_score(perch_ctx* c, const SceneRec& s, const MeshRec& m,
-                           const perch::ScoreConfig& cfg, int mark_words, int* grid,
-                           unsigned long long** vc, long long* vstride)
+perch_status scratch_init(perch_ctx* c, ScoreScratch& X)
 {
-    *grid = perch::score_grid(cfg, mark_words);
-    if (*grid <= 0) {
-        cudaGetLastError();
-        return fail(c, PERCH_E_CUDA, "scoring kernel does not fit on the device");
-    }
-    *vc = nullptr;
-    *vstride = 0;
-    if (s.ds.W > 1023 || s.ds.H > 1023) return PERCH_OK;
-    long long stride = ((long long)m.dm.n_verts + 31) / 32 * 32;
-    size_t need = (size_t)*grid * stride * sizeof(unsigned long long);
-    if (need > c->vcache_bytes) {
-        if (c->ev_score) cudaEventSynchronize(c->ev_score);
-        cudaStreamSynchronize(c->stream);
-        dfree(c, c->vcache);
-        c->vcache = nullptr;
-        c->vcache_bytes = 0;
-        perch_status st = dalloc(c, need, &c->vcache);
-        if (st != PERCH_OK) return st;
-        c->vcache_bytes = need;
-    }
-    *vc = (unsigned long long*)c->vcache;
-    *vstride = stride;
+    void* p = nullptr;
+    perch_status st = dalloc(c, 16, &p);
+    if (st != PERCH_OK) return st;
+    X.next = (unsigned*)p;
+    cudaError_t e = cudaEventCreateWithFlags(&X.last, cudaEventDisableTiming);
+    for (int i = 0; i < kStageRing && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&X.stage[i].done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(X.last, c->stream);
+    for (int i = 0; i < kStageRing && e == cudaSuccess; ++i) e = cudaEventRecord(X.stage[i].done, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "scratch events");
     return PERCH_OK;
 }
 
-// Launch the scorer on stream st after every earlier scoring launch of this
-// context (they share the counter and the vertex caches).
-cudaError_t launch_ordered(perch_ctx* c, const perch::ScoreArgs& a, const perch::ScoreConfig& cfg,
-                           int grid, cudaStream_t st)
+void scratch_free(perch_ctx* c, ScoreScratch& X)
 {
-    cudaError_t e = cudaStreamWaitEvent(st, c->ev_score, 0);
-    if (e == cudaSuccess) e = perch::launch_score(a, cfg, grid, st);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev_score, st);
-    return e;
+    if (X.last) cudaEventSynchronize(X.last);
+    dfree(c, X.next);
+    dfree(c, X.vcache);
+    for (int i = 0; i < kStageRing; ++i) {
+        if (X.stage[i].done) cudaEventSynchronize(X.stage[i].done);
+        if (X.stage[i].host) cudaFreeHost(X.stage[i].host);
+        dfree(c, X.stage[i].dev);
+        if (X.stage[i].done) cudaEventDestroy(X.stage[i].done);
+        X.stage[i] = JobStage{};
+    }
+    if (X.last) cudaEventDestroy(X.last);
+    X = ScoreScratch{};
 }
 
-perch::ScoreArgs make_args(perch_ctx* c, const SceneRec& s, const MeshRec& m, int label,
-                           const int roi[4], const float* poses, int32_t* costs, long long n,
-                           const perch::ScoreConfig& cfg, int mark_words)
+// Build the device description of one work item.
+perch_status make_job(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t label,
+                      const int32_t* roi, const float* poses, int32_t* costs, long long n,
+                      perch::Job* J, int* mark_words, const SceneRec** scene, const MeshRec** mesh)
 {
+    auto si = c->scenes.find(scene_id);
+    if (si == c->scenes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown scene %d", scene_id);
+    auto mi = c->meshes.find(mesh_id);
+    if (mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
+    if (label < -1) return fail(c, PERCH_E_INVALID, "label must be -1 or >= 0");
+    if (label >= 0 && !si->second.labels)
+        return fail(c, PERCH_E_INVALID, "label %d given but the observation has no labels", label);
+    if (n < 0) return fail(c, PERCH_E_INVALID, "n < 0");
+    int r[4];
+    clip_roi(c, si->second, roi, r);
+    *J = perch::Job{};
+    J->sc = si->second.ds;
+    J->m = mi->second.dm;
+    J->label = label;
+    for (int i = 0; i < 4; ++i) J->roi[i] = r[i];
+    J->poses = poses;
+    J->costs = costs;
+    J->n = n;
+    *mark_words = mark_words_for(si->second, label, r, c->cfg.mark_bits);
+    if (scene) *scene = &si->second;
+    if (mesh) *mesh = &mi->second;
+    return PERCH_OK;
+}
+
+// Upload the job table to the next ring slot and launch the persistent scorer
+// over it on stream st, after every earlier launch that used X.
+perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Job>& jobs,
+                      int mark_words, const perch::ScoreConfig& cfg_in, cudaStream_t st,
+                      unsigned long long* dump)
+{
+    long long total = 0;
+    int max_verts = 0;
+    bool small_images = true;
+    for (const auto& j : jobs) {
+        total += j.n;
+        max_verts = std::max(max_verts, j.m.n_verts);
+        small_images = small_images && j.sc.W <= 1023 && j.sc.H <= 1023;
+    }
+    if (total == 0) return PERCH_OK;
+    if (total > 0xFFFFFFF0ll) return fail(c, PERCH_E_INVALID, "more than 2^32 hypotheses in one launch");
+    perch::ScoreConfig cfg = cfg_in;
+    perch_status stt = fit_config(c, mark_words, &cfg);
+    if (stt != PERCH_OK) return stt;
+    const int grid = perch::score_grid(cfg, mark_words);
+    if (grid <= 0) {
+        cudaGetLastError();
+        return fail(c, PERCH_E_CUDA, "scoring kernel does not fit on the device");
+    }
+    // vertex caches: one slot per block, used when snapped coordinates fit in int16
+    long long vstride = 0;
+    if (small_images) {
+        vstride = ((long long)max_verts + 31) / 32 * 32;
+        size_t need = (size_t)grid * vstride * sizeof(unsigned long long);
+        if (need > X.vcache_bytes) {
+            cudaEventSynchronize(X.last);
+            dfree(c, X.vcache);
+            X.vcache = nullptr;
+            X.vcache_bytes = 0;
+            if ((stt = dalloc(c, need, &X.vcache)) != PERCH_OK) return stt;
+            X.vcache_bytes = need;
+        }
+    }
+    // job table: jobs followed by their inclusive prefix sums
+    JobStage& S = X.stage[X.turn];
+    X.turn = (X.turn + 1) % kStageRing;
+    const size_t jb = ((jobs.size() * sizeof(perch::Job)) + 15) & ~(size_t)15;
+    const size_t bytes = jb + jobs.size() * sizeof(long long);
+    cudaError_t e = cudaEventSynchronize(S.done);
+    if (e != cudaSuccess) return cuda_fail(c, e, "job staging");
+    if (bytes > S.bytes) {
+        if (S.host) cudaFreeHost(S.host);
+        S.host = nullptr;
+        dfree(c, S.dev);
+        S.dev = nullptr;
+        S.bytes = 0;
+        size_t want = std::max(bytes, (size_t)4096);
+        if (cudaMallocHost(&S.host, want) != cudaSuccess) {
+            cudaGetLastError();
+            S.host = nullptr;
+            return fail(c, PERCH_E_NOMEM, "pinned job staging");
+        }
+        if ((stt = dalloc(c, want, &S.dev)) != PERCH_OK) return stt;
+        S.bytes = want;
+    }
+    std::memcpy(S.host, jobs.data(), jobs.size() * sizeof(perch::Job));
+    long long* ends = (long long*)((char*)S.host + jb);
+    long long acc = 0;
+    for (size_t i = 0; i < jobs.size(); ++i) ends[i] = (acc += jobs[i].n);
     perch::ScoreArgs a{};
-    a.sc = s.ds;
-    a.m = m.dm;
-    a.label = label;
-    for (int i = 0; i < 4; ++i) a.roi[i] = roi[i];
-    a.poses = poses;
-    a.costs = costs;
-    a.n = n;
+    a.jobs = (const perch::Job*)S.dev;
+    a.job_end = (const long long*)((char*)S.dev + jb);
+    a.n_jobs = (int)jobs.size();
+    a.n = total;
     a.zcap_words = cfg.zcap_words;
     a.mark_words = mark_words;
-    a.dump = nullptr;
+    a.dump = dump;
     a.err = c->d_err;
-    a.next = c->d_next;
-    return a;
+    a.next = X.next;
+    a.vcache = (unsigned long long*)X.vcache;
+    a.vstride = vstride;
+    e = cudaStreamWaitEvent(st, X.last, 0);
+    if (!e) e = cudaMemcpyAsync(S.dev, S.host, bytes, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaEventRecord(S.done, st);
+    if (!e) e = perch::launch_score(a, cfg, grid, st);
+    if (!e) e = cudaEventRecord(X.last, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "scoring launch");
+    return PERCH_OK;
 }
 
 }  // namespace
@@ -314,12 +427,8 @@ perch_status perch_create(perch_ctx** out, int32_t device, uint64_t hbm_budget_b
         c->d_best_ticket = (unsigned*)p;
         c->d_best_index = (long long*)((char*)p + 16);
         c->d_best_cost = (int32_t*)((char*)p + 32);
-        c->d_next = (unsigned*)((char*)p + 48);
     }
-    if (st == PERCH_OK && (e = cudaEventCreateWithFlags(&c->ev_score, cudaEventDisableTiming)) != cudaSuccess)
-        st = cuda_fail(c, e, "cudaEventCreate");
-    if (st == PERCH_OK && (e = cudaEventRecord(c->ev_score, c->stream)) != cudaSuccess)
-        st = cuda_fail(c, e, "cudaEventRecord");
+    if (st == PERCH_OK) st = scratch_init(c, c->plain);
     if (st == PERCH_OK) {
         cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
         cudaMemsetAsync(c->d_best_ticket, 0, 64, c->stream);
@@ -340,10 +449,9 @@ perch_status perch_destroy(perch_ctx* c)
     if (!c) return PERCH_OK;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->ev_score) cudaEventSynchronize(c->ev_score);
+    scratch_free(c, c->plain);
     for (auto& kv : c->allocs) cudaFree(kv.first);
     c->allocs.clear();
-    if (c->ev_score) cudaEventDestroy(c->ev_score);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return PERCH_OK;
@@ -585,21 +693,6 @@ perch_status perch_release_scene(perch_ctx* c, int32_t scene_id)
     return PERCH_OK;
 }
 
-static perch_status lookup(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t label,
-                           SceneRec** s, MeshRec** m)
-{
-    auto si = c->scenes.find(scene_id);
-    if (si == c->scenes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown scene %d", scene_id);
-    auto mi = c->meshes.find(mesh_id);
-    if (mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
-    if (label < -1) return fail(c, PERCH_E_INVALID, "label must be -1 or >= 0");
-    if (label >= 0 && !si->second.labels)
-        return fail(c, PERCH_E_INVALID, "label %d given but the observation has no labels", label);
-    *s = &si->second;
-    *m = &mi->second;
-    return PERCH_OK;
-}
-
 perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh_id,
                                     int32_t label, const int32_t* roi, const float* poses,
                                     int64_t n, int32_t* costs, void* cuda_stream)
@@ -609,28 +702,14 @@ perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh
     if (n < 0) return fail(c, PERCH_E_INVALID, "n < 0");
     if (n == 0) return PERCH_OK;
     if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
-    SceneRec* s;
-    MeshRec* m;
-    perch_status st = lookup(c, scene_id, mesh_id, label, &s, &m);
-    if (st != PERCH_OK) return st;
-    int r[4];
-    clip_roi(c, *s, roi, r);
-    int mw = mark_words_for(*s, label, r, c->cfg.mark_bits);
-    perch::ScoreConfig cfg;
-    if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
     DeviceGuard g(c->device);
-    cudaError_t e;
-    int grid;
-    unsigned long long* vc;
-    long long vstride;
-    if ((st = prepare_score(c, *s, *m, cfg, mw, &grid, &vc, &vstride)) != PERCH_OK) return st;
+    perch::Job J;
+    int mw;
+    perch_status st = make_job(c, scene_id, mesh_id, label, roi, poses, costs, n, &J, &mw, nullptr, nullptr);
+    if (st != PERCH_OK) return st;
     if (cuda_stream) {
-        perch::ScoreArgs a = make_args(c, *s, *m, label, r, poses, costs, n, cfg, mw);
-        a.vcache = vc;
-        a.vstride = vstride;
-        if ((e = launch_ordered(c, a, cfg, grid, (cudaStream_t)cuda_stream)) != cudaSuccess)
-            return cuda_fail(c, e, "perch_score_hypotheses launch");
-        return PERCH_OK;
+        std::vector<perch::Job> jobs(1, J);
+        return run_jobs(c, c->plain, jobs, mw, c->cfg, (cudaStream_t)cuda_stream, nullptr);
     }
     const long long chunk = 1 << 20;
     if ((st = ensure_stage(c, (size_t)std::min<long long>(n, chunk) * (48 + 8))) != PERCH_OK) return st;
@@ -638,15 +717,83 @@ perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh
     int32_t* d_costs = (int32_t*)((char*)c->stage + (size_t)std::min<long long>(n, chunk) * 48);
     for (long long off = 0; off < n; off += chunk) {
         long long k = std::min(chunk, n - off);
-        e = cudaMemcpyAsync(d_poses, poses + 12 * off, k * 48, cudaMemcpyHostToDevice, c->stream);
-        perch::ScoreArgs a = make_args(c, *s, *m, label, r, d_poses, d_costs, k, cfg, mw);
-        a.vcache = vc;
-        a.vstride = vstride;
-        if (!e) e = launch_ordered(c, a, cfg, grid, c->stream);
-        if (!e) e = cudaMemcpyAsync(costs + 2 * off, d_costs, k * 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaMemcpyAsync(d_poses, poses + 12 * off, k * 48, cudaMemcpyHostToDevice, c->stream);
+        if (e) return cuda_fail(c, e, "perch_score_hypotheses upload");
+        std::vector<perch::Job> jobs(1, J);
+        jobs[0].poses = d_poses;
+        jobs[0].costs = d_costs;
+        jobs[0].n = k;
+        if ((st = run_jobs(c, c->plain, jobs, mw, c->cfg, c->stream, nullptr)) != PERCH_OK) return st;
+        e = cudaMemcpyAsync(costs + 2 * off, d_costs, k * 8, cudaMemcpyDeviceToHost, c->stream);
         if (!e) e = cudaStreamSynchronize(c->stream);
         if (e) return cuda_fail(c, e, "perch_score_hypotheses");
     }
+    return check_device_error(c);
+}
+
+// Validate a batch and turn it into jobs; `base_poses` / `base_costs` are the
+// arrays the item offsets index.
+static perch_status batch_jobs(perch_ctx* c, const perch_work_item* items, int32_t n_items,
+                               const float* base_poses, int32_t* base_costs,
+                               std::vector<perch::Job>* jobs, int* mark_words, long long* total)
+{
+    if (!items || n_items < 0) return fail(c, PERCH_E_INVALID, "bad item list");
+    jobs->clear();
+    *mark_words = 0;
+    *total = 0;
+    std::vector<std::pair<long long, long long>> spans;
+    for (int32_t i = 0; i < n_items; ++i) {
+        const perch_work_item& it = items[i];
+        if (it.n < 0 || it.pose_offset < 0) return fail(c, PERCH_E_INVALID, "item %d: negative n or offset", i);
+        if (it.n == 0) continue;
+        const int32_t* roi = (it.roi[2] > it.roi[0] && it.roi[3] > it.roi[1]) ? it.roi : nullptr;
+        perch::Job J;
+        int mw;
+        perch_status st = make_job(c, it.scene_id, it.mesh_id, it.label, roi, base_poses + 12 * it.pose_offset,
+                                   base_costs + 2 * it.pose_offset, it.n, &J, &mw, nullptr, nullptr);
+        if (st != PERCH_OK) return st;
+        jobs->push_back(J);
+        *mark_words = std::max(*mark_words, mw);
+        *total += it.n;
+        spans.push_back({it.pose_offset, it.pose_offset + it.n});
+    }
+    std::sort(spans.begin(), spans.end());
+    for (size_t i = 1; i < spans.size(); ++i)
+        if (spans[i].first < spans[i - 1].second) return fail(c, PERCH_E_INVALID, "batch items overlap");
+    return PERCH_OK;
+}
+
+perch_status perch_score_batch(perch_ctx* c, const perch_work_item* items, int32_t n_items,
+                               const float* poses, int32_t* costs, void* cuda_stream)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
+    DeviceGuard g(c->device);
+    std::vector<perch::Job> jobs;
+    int mw;
+    long long total;
+    long long extent = 0;
+    for (int32_t i = 0; items && i < n_items; ++i) extent = std::max<long long>(extent, items[i].pose_offset + items[i].n);
+    if (cuda_stream) {
+        perch_status st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
+        if (st != PERCH_OK) return st;
+        return run_jobs(c, c->plain, jobs, mw, c->cfg, (cudaStream_t)cuda_stream, nullptr);
+    }
+    perch_status st = ensure_stage(c, (size_t)std::max<long long>(1, extent) * (48 + 8));
+    if (st != PERCH_OK) return st;
+    float* d_poses = (float*)c->stage;
+    int32_t* d_costs = (int32_t*)((char*)c->stage + (size_t)extent * 48);
+    if ((st = batch_jobs(c, items, n_items, d_poses, d_costs, &jobs, &mw, &total)) != PERCH_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(d_poses, poses, extent * 48, cudaMemcpyHostToDevice, c->stream);
+    if (e) return cuda_fail(c, e, "perch_score_batch upload");
+    if ((st = run_jobs(c, c->plain, jobs, mw, c->cfg, c->stream, nullptr)) != PERCH_OK) return st;
+    for (int32_t i = 0; i < n_items && !e; ++i)
+        if (items[i].n > 0)
+            e = cudaMemcpyAsync(costs + 2 * items[i].pose_offset, d_costs + 2 * items[i].pose_offset,
+                                items[i].n * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "perch_score_batch");
     return check_device_error(c);
 }
 
@@ -717,43 +864,215 @@ perch_status perch_debug_render_keys(perch_ctx* c, int32_t scene_id, int32_t mes
     if (!c) return PERCH_E_INVALID;
     c->err.clear();
     if (!pose || !keys) return fail(c, PERCH_E_INVALID, "null pose or keys");
-    SceneRec* s;
-    MeshRec* m;
-    perch_status st = lookup(c, scene_id, mesh_id, -1, &s, &m);
-    if (st != PERCH_OK) return st;
-    int r[4];
-    clip_roi(c, *s, roi, r);
-    int mw = mark_words_for(*s, -1, r, c->cfg.mark_bits);
-    perch::ScoreConfig cfg;
-    if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
     DeviceGuard g(c->device);
+    perch_status st = ensure_stage(c, 64);
+    if (st != PERCH_OK) return st;
+    float* d_pose = (float*)c->stage;
+    int32_t* d_cost = (int32_t*)((char*)c->stage + 48);
+    perch::Job J;
+    int mw;
+    const SceneRec* s;
+    if ((st = make_job(c, scene_id, mesh_id, -1, roi, d_pose, d_cost, 1, &J, &mw, &s, nullptr)) != PERCH_OK)
+        return st;
     size_t npx = (size_t)s->ds.W * s->ds.H;
     void* dump = nullptr;
     if ((st = dalloc(c, npx * 8, &dump)) != PERCH_OK) return st;
-    if ((st = ensure_stage(c, 64)) != PERCH_OK) {
-        dfree(c, dump);
-        return st;
-    }
-    float* d_pose = (float*)c->stage;
-    int32_t* d_cost = (int32_t*)((char*)c->stage + 48);
     cudaError_t e = cudaMemsetAsync(dump, 0xFF, npx * 8, c->stream);
     if (!e) e = cudaMemcpyAsync(d_pose, pose, 48, cudaMemcpyHostToDevice, c->stream);
-    int grid;
-    unsigned long long* vc;
-    long long vstride;
-    if ((st = prepare_score(c, *s, *m, cfg, mw, &grid, &vc, &vstride)) != PERCH_OK) {
+    if (e) {
         dfree(c, dump);
+        return cuda_fail(c, e, "perch_debug_render_keys");
+    }
+    std::vector<perch::Job> jobs(1, J);
+    st = run_jobs(c, c->plain, jobs, mw, c->cfg, c->stream, (unsigned long long*)dump);
+    if (st == PERCH_OK) {
+        e = cudaMemcpyAsync(keys, dump, npx * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (!e) e = cudaStreamSynchronize(c->stream);
+        if (e) st = cuda_fail(c, e, "perch_debug_render_keys");
+    }
+    cudaStreamSynchronize(c->stream);
+    dfree(c, dump);
+    if (st != PERCH_OK) return st;
+    return check_device_error(c);
+}
+
+perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items, int32_t n_items,
+                                      const float* poses, int32_t* costs, perch_batch_graph** out)
+{
+    if (!c || !out) return PERCH_E_INVALID;
+    c->err.clear();
+    *out = nullptr;
+    if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
+    DeviceGuard g(c->device);
+    std::vector<perch::Job> jobs;
+    int mw;
+    long long total;
+    perch_status st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
+    if (st != PERCH_OK) return st;
+    if (total == 0 || total > 0xFFFFFFF0ll) return fail(c, PERCH_E_INVALID, "batch of %lld hypotheses", total);
+    perch::ScoreConfig cfg;
+    if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
+    const int grid = perch::score_grid(cfg, mw);
+    if (grid <= 0) {
+        cudaGetLastError();
+        return fail(c, PERCH_E_CUDA, "scoring kernel does not fit on the device");
+    }
+    perch_batch_graph* G = new (std::nothrow) perch_batch_graph();
+    if (!G) return fail(c, PERCH_E_NOMEM, "graph handle");
+    G->ctx = c;
+    int max_verts = 0;
+    bool small_images = true;
+    for (const auto& j : jobs) {
+        max_verts = std::max(max_verts, j.m.n_verts);
+        small_images = small_images && j.sc.W <= 1023 && j.sc.H <= 1023;
+    }
+    const long long vstride = small_images ? ((long long)max_verts + 31) / 32 * 32 : 0;
+    const size_t jb = ((jobs.size() * sizeof(perch::Job)) + 15) & ~(size_t)15;
+    std::vector<char> table(jb + jobs.size() * sizeof(long long));
+    std::memcpy(table.data(), jobs.data(), jobs.size() * sizeof(perch::Job));
+    long long* ends = (long long*)(table.data() + jb);
+    long long acc = 0;
+    for (size_t i = 0; i < jobs.size(); ++i) ends[i] = (acc += jobs[i].n);
+    void* p = nullptr;
+    if ((st = dalloc(c, 16, &p)) == PERCH_OK) G->next = (unsigned*)p;
+    if (st == PERCH_OK && vstride > 0)
+        st = dalloc(c, (size_t)grid * vstride * sizeof(unsigned long long), &G->vcache);
+    if (st == PERCH_OK) st = dalloc(c, table.size(), &G->table);
+    cudaError_t e = cudaSuccess;
+    if (st == PERCH_OK) {
+        e = cudaMemcpyAsync(G->table, table.data(), table.size(), cudaMemcpyHostToDevice, c->stream);
+        if (!e) e = cudaStreamSynchronize(c->stream);
+    }
+    cudaStream_t cs = nullptr;
+    if (st == PERCH_OK && !e) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (st == PERCH_OK && !e) {
+        perch::ScoreArgs a{};
+        a.jobs = (const perch::Job*)G->table;
+        a.job_end = (const long long*)((char*)G->table + jb);
+        a.n_jobs = (int)jobs.size();
+        a.n = total;
+        a.zcap_words = cfg.zcap_words;
+        a.mark_words = mw;
+        a.err = c->d_err;
+        a.next = G->next;
+        a.vcache = (unsigned long long*)G->vcache;
+        a.vstride = vstride;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (!e) {
+            cudaError_t le = perch::launch_score(a, cfg, grid, cs);
+            e = cudaStreamEndCapture(cs, &G->graph);
+            if (!e) e = le;
+        }
+        if (!e) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (st == PERCH_OK && e) st = cuda_fail(c, e, "perch_batch_graph_create");
+    if (st != PERCH_OK) {
+        perch_batch_graph_destroy(G);
         return st;
     }
-    perch::ScoreArgs a = make_args(c, *s, *m, -1, r, d_pose, d_cost, 1, cfg, mw);
-    a.dump = (unsigned long long*)dump;
-    a.vcache = vc;
-    a.vstride = vstride;
-    if (!e) e = launch_ordered(c, a, cfg, grid, c->stream);
-    if (!e) e = cudaMemcpyAsync(keys, dump, npx * 8, cudaMemcpyDeviceToHost, c->stream);
-    if (!e) e = cudaStreamSynchronize(c->stream);
-    dfree(c, dump);
-    if (e) return cuda_fail(c, e, "perch_debug_render_keys");
+    *out = G;
+    return PERCH_OK;
+}
+
+perch_status perch_batch_graph_launch(perch_batch_graph* G, void* cuda_stream)
+{
+    if (!G || !G->exec) return PERCH_E_INVALID;
+    DeviceGuard g(G->ctx->device);
+    cudaError_t e = cudaGraphLaunch(G->exec, (cudaStream_t)cuda_stream);
+    if (e) return cuda_fail(G->ctx, e, "perch_batch_graph_launch");
+    return PERCH_OK;
+}
+
+perch_status perch_batch_graph_destroy(perch_batch_graph* G)
+{
+    if (!G) return PERCH_OK;
+    perch_ctx* c = G->ctx;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    dfree(c, G->next);
+    dfree(c, G->vcache);
+    dfree(c, G->table);
+    delete G;
+    return PERCH_OK;
+}
+
+perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t n_items,
+                            const float* poses, int32_t* costs, int32_t* threads, int32_t* zbuf_words)
+{
+    if (!c || !threads || !zbuf_words) return PERCH_E_INVALID;
+    c->err.clear();
+    if (!items || n_items < 1 || !poses || !costs) return fail(c, PERCH_E_INVALID, "empty batch");
+    DeviceGuard g(c->device);
+    // class of the batch: largest ROI area and triangle count, as powers of two
+    long long max_area = 0, max_tris = 0;
+    for (int32_t i = 0; i < n_items; ++i) {
+        auto si = c->scenes.find(items[i].scene_id);
+        auto mi = c->meshes.find(items[i].mesh_id);
+        if (si == c->scenes.end() || mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "item %d", i);
+        long long area = (items[i].roi[2] > items[i].roi[0] && items[i].roi[3] > items[i].roi[1])
+                             ? (long long)(items[i].roi[2] - items[i].roi[0]) * (items[i].roi[3] - items[i].roi[1])
+                             : (long long)si->second.ds.W * si->second.ds.H;
+        max_area = std::max(max_area, area);
+        max_tris = std::max<long long>(max_tris, mi->second.dm.n_tris);
+    }
+    const uint64_t key = ((uint64_t)next_pow2(max_area) << 32) | next_pow2(max_tris);
+    auto hit = c->tuned.find(key);
+    if (hit != c->tuned.end()) {
+        c->cfg.threads = hit->second.threads;
+        c->cfg.zcap_words = hit->second.zcap_words;
+        *threads = c->cfg.threads;
+        *zbuf_words = c->cfg.zcap_words;
+        return PERCH_OK;
+    }
+    // time each shape on a sample: the first min(n, 384) hypotheses of each item
+    std::vector<perch_work_item> sample(items, items + n_items);
+    for (auto& it : sample) it.n = std::min<int64_t>(it.n, 384);
+    std::vector<perch::Job> jobs;
+    int mw;
+    long long total;
+    perch_status st = batch_jobs(c, sample.data(), n_items, poses, costs, &jobs, &mw, &total);
+    if (st != PERCH_OK) return st;
+    const perch::ScoreConfig saved = c->cfg;
+    perch::ScoreConfig best = saved;
+    float best_ms = 3.0e38f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int th[3] = {128, 256, 512};
+    const int zw[4] = {2048, 4096, 8192, 16384};
+    for (int ti = 0; ti < 3 && st == PERCH_OK; ++ti) {
+        for (int zi = 0; zi < 4 && st == PERCH_OK; ++zi) {
+            perch::ScoreConfig cfg = saved;
+            cfg.threads = th[ti];
+            cfg.zcap_words = zw[zi];
+            if (perch::score_smem_bytes(cfg, mw) > 200 * 1024) continue;
+            float ms = 3.0e38f;
+            for (int rep = 0; rep < 3 && st == PERCH_OK; ++rep) {
+                cudaEventRecord(e0, c->stream);
+                st = run_jobs(c, c->plain, jobs, mw, cfg, c->stream, nullptr);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms = std::min(ms, t);
+            }
+            if (st == PERCH_OK && ms < best_ms) {
+                best_ms = ms;
+                best = cfg;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PERCH_OK) return st;
+    c->cfg.threads = best.threads;
+    c->cfg.zcap_words = best.zcap_words;
+    c->tuned[key] = c->cfg;
+    *threads = c->cfg.threads;
+    *zbuf_words = c->cfg.zcap_words;
     return check_device_error(c);
 }
 

@@ -36,15 +36,24 @@ struct DevMesh {
     float lo[3], hi[3];       // object-frame bounding box of the vertices
 };
 
-// One scoring launch: n hypotheses of one mesh against one scene.
-struct ScoreArgs {
+// One work item: n hypotheses of one mesh against one scene.
+struct Job {
     DevScene sc;
     DevMesh m;
     int label;                // -1: cylinder V(O); >= 0: label V(O)
     int roi[4];               // clipped to the image, half-open
-    const float* poses;       // n*12
-    int32_t* costs;           // n*2
+    const float* poses;       // n*12 (device)
+    int32_t* costs;           // n*2 (device)
     long long n;
+};
+
+// One scoring launch over a list of work items.  Hypothesis h of the launch
+// belongs to the first job j with h < job_end[j].
+struct ScoreArgs {
+    const Job* jobs;          // n_jobs (device)
+    const long long* job_end; // n_jobs inclusive prefix sums of Job::n (device)
+    int n_jobs;
+    long long n;              // total hypotheses
     int zcap_words;           // z-buffer capacity in 32-bit words
     int mark_words;           // marks bitset capacity in 32-bit words
     unsigned long long* dump; // debug: W*H 64-bit keys, or nullptr

@@ -716,11 +716,11 @@ __device__ __forceinline__ bool get_triangle(const DevScene& sc, const DevMesh& 
 // J_r is accumulated when count_jr; marks are set for nearest neighbours that
 // fall in rows [mv0, mv1) of the admissible box vbox.
 template <int NT, bool K32, bool VC>
-__device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned long long* vc,
+__device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, const unsigned long long* vc,
                             const int* rbox, const ScoreSmem& S, const int* vbox, int mv0, int mv1,
                             bool count_jr, int& jr_local)
 {
-    const DevScene& sc = a.sc;
+    const DevScene& sc = J.sc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpProbe& WP = *reinterpret_cast<WarpProbe*>(reinterpret_cast<char*>(S.probe) + warp * kWarpScratch);
     TriStage* TS = reinterpret_cast<TriStage*>(reinterpret_cast<char*>(S.stage) + warp * kWarpScratch);
@@ -745,11 +745,11 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
             // them in shared memory and spreads the pixels of their boxes
             // evenly over its lanes (a prefix sum of the box areas, then a
             // binary search per pixel for its triangle)
-            for (int base = warp * 32; base < a.m.n_tris; base += NT) {
+            for (int base = warp * 32; base < J.m.n_tris; base += NT) {
                 const int t = base + lane;
                 int area = 0;
                 TriSetup o;
-                if (t < a.m.n_tris && get_triangle<VC>(sc, a.m, P, vc, t, o)) {
+                if (t < J.m.n_tris && get_triangle<VC>(sc, J.m, P, vc, t, o)) {
                     int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
                     int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
                     int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
@@ -857,17 +857,17 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
                             int pix = v * sc.W + u;
                             unsigned dobs = __ldg(&sc.depth[pix]);
                             bool occluded = dobs > 0 && (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
-                                            (a.label < 0 || __ldg(&sc.labels[pix]) != a.label);
+                                            (J.label < 0 || __ldg(&sc.labels[pix]) != J.label);
                             if (!occluded) {
                                 TriSetup o;
-                                get_triangle<VC>(sc, a.m, P, vc, tri, o);
+                                get_triangle<VC>(sc, J.m, P, vc, tri, o);
                                 int sx = 16 * u, sy = 16 * v;
                                 long long w0 = edge_fn(o.x[1], o.y[1], o.x[2], o.y[2], sx, sy);
                                 long long w1 = edge_fn(o.x[2], o.y[2], o.x[0], o.y[0], sx, sy);
                                 long long w2 = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], sx, sy);
-                                uint32_t c0 = __float_as_uint(__ldg(&a.m.verts[o.vid[0]].w));
-                                uint32_t c1 = __float_as_uint(__ldg(&a.m.verts[o.vid[1]].w));
-                                uint32_t c2 = __float_as_uint(__ldg(&a.m.verts[o.vid[2]].w));
+                                uint32_t c0 = __float_as_uint(__ldg(&J.m.verts[o.vid[0]].w));
+                                uint32_t c1 = __float_as_uint(__ldg(&J.m.verts[o.vid[1]].w));
+                                uint32_t c2 = __float_as_uint(__ldg(&J.m.verts[o.vid[2]].w));
                                 long long half = o.A / 2;
                                 uint32_t crgb = 0;
 #pragma unroll
@@ -926,27 +926,27 @@ __device__ void score_tiles(const ScoreArgs& a, const float* P, const unsigned l
 
 // Score hypothesis h (one block).  Writes costs[2h] = J_o, costs[2h+1] = J_r.
 template <int NT>
-__device__ void score_one(const ScoreArgs& a, long long h, const ScoreSmem& S, float* s_pose,
+__device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const ScoreSmem& S, float* s_pose,
                           int* s_rbox, int* s_vbox, int* s_k32, int (*s_red)[NT / 32],
                           unsigned long long* vc)
 {
-    const DevScene& sc = a.sc;
-    if (threadIdx.x < 12) s_pose[threadIdx.x] = a.poses[h * 12 + threadIdx.x];
+    const DevScene& sc = J.sc;
+    if (threadIdx.x < 12) s_pose[threadIdx.x] = J.poses[h * 12 + threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         float zmax;
-        project_box(sc, s_pose, a.m.lo, a.m.hi, a.roi[0], a.roi[1], a.roi[2], a.roi[3], s_rbox, &zmax);
-        *s_k32 = (a.m.n_tris <= 65535 && zmax < 6.5f) ? 1 : 0;
-        if (a.label >= 0) {
-            s_vbox[0] = a.roi[0]; s_vbox[1] = a.roi[1]; s_vbox[2] = a.roi[2]; s_vbox[3] = a.roi[3];
+        project_box(sc, s_pose, J.m.lo, J.m.hi, J.roi[0], J.roi[1], J.roi[2], J.roi[3], s_rbox, &zmax);
+        *s_k32 = (J.m.n_tris <= 65535 && zmax < 6.5f) ? 1 : 0;
+        if (J.label >= 0) {
+            s_vbox[0] = J.roi[0]; s_vbox[1] = J.roi[1]; s_vbox[2] = J.roi[2]; s_vbox[3] = J.roi[3];
         } else {
-            float lo[3] = {-a.m.vol_r, -a.m.vol_r, 0.0f}, hi[3] = {a.m.vol_r, a.m.vol_r, a.m.vol_h};
+            float lo[3] = {-J.m.vol_r, -J.m.vol_r, 0.0f}, hi[3] = {J.m.vol_r, J.m.vol_r, J.m.vol_h};
             float zv;
             project_box(sc, s_pose, lo, hi, 0, 0, sc.W, sc.H, s_vbox, &zv);
         }
     }
     const bool use_vc = vc != nullptr;
-    if (use_vc) vertex_pass(sc, a.m, s_pose, vc, NT);
+    if (use_vc) vertex_pass(sc, J.m, s_pose, vc, NT);
     __syncthreads();
 
     // The admissible box is handled in bands of rows that fit the marks
@@ -957,7 +957,7 @@ __device__ void score_one(const ScoreArgs& a, long long h, const ScoreSmem& S, f
     int jr = 0, n_in = 0, n_marked = 0;
     const int s = sc.stride;
     const float* P = s_pose;
-    const float rr = __fmul_rn(a.m.vol_r, a.m.vol_r);
+    const float rr = __fmul_rn(J.m.vol_r, J.m.vol_r);
     for (int band = 0; band < n_bands; ++band) {
         const int mv0 = s_vbox[1] + band * band_rows;
         const int mv1 = min(mv0 + band_rows, s_vbox[3]);
@@ -965,11 +965,11 @@ __device__ void score_one(const ScoreArgs& a, long long h, const ScoreSmem& S, f
         for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = 0u;
         __syncthreads();
         if (*s_k32) {
-            if (use_vc) score_tiles<NT, true, true>(a, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, true, false>(a, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, true, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, true, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
         } else {
-            if (use_vc) score_tiles<NT, false, true>(a, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, false, false>(a, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, false, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, false, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
         }
         __syncthreads();
         // ---- J_o over the admissible set V(h), rows [mv0, mv1)
@@ -982,15 +982,15 @@ __device__ void score_one(const ScoreArgs& a, long long h, const ScoreSmem& S, f
             unsigned d = __ldg(&sc.depth[pix]);
             if (d == 0) continue;
             bool in;
-            if (a.label >= 0) {
-                in = __ldg(&sc.labels[pix]) == a.label;
+            if (J.label >= 0) {
+                in = __ldg(&sc.labels[pix]) == J.label;
             } else {
                 float3 p = back_project(sc, u, v, d);
                 float e0 = __fsub_rn(p.x, P[3]), e1 = __fsub_rn(p.y, P[7]), e2 = __fsub_rn(p.z, P[11]);
                 float q0 = __fadd_rn(__fadd_rn(__fmul_rn(P[0], e0), __fmul_rn(P[4], e1)), __fmul_rn(P[8], e2));
                 float q1 = __fadd_rn(__fadd_rn(__fmul_rn(P[1], e0), __fmul_rn(P[5], e1)), __fmul_rn(P[9], e2));
                 float q2 = __fadd_rn(__fadd_rn(__fmul_rn(P[2], e0), __fmul_rn(P[6], e1)), __fmul_rn(P[10], e2));
-                in = __fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)) <= rr && q2 >= 0.0f && q2 <= a.m.vol_h;
+                in = __fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)) <= rr && q2 >= 0.0f && q2 <= J.m.vol_h;
             }
             if (in) {
                 ++n_in;
@@ -1021,8 +1021,8 @@ __device__ void score_one(const ScoreArgs& a, long long h, const ScoreSmem& S, f
             z += __shfl_xor_sync(0xffffffffu, z, o);
         }
         if (lane == 0) {
-            a.costs[2 * h] = y - z;
-            a.costs[2 * h + 1] = x;
+            J.costs[2 * h] = y - z;
+            J.costs[2 * h + 1] = x;
         }
     }
     __syncthreads();
@@ -1054,7 +1054,9 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
-    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_h;
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_job_idx;
+    __shared__ long long s_h, s_local;
+    __shared__ Job s_job;
     __shared__ int s_red[3][NT / 32];
 
     SmemLayout L = smem_layout(a.zcap_words, a.mark_words, NT);
@@ -1066,12 +1068,28 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.stage = reinterpret_cast<TriStage*>(smem + L.probe);
     S.next_batch = &s_next;
     unsigned long long* vc = a.vcache ? a.vcache + (size_t)blockIdx.x * a.vstride : nullptr;
+    int cur = -1;
     for (;;) {
-        if (threadIdx.x == 0) s_h = (int)atomicAdd(a.next, 1u);
+        if (threadIdx.x == 0) {
+            const long long h = (long long)atomicAdd(a.next, 1u);
+            s_h = h;
+            if (h < a.n) {
+                // the job holding h: binary search of the inclusive prefix sums
+                int lo = 0, hi = a.n_jobs - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (a.job_end[mid] > h) hi = mid;
+                    else lo = mid + 1;
+                }
+                s_job_idx = lo;
+                if (lo != cur) s_job = a.jobs[lo];
+                s_local = h - (a.job_end[lo] - s_job.n);
+            }
+        }
         __syncthreads();
-        const long long h = s_h;
-        if (h >= a.n) break;
-        score_one<NT>(a, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+        if (s_h >= a.n) break;
+        cur = s_job_idx;
+        score_one<NT>(a, s_job, s_local, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
     }
 }
 
@@ -1111,24 +1129,16 @@ static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, i
     cudaError_t e = cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const long long kMaxPerLaunch = 0x7FFFFFFFll;
-    ScoreArgs b = a;
-    for (long long off = 0; off < a.n; off += kMaxPerLaunch) {
-        long long cnt = a.n - off < kMaxPerLaunch ? a.n - off : kMaxPerLaunch;
-        b.poses = a.poses + 12 * off;
-        b.costs = a.costs + 2 * off;
-        b.n = cnt;
-        if ((e = cudaMemsetAsync(a.next, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-        int g = (int)(cnt < grid ? cnt : grid);
-        k_score<NT><<<g, NT, smem, s>>>(b);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    if ((e = cudaMemsetAsync(a.next, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    int g = (int)(a.n < grid ? a.n : grid);
+    k_score<NT><<<g, NT, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
+    if (a.n > 0xFFFFFFF0ll) return cudaErrorInvalidValue;   // the counter is 32-bit
     switch (cfg.threads) {
     case 128: return launch_score_nt<128>(a, cfg, grid, s);
     case 512: return launch_score_nt<512>(a, cfg, grid, s);

@@ -25,13 +25,32 @@ STATUS = {0: "PERCH_OK", -1: "PERCH_E_INVALID", -2: "PERCH_E_NOMEM", -3: "PERCH_
 EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_error",
            "perch_hbm_used", "perch_load_mesh", "perch_release_mesh", "perch_set_observation",
            "perch_release_scene", "perch_score_hypotheses", "perch_best", "perch_set_launch_config",
-           "perch_debug_render_keys", "perch_best_noalloc")
+           "perch_debug_render_keys", "perch_best_noalloc", "perch_score_batch",
+           "perch_batch_graph_create", "perch_batch_graph_launch", "perch_batch_graph_destroy",
+           "perch_autotune")
 
 
 class PerchError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
         self.status = status
+
+
+class perch_work_item(C.Structure):
+    _fields_ = [("scene_id", C.c_int32), ("mesh_id", C.c_int32), ("label", C.c_int32),
+                ("roi", C.c_int32 * 4), ("pose_offset", C.c_int64), ("n", C.c_int64)]
+
+
+def work_items(specs):
+    """ctypes array of perch_work_item from (scene_id, mesh_id, label, roi|None, offset, n)."""
+    arr = (perch_work_item * max(1, len(specs)))()
+    for i, (sid, mid, label, roi, off, n) in enumerate(specs):
+        arr[i].scene_id, arr[i].mesh_id, arr[i].label = sid, mid, label
+        r = roi if roi is not None else (0, 0, 0, 0)
+        for k in range(4):
+            arr[i].roi[k] = int(r[k])
+        arr[i].pose_offset, arr[i].n = int(off), int(n)
+    return arr
 
 
 class perch_params(C.Structure):
@@ -70,6 +89,11 @@ def load(path: str | None = None):
         "perch_set_launch_config": ([P, I32, I32, I32], I32),
         "perch_debug_render_keys": ([P, I32, I32, P, P, P], I32),
         "perch_best_noalloc": ([P, P, I64, P, P, P], I32),
+        "perch_score_batch": ([P, P, I32, P, P, P], I32),
+        "perch_batch_graph_create": ([P, P, I32, P, P, P], I32),
+        "perch_batch_graph_launch": ([P, P], I32),
+        "perch_batch_graph_destroy": ([P], I32),
+        "perch_autotune": ([P, P, I32, P, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -208,6 +232,43 @@ def perch_best_noalloc(costs, ids, out_index, out_cost, stream=None):
                                    _ptr_of(out_index), _ptr_of(out_cost), handle)
     if st != PERCH_OK:
         raise PerchError(st, "perch_best_noalloc failed")
+
+
+def perch_score_batch(ctx, items, poses, costs=None, stream=None):
+    """items: ctypes array from work_items().  Host mode: poses numpy (N,12) ->
+    costs (N,2).  Device mode: poses/costs torch CUDA tensors and a stream."""
+    n_items = len(items)
+    if stream is None:
+        p, pp = _host(poses, np.float32)
+        out = np.zeros((p.size // 12, 2), np.int32) if costs is None else costs
+        _check(ctx, load().perch_score_batch(ctx, items, n_items, pp, out.ctypes.data, None))
+        return out
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(ctx, load().perch_score_batch(ctx, items, n_items, _ptr_of(poses), _ptr_of(costs), handle))
+    return costs
+
+
+def perch_batch_graph_create(ctx, items, poses, costs):
+    g = C.c_void_p()
+    _check(ctx, load().perch_batch_graph_create(ctx, items, len(items), _ptr_of(poses), _ptr_of(costs),
+                                                 C.byref(g)))
+    return g
+
+
+def perch_batch_graph_launch(ctx, graph, stream):
+    _check(ctx, load().perch_batch_graph_launch(graph, getattr(stream, "cuda_stream", stream)))
+
+
+def perch_batch_graph_destroy(graph):
+    load().perch_batch_graph_destroy(graph)
+
+
+def perch_autotune(ctx, items, poses, costs):
+    t = C.c_int32()
+    z = C.c_int32()
+    _check(ctx, load().perch_autotune(ctx, items, len(items), _ptr_of(poses), _ptr_of(costs),
+                                       C.byref(t), C.byref(z)))
+    return t.value, z.value
 
 
 def perch_set_launch_config(ctx, threads, zbuf_words, mark_bits=0):

@@ -52,6 +52,17 @@ def rodrigues(axis: np.ndarray, theta: float) -> np.ndarray:
     return np.eye(3) + math.sin(theta) * k + (1.0 - math.cos(theta)) * (k @ k)
 
 
+def rodrigues_batch(axes: np.ndarray, theta: np.ndarray) -> np.ndarray:
+    """Rotation matrices (n,3,3) about unit(axes) by theta, float64."""
+    a = axes / np.linalg.norm(axes, axis=1, keepdims=True)
+    k = np.zeros((len(a), 3, 3))
+    k[:, 0, 1], k[:, 0, 2] = -a[:, 2], a[:, 1]
+    k[:, 1, 0], k[:, 1, 2] = a[:, 2], -a[:, 0]
+    k[:, 2, 0], k[:, 2, 1] = -a[:, 1], a[:, 0]
+    s, c = np.sin(theta)[:, None, None], np.cos(theta)[:, None, None]
+    return np.eye(3)[None] + s * k + (1.0 - c) * (k @ k)
+
+
 def random_rotation(rng: np.random.Generator) -> np.ndarray:
     q = rng.normal(size=4)
     q /= np.linalg.norm(q)
@@ -571,6 +582,87 @@ def sixdof_5obj(seed=1003, n_hyp=4096, W=640, H=480, tri_scale=1.0, noise_m=0.00
             poses[i] = pose_rows(r, t)
         reqs.append(Request(k, k, rois[k], poses.astype(np.float32)))
     return Scene("sixdof_5obj", W, H, f, f, cx, cy, depth, rgb, lab, params, meshes, reqs, gts)
+
+
+def mesh_pool(seed=77, tri_counts=(500, 2000, 5000, 10000, 20000, 30000)):
+    """Meshes of three shapes at several triangle counts, shared by batched scenes."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for k, t in enumerate(tri_counts):
+        kind = k % 3
+        if kind == 0:
+            n = max(4, int(round(math.sqrt(t / 2))))
+            a, b, c = rng.uniform(0.03, 0.06, size=3)
+            pool.append(ellipsoid_mesh(a, b, c, n + 1, n, name=f"ellipsoid_{t}"))
+        elif kind == 1:
+            nseg = max(8, int(round(math.sqrt(t * 3))))
+            nrow = max(1, int(round(t / (2 * nseg))))
+            pool.append(cylinder_mesh(rng.uniform(0.025, 0.045), rng.uniform(0.08, 0.15), nseg, nrow,
+                                      colour_wheel(rng.uniform(), 0.7, 0.9, 0.12), name=f"cylinder_{t}"))
+        else:
+            q = max(1, int(round(math.sqrt(t / 12))))
+            pool.append(box_mesh(*rng.uniform(0.04, 0.10, size=3), q, q, q, name=f"box_{t}"))
+    return pool
+
+
+def batched_scenes(seed=1004, n_scenes=64, W=320, H=240, hyp_range=(500, 40000), max_objects=6,
+                   pool=None):
+    """Scenes of uneven size for the batched form: 1-6 objects each (meshes from a
+    shared pool of 500-30k triangles), 6-DoF ground truth, labels and ROIs from
+    perturbed masks (ROI clamped to 64x64 .. 320x240 around the mask), and a
+    per-scene hypothesis budget drawn from hyp_range, split over the objects."""
+    rng = np.random.default_rng(seed)
+    pool = pool if pool is not None else mesh_pool()
+    f = 615.0 * W / 640.0
+    cx, cy = W / 2.0, H / 2.0
+    out = []
+    for sidx in range(n_scenes):
+        k = int(rng.integers(1, max_objects + 1))
+        picks = rng.choice(len(pool), size=k, replace=True)
+        meshes = [pool[i] for i in picks]
+        objs, gts = [], []
+        for j, m in enumerate(meshes):
+            zc = rng.uniform(0.45, 0.9)
+            u = rng.uniform(0.2 * W, 0.8 * W)
+            v = rng.uniform(0.2 * H, 0.8 * H)
+            r = random_rotation(rng)
+            c_cam = np.array([(u - cx) / f * zc, (v - cy) / f * zc, zc])
+            t = c_cam - r @ np.array([0.0, 0.0, m.vol_height / 2])
+            gts.append(pose_rows(r, t))
+            objs.append((m, r, t, j))
+        z, rgbf, labels = raycast(W, H, f, f, cx, cy, objs, ("wall", 1.2, (100.0, 110.0, 105.0)))
+        depth = quantise_depth(z, rng, 0.002)
+        lab = np.full((H, W), -1, np.int32)
+        rois = []
+        for j in range(k):
+            mk = _dilate(labels == j, int(rng.integers(0, 3)))
+            lab[mk] = j
+            ys, xs = np.nonzero(mk)
+            if len(xs) == 0:
+                xs, ys = np.array([W // 2]), np.array([H // 2])
+            u0, u1, v0, v1 = xs.min(), xs.max() + 1, ys.min(), ys.max() + 1
+            w = int(np.clip(u1 - u0, 64, 320))
+            h = int(np.clip(v1 - v0, 64, 240))
+            uc, vc = (u0 + u1) // 2, (v0 + v1) // 2
+            ru0 = int(np.clip(uc - w // 2, 0, W - w))
+            rv0 = int(np.clip(vc - h // 2, 0, H - h))
+            rois.append((ru0, rv0, ru0 + w, rv0 + h))
+        budget = int(rng.integers(hyp_range[0], hyp_range[1] + 1))
+        share = np.maximum(1, rng.multinomial(budget - k, np.ones(k) / k) + 1)
+        reqs = []
+        for j in range(k):
+            g = gts[j].reshape(3, 4)
+            n = int(share[j])
+            axes = rng.normal(size=(n, 3))
+            th = np.radians(rng.normal(0.0, 15.0, size=n))
+            rot = rodrigues_batch(axes, th) @ g[:, :3]
+            trans = g[:, 3][None, :] + rng.normal(0.0, 0.02, size=(n, 3))
+            poses = np.concatenate([rot, trans[:, :, None]], axis=2).reshape(n, 12)
+            reqs.append(Request(j, j, rois[j], poses.astype(np.float32)))
+        params = Params(delta_m=0.01, tau_c=12.5, color_check=1, occ_margin_units=100)
+        out.append(Scene(f"batched_{sidx}", W, H, f, f, cx, cy, depth, _u8(rgbf), lab, params, meshes,
+                         reqs, gts))
+    return out
 
 
 WORKLOADS = {

@@ -249,6 +249,56 @@ PERCH_API perch_status perch_autotune(perch_ctx *ctx, const perch_work_item *ite
                                       const float *poses, int32_t *costs, int32_t *threads,
                                       int32_t *zbuf_words);
 
+/* ---- served form -----------------------------------------------------------
+ * A continuous-batching server on a context: requests (one search each: a
+ * scene, a mesh and its pose hypotheses) are queued as they arrive; a
+ * scheduler thread packs the queued requests into launches of the batched
+ * scorer whenever one of `slots` launch slots is free, so requests that
+ * arrive while others are on the GPU join the next launch and launches overlap
+ * on the device (each slot has its own scratch and stream).  Scenes and meshes
+ * stay resident in the context; each slot's device staging for
+ * max_batch_hypotheses poses and costs is allocated at start-up and charged
+ * to the context's HBM budget, so admission is bounded by that budget.
+ * While a server runs, the context may be used only through the server calls. */
+typedef struct perch_server perch_server;
+
+typedef struct perch_server_config {
+    int32_t slots;                 /* launches in flight, >= 1 (2 is typical) */
+    int64_t max_batch_hypotheses;  /* hypotheses per launch; a larger request is refused */
+    int32_t max_wait_us;           /* a free slot waits at most this long for more requests
+                                      when fewer than max_batch_hypotheses are queued (0: none) */
+} perch_server_config;
+
+typedef struct perch_request {
+    int32_t scene_id;
+    int32_t mesh_id;
+    int32_t label;                 /* as in perch_score_hypotheses */
+    int32_t roi[4];                /* u1 <= u0 or v1 <= v0: the whole image */
+    const float *poses;            /* HOST, n*12; copied by perch_submit */
+    int64_t n;                     /* >= 1 */
+    int32_t *costs;                /* HOST, n*2; written before the ticket completes and
+                                      must stay valid until then */
+} perch_request;
+
+/* Start a server.  PERCH_E_BUDGET when the slots' staging does not fit the budget. */
+PERCH_API perch_status perch_server_start(perch_ctx *ctx, const perch_server_config *cfg,
+                                          perch_server **out);
+/* Queue a request; *ticket identifies it.  PERCH_E_BUDGET if n exceeds
+ * max_batch_hypotheses, PERCH_E_NOTFOUND for unknown ids, PERCH_E_INVALID for
+ * bad arguments, PERCH_E_BUSY once the server is stopping. */
+PERCH_API perch_status perch_submit(perch_server *srv, const perch_request *req, uint64_t *ticket);
+/* PERCH_OK if the request completed, PERCH_E_BUSY if still queued or running,
+ * the request's error otherwise (PERCH_E_NOTFOUND for an unknown ticket). */
+PERCH_API perch_status perch_poll(perch_server *srv, uint64_t ticket);
+/* Wait for a ticket at most timeout_us microseconds (< 0: no limit);
+ * PERCH_E_TIMEOUT when the limit runs out. */
+PERCH_API perch_status perch_wait(perch_server *srv, uint64_t ticket, int64_t timeout_us);
+/* Steady-clock times (ns) of submission and completion of a finished ticket. */
+PERCH_API perch_status perch_ticket_times(perch_server *srv, uint64_t ticket, int64_t *submit_ns,
+                                          int64_t *done_ns);
+/* Finish every queued request, stop the threads and free the server. */
+PERCH_API perch_status perch_server_stop(perch_server *srv);
+
 /* Debug view of the rasteriser used by perch_score_hypotheses: the z-buffer of
  * one pose as 64-bit keys (depth << 32) | triangle id, 0xFFFFFFFFFFFFFFFF where
  * nothing is covered.  keys is a HOST buffer of W*H uint64 of the scene; the

@@ -27,7 +27,8 @@ EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_
            "perch_release_scene", "perch_score_hypotheses", "perch_best", "perch_set_launch_config",
            "perch_debug_render_keys", "perch_best_noalloc", "perch_score_batch",
            "perch_batch_graph_create", "perch_batch_graph_launch", "perch_batch_graph_destroy",
-           "perch_autotune")
+           "perch_autotune", "perch_server_start", "perch_submit", "perch_poll", "perch_wait",
+           "perch_ticket_times", "perch_server_stop")
 
 
 class PerchError(RuntimeError):
@@ -51,6 +52,76 @@ def work_items(specs):
             arr[i].roi[k] = int(r[k])
         arr[i].pose_offset, arr[i].n = int(off), int(n)
     return arr
+
+
+class perch_server_config(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("max_batch_hypotheses", C.c_int64), ("max_wait_us", C.c_int32)]
+
+
+class perch_request(C.Structure):
+    _fields_ = [("scene_id", C.c_int32), ("mesh_id", C.c_int32), ("label", C.c_int32),
+                ("roi", C.c_int32 * 4), ("poses", C.c_void_p), ("n", C.c_int64), ("costs", C.c_void_p)]
+
+
+class Server:
+    """A continuous-batching server on a Context (perch_server_* calls).
+
+    submit() copies the poses and returns (ticket, costs array); the costs are
+    valid once wait(ticket) returns."""
+
+    def __init__(self, ctx, slots=2, max_batch_hypotheses=1 << 17, max_wait_us=0):
+        self.ctx = ctx
+        cfg = perch_server_config(slots, max_batch_hypotheses, max_wait_us)
+        self.h = C.c_void_p()
+        st = load().perch_server_start(ctx.ctx, C.byref(cfg), C.byref(self.h))
+        if st != PERCH_OK:
+            raise PerchError(st, perch_last_error(ctx.ctx))
+        self._keep = {}
+
+    def submit(self, scene_id, mesh_id, label, roi, poses):
+        p = np.ascontiguousarray(poses, np.float32)
+        n = p.size // 12
+        costs = np.zeros((n, 2), np.int32)
+        r = perch_request()
+        r.scene_id, r.mesh_id, r.label = scene_id, mesh_id, label
+        rr = roi if roi is not None else (0, 0, 0, 0)
+        for k in range(4):
+            r.roi[k] = int(rr[k])
+        r.poses, r.n, r.costs = p.ctypes.data, n, costs.ctypes.data
+        t = C.c_uint64()
+        st = load().perch_submit(self.h, C.byref(r), C.byref(t))
+        if st != PERCH_OK:
+            raise PerchError(st, "perch_submit")
+        self._keep[t.value] = costs
+        return t.value, costs
+
+    def poll(self, ticket):
+        return load().perch_poll(self.h, ticket)
+
+    def wait(self, ticket, timeout_us=-1):
+        st = load().perch_wait(self.h, ticket, timeout_us)
+        if st != PERCH_OK:
+            raise PerchError(st, "perch_wait")
+        return self._keep.pop(ticket)
+
+    def times(self, ticket):
+        a = C.c_int64()
+        b = C.c_int64()
+        st = load().perch_ticket_times(self.h, ticket, C.byref(a), C.byref(b))
+        if st != PERCH_OK:
+            raise PerchError(st, "perch_ticket_times")
+        return a.value, b.value
+
+    def stop(self):
+        if self.h is not None and self.h.value:
+            load().perch_server_stop(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
 
 
 class perch_params(C.Structure):
@@ -94,6 +165,12 @@ def load(path: str | None = None):
         "perch_batch_graph_launch": ([P, P], I32),
         "perch_batch_graph_destroy": ([P], I32),
         "perch_autotune": ([P, P, I32, P, P, P, P], I32),
+        "perch_server_start": ([P, P, P], I32),
+        "perch_submit": ([P, P, P], I32),
+        "perch_poll": ([P, U64], I32),
+        "perch_wait": ([P, U64, I64], I32),
+        "perch_ticket_times": ([P, U64, P, P], I32),
+        "perch_server_stop": ([P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

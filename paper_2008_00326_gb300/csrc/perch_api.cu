@@ -1174,7 +1174,6 @@ void serve_schedule(perch_server* S)
             total += r->n;
         }
         slot.busy = true;
-        S->in_flight.push_back(si);
         lk.unlock();
 
         std::vector<perch::Job> jobs;
@@ -1203,6 +1202,8 @@ void serve_schedule(perch_server* S)
         if (st != PERCH_OK)
             for (auto& r : slot.reqs) r->status = st;
         lk.lock();
+        // hand the slot to the completion thread only once its event is recorded
+        S->in_flight.push_back(si);
         S->cv_done.notify_all();
     }
     std::lock_guard<std::mutex> lk(S->mu);

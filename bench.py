@@ -50,6 +50,7 @@ def _args():
     ap.add_argument("--grid-half", type=int, default=21, help="positions per axis = 2*g+1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served legs")
     return ap.parse_args()
 
 
@@ -182,6 +183,127 @@ def reference_arm(a):
     }))
 
 
+def batched_leg(P, torch, dev, n_scenes=64):
+    """64 scenes of uneven size: per-scene launches vs one batched launch vs a
+    replayed CUDA graph, after the autotuner picked the launch shape."""
+    from paper_2008_00326_gb300 import scenes
+    batch = scenes.batched_scenes(n_scenes=n_scenes)
+    ctx = P.Context(dev.index or 0)
+    mesh_ids, specs, poses, off = {}, [], [], 0
+    for sc in batch:
+        sid = ctx.set_observation(sc)
+        for req in sc.requests:
+            m = sc.meshes[req.mesh_index]
+            if id(m) not in mesh_ids:
+                mesh_ids[id(m)] = ctx.load_mesh(m)
+            specs.append((sid, mesh_ids[id(m)], req.label, req.roi, off, len(req.poses)))
+            poses.append(req.poses)
+            off += len(req.poses)
+    n = off
+    items = P.work_items(specs)
+    dp = torch.from_numpy(np.concatenate(poses)).to(dev)
+    dc = torch.zeros((n, 2), dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(dev)
+    threads, zbuf = P.perch_autotune(ctx.ctx, items, dp, dc)
+
+    def timed(fn, reps=3):
+        best = float("inf")
+        with torch.cuda.stream(s):
+            fn()
+            s.synchronize()
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                fn()
+                e1.record(s)
+                s.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def per_scene():
+        for (sid, mid, label, roi, o, k) in specs:
+            P.perch_score_hypotheses(ctx.ctx, sid, mid, label, roi, dp[o:o + k], dc[o:o + k], s)
+
+    t_plain = timed(per_scene)
+    ref = dc.clone()
+    t_batch = timed(lambda: P.perch_score_batch(ctx.ctx, items, dp, dc, stream=s))
+    same = bool(torch.equal(ref, dc))
+    g = P.perch_batch_graph_create(ctx.ctx, items, dp, dc)
+    t_graph = timed(lambda: P.perch_batch_graph_launch(ctx.ctx, g, s))
+    same = same and bool(torch.equal(ref, dc))
+    P.perch_batch_graph_destroy(g)
+    ctx.close()
+    return {"workload": f"{n_scenes} scenes 320x240, 1-6 objects from a 500-30k triangle mesh pool, "
+                        f"ROI 64x64..320x240, 500-40k hypotheses per scene, colour on",
+            "items": len(specs), "hypotheses": n, "autotuned": {"threads": threads, "zbuf_words": zbuf},
+            "per_scene_launches": {"ms": t_plain, "hyp_s": n / t_plain * 1e3, "launches": len(specs)},
+            "batched_launch": {"ms": t_batch, "hyp_s": n / t_batch * 1e3},
+            "graph_replay": {"ms": t_graph, "hyp_s": n / t_graph * 1e3},
+            "identical_costs": same}
+
+
+def served_leg(P, dev, rates=(5, 20, 50, 100, 200), max_requests=120, window_s=2.0, seed=9):
+    """Poisson request traces mixing the three workloads; serial plain path vs
+    the continuous-batching server.  Latency = submission (arrival) to results."""
+    import threading
+    from paper_2008_00326_gb300 import scenes
+    ctx = P.Context(dev.index or 0)
+    kinds = []
+    for sc in (scenes.tabletop_small(), scenes.tabletop_3obj(), scenes.sixdof_5obj()):
+        sid = ctx.set_observation(sc)
+        mids = [ctx.load_mesh(m) for m in sc.meshes]
+        kinds.append([(sid, mids[r.mesh_index], r.label, r.roi, r.poses) for r in sc.requests])
+    rng = np.random.default_rng(seed)
+    out = []
+    for rate in rates:
+        n = int(min(max_requests, max(10, rate * window_s)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        trace = []
+        for _ in range(n):
+            group = kinds[int(rng.integers(0, 3))]
+            trace.append(group[int(rng.integers(0, len(group)))])
+        hyps = sum(len(t[4]) for t in trace)
+        # serial plain path: requests scored one at a time in arrival order
+        lat = []
+        t0 = time.perf_counter()
+        for at, req in zip(arrivals, trace):
+            now = time.perf_counter() - t0
+            if now < at:
+                time.sleep(at - now)
+            ctx.score(*req)
+            lat.append(time.perf_counter() - t0 - at)
+        span_plain = time.perf_counter() - t0
+        # served: submitted at arrival, continuous batching
+        srv = P.Server(ctx, slots=2, max_batch_hypotheses=1 << 16, max_wait_us=0)
+        tickets = []
+        t0 = time.perf_counter()
+        for at, req in zip(arrivals, trace):
+            now = time.perf_counter() - t0
+            if now < at:
+                time.sleep(at - now)
+            tickets.append(srv.submit(*req)[0])
+        for t in tickets:
+            srv.wait(t)
+        span_served = time.perf_counter() - t0
+        slat = []
+        for t in tickets:
+            a_ns, b_ns = srv.times(t)
+            slat.append((b_ns - a_ns) / 1e9)
+        srv.stop()
+
+        def stats(v, span):
+            v = np.sort(np.asarray(v)) * 1e3
+            return {"p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99)),
+                    "hyp_s": hyps / span}
+        out.append({"rate_req_s": rate, "requests": n, "hypotheses": hyps,
+                    "plain_serial": stats(lat, span_plain), "served": stats(slat, span_served)})
+    ctx.close()
+    return {"mix": "uniform over tabletop_small (968 hyp), one tabletop_3obj object (29,584 hyp), "
+                   "one sixdof_5obj object (4,096 hyp); scenes resident",
+            "server": {"slots": 2, "max_batch_hypotheses": 1 << 16}, "rates": out}
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -303,6 +425,12 @@ def main():
             dist.destroy_process_group()
         return
 
+    # ---- batched and served forms (rank 0, N = 1)
+    batched = served = None
+    if not a.no_forms and world == 1:
+        batched = batched_leg(P, torch, dev)
+        served = served_leg(P, dev)
+
     # ---- CPU oracle baseline and the roofline's algorithmic work
     cpu, work = (None, None)
     if not a.no_cpu_baseline and world == 1:
@@ -342,6 +470,8 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "kernel_ms_per_step": score_total_ms,
+        "batched": batched,
+        "served": served,
     }
     print(json.dumps(out))
     ctx.close()

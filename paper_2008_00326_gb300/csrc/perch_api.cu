@@ -370,6 +370,7 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
     long long acc = 0;
     for (size_t i = 0; i < jobs.size(); ++i) ends[i] = (acc += jobs[i].n);
     perch::ScoreArgs a{};
+    a.job0 = jobs[0];
     a.jobs = (const perch::Job*)S.dev;
     a.job_end = (const long long*)((char*)S.dev + jb);
     a.n_jobs = (int)jobs.size();
@@ -382,7 +383,7 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
     a.vcache = (unsigned long long*)X.vcache;
     a.vstride = vstride;
     e = cudaStreamWaitEvent(st, X.last, 0);
-    if (!e) e = cudaMemcpyAsync(S.dev, S.host, bytes, cudaMemcpyHostToDevice, st);
+    if (!e && jobs.size() > 1) e = cudaMemcpyAsync(S.dev, S.host, bytes, cudaMemcpyHostToDevice, st);
     if (!e) e = cudaEventRecord(S.done, st);
     if (!e) e = perch::launch_score(a, cfg, grid, st);
     if (!e) e = cudaEventRecord(X.last, st);
@@ -953,6 +954,7 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
     if (st == PERCH_OK && !e) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (st == PERCH_OK && !e) {
         perch::ScoreArgs a{};
+        a.job0 = jobs[0];
         a.jobs = (const perch::Job*)G->table;
         a.job_end = (const long long*)((char*)G->table + jb);
         a.n_jobs = (int)jobs.size();

@@ -50,7 +50,8 @@ struct Job {
 // One scoring launch over a list of work items.  Hypothesis h of the launch
 // belongs to the first job j with h < job_end[j].
 struct ScoreArgs {
-    const Job* jobs;          // n_jobs (device)
+    Job job0;                 // the job of a single-job launch (read from the parameter bank)
+    const Job* jobs;          // n_jobs (device); unused when n_jobs == 1
     const long long* job_end; // n_jobs inclusive prefix sums of Job::n (device)
     int n_jobs;
     long long n;              // total hypotheses

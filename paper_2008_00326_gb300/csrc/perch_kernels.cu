@@ -1048,8 +1048,10 @@ __host__ __device__ inline SmemLayout smem_layout(int zcap_words, int mark_words
 }
 
 // Persistent scoring kernel: each block repeatedly takes the next hypothesis
-// index from a device counter (zero at launch) and scores it.
-template <int NT>
+// index from a device counter (zero at launch) and scores it.  SINGLE: one job,
+// read from the kernel parameters; otherwise the job holding the hypothesis is
+// found in the job table and copied to shared memory.
+template <int NT, bool SINGLE>
 __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1068,6 +1070,16 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.stage = reinterpret_cast<TriStage*>(smem + L.probe);
     S.next_batch = &s_next;
     unsigned long long* vc = a.vcache ? a.vcache + (size_t)blockIdx.x * a.vstride : nullptr;
+    if (SINGLE) {
+        for (;;) {
+            if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.next, 1u);
+            __syncthreads();
+            const long long h = s_h;
+            if (h >= a.n) break;
+            score_one<NT>(a, a.job0, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+        }
+        return;
+    }
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1098,16 +1110,16 @@ size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
     return smem_layout(cfg.zcap_words, mark_words, cfg.threads).total;
 }
 
-template <int NT>
+template <int NT, bool SINGLE>
 static int score_grid_nt(size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(k_score<NT, SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT>, NT, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT, SINGLE>, NT, smem) != cudaSuccess)
         return -1;
     return max(1, per) * max(1, sms);
 }
@@ -1115,23 +1127,27 @@ static int score_grid_nt(size_t smem)
 int score_grid(const ScoreConfig& cfg, int mark_words)
 {
     size_t smem = score_smem_bytes(cfg, mark_words);
+    int g1, g2;
     switch (cfg.threads) {
-    case 128: return score_grid_nt<128>(smem);
-    case 512: return score_grid_nt<512>(smem);
-    default: return score_grid_nt<256>(smem);
+    case 128: g1 = score_grid_nt<128, true>(smem); g2 = score_grid_nt<128, false>(smem); break;
+    case 512: g1 = score_grid_nt<512, true>(smem); g2 = score_grid_nt<512, false>(smem); break;
+    default: g1 = score_grid_nt<256, true>(smem); g2 = score_grid_nt<256, false>(smem); break;
     }
+    return min(g1, g2);
 }
 
 template <int NT>
 static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s)
 {
     size_t smem = score_smem_bytes(cfg, a.mark_words);
-    cudaError_t e = cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const bool single = a.n_jobs == 1;
+    cudaError_t e = single ? cudaFuncSetAttribute(k_score<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                           : cudaFuncSetAttribute(k_score<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.next, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     int g = (int)(a.n < grid ? a.n : grid);
-    k_score<NT><<<g, NT, smem, s>>>(a);
+    if (single) k_score<NT, true><<<g, NT, smem, s>>>(a);
+    else k_score<NT, false><<<g, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -433,6 +433,7 @@ __device__ __forceinline__ void zmin(uint32_t* zbuf, int idx, unsigned d, int tr
 // ---- resolve queue and per-warp cell groups -------------------------------
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
+constexpr int kChunk = 4;         // consecutive hypotheses a block takes per counter fetch
 constexpr int kGroups = 1;        // distinct query cells looked up together per warp
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
@@ -1071,12 +1072,16 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.next_batch = &s_next;
     unsigned long long* vc = a.vcache ? a.vcache + (size_t)blockIdx.x * a.vstride : nullptr;
     if (SINGLE) {
+        // kChunk consecutive hypotheses per fetch: neighbouring poses touch the
+        // same observed cells, so the block's L1 keeps serving them
         for (;;) {
-            if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.next, 1u);
+            if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.next, (unsigned)kChunk);
             __syncthreads();
-            const long long h = s_h;
-            if (h >= a.n) break;
-            score_one<NT>(a, a.job0, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+            const long long h0 = s_h;
+            if (h0 >= a.n) break;
+            const long long h1 = min(h0 + kChunk, a.n);
+            for (long long h = h0; h < h1; ++h)
+                score_one<NT>(a, a.job0, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
         }
         return;
     }

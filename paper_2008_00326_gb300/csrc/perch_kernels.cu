@@ -433,7 +433,7 @@ __device__ __forceinline__ void zmin(uint32_t* zbuf, int idx, unsigned d, int tr
 // ---- resolve queue and per-warp cell groups -------------------------------
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
-constexpr int kChunk = 4;         // consecutive hypotheses a block takes per counter fetch
+constexpr int kChunk = 1;         // consecutive hypotheses a block takes per counter fetch (measured: 1 is best)
 constexpr int kGroups = 1;        // distinct query cells looked up together per warp
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search

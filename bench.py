@@ -38,7 +38,36 @@ if ROOT not in sys.path:
 
 METRIC = "hypotheses rendered+scored/s"
 UNIT = "hypotheses/s"
-FP32_OPS_PER_TEST = 8      # 3 sub, 3 mul, 2 add per squared distance
+# Algorithmic 32-bit ALU operations per unit of work (counted from the
+# definitions the path evaluates; the unit counts come from the oracle):
+OPS = {
+    "vertex": 27,      # R v + t (9 mul, 9 add), two divisions, projection and snap (6), 1/Z
+    "triangle": 11,    # doubled area, orientation, pixel box
+    "fragment": 27,    # three edge functions (15) and the depth (12) of a covered sample
+    "kept": 186,       # back-projection (10), colour (21), CIELAB (35), CIEDE2000 (120)
+    "candidate": 8,    # squared distance: 3 sub, 3 mul, 2 add
+    "in_volume": 34,   # back-projection and the inscribed-cylinder test of an observed point
+}
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_score_tabletop_3obj_traffic.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2008_00326_gb300", "csrc", "perch_kernels.cu")
+
+
+def measured_traffic():
+    """DRAM bytes per k_score launch from the committed ncu capture, or None when
+    the kernel source has changed since it was taken."""
+    import hashlib
+    try:
+        text = open(PROFILE_TRAFFIC).read()
+        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and not line.startswith("#"))
+    if fields.get("kernel_source_sha256", "").strip() != src:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def _args():
@@ -134,7 +163,7 @@ def cpu_baseline(sc, seconds, rng_seed=0):
             _, _, w = O.score(osc, om, req.poses[pick], label=req.label, roi=req.roi, with_work=True)
             total_t += time.perf_counter() - t0
             total_h += len(pick)
-            work.append(w)
+            work.append(np.concatenate([w, np.full((len(w), 1), req.mesh_index, np.int64)], axis=1))
         rounds += 1
         if time.perf_counter() >= deadline:
             break
@@ -443,17 +472,24 @@ def main():
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak_ops = 152 * 128 * sm_max * 1e6
     if work is not None:
-        cand_per_hyp = float(work[:, 5].mean())
-        ops = cand_per_hyp * n_step * FP32_OPS_PER_TEST
-        achieved = ops / (score_total_ms / 1000.0)
+        w_obj, ops_step, mean = work, 0.0, {}
+        for k, r in enumerate(reqs):
+            wk = w_obj[w_obj[:, 8] == k] if w_obj.shape[1] > 8 else w_obj
+            T, F, L, C, IV = (float(wk[:, i].mean()) for i in (0, 2, 4, 5, 6))
+            V = float(sc.meshes[r.mesh_index].verts.shape[0])
+            per_h = (OPS["vertex"] * V + OPS["triangle"] * T + OPS["fragment"] * F + OPS["kept"] * L
+                     + OPS["candidate"] * C + OPS["in_volume"] * IV)
+            ops_step += per_h * len(r.poses)
+            mean[k] = {"vertices": V, "tri_setups": T, "fragments": F, "kept_points": L,
+                       "cell_candidates": C, "in_volume": IV, "ops": per_h}
+        achieved = ops_step / (score_total_ms / 1000.0)
+        traffic = measured_traffic()
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_ops,
+                "traffic": None if traffic is None else traffic,
                 "kernel": "k_score (fused raster + resolve + 27-cell radius search + J_o)",
-                "work_per_hypothesis": {"cell_candidates": cand_per_hyp,
-                                        "kept_points": float(work[:, 4].mean()),
-                                        "fragments": float(work[:, 2].mean()),
-                                        "tri_setups": float(work[:, 0].mean())},
-                "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock)"}
+                "ops_per_unit": OPS, "work_per_hypothesis_by_object": mean,
+                "peak_basis": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz (max SM clock)"}
     lat = sorted(obj_lat)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,

@@ -443,9 +443,8 @@ struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its r
 
 // Per-warp scratch of the radius search (shared memory).
 struct __align__(16) WarpProbe {
-    int2 runs[kGroups][27];       // per group: non-empty runs of its 27 cells as (start, count)
+    int2 runs[kGroups][27];       // per group: non-empty runs as (start - first pair index, end pair index)
     int total[kGroups];           // per group: candidates in its 27 cells
-    int nruns[kGroups];           // per group: non-empty runs
     unsigned mask[kGroups];       // per group: lanes whose query lies in the group's cell
     unsigned char qlist[kGroups][32];  // per group: the lanes of its queries, in lane order
     float4 q[32];                 // query of each lane
@@ -509,9 +508,9 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
         }
         const unsigned nonempty = __ballot_sync(0xffffffffu, cnt != 0);
         if (cnt != 0)
-            W.runs[g][__popc(nonempty & ((1u << lane) - 1u))] = make_int2((int)start, (int)cnt);
+            W.runs[g][__popc(nonempty & ((1u << lane) - 1u))] =
+                make_int2((int)start - (int)(incl - cnt), (int)incl);
         if (lane == 26) W.total[g] = (int)incl;
-        if (lane == 0) W.nruns[g] = __popc(nonempty);
     }
 }
 
@@ -575,23 +574,16 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
                 const int ql = W.qlist[g][lane / k];
                 const float4 q = W.q[ql];
                 unsigned long long local = kEmptyKey;
-                const int j = lane % k;
-                const int nr = W.nruns[g];
-                // runs outer, points inner: the inner trip count is known, so
-                // consecutive candidate loads are independent and overlap
-                for (int r = 0; r < nr; ++r) {
-                    const int2 run = W.runs[g][r];
-                    const float4* base = sc.pts + run.x;
-#pragma unroll 2
-                    for (int i = j; i < run.y; i += k) {
-                        const float4 c = __ldg(base + i);
-                        float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
-                        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-                        if (d2 <= sc.delta2) {
-                            unsigned long long key =
-                                ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
-                            local = key < local ? key : local;
-                        }
+                int r = 0;
+                for (int ci = lane % k; ci < T; ci += k) {
+                    while (W.runs[g][r].y <= ci) ++r;
+                    const float4 c = __ldg(&sc.pts[W.runs[g][r].x + ci]);
+                    float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
+                    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+                    if (d2 <= sc.delta2) {
+                        unsigned long long key =
+                            ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
+                        local = key < local ? key : local;
                     }
                 }
                 if (local != kEmptyKey) atomicMin(&W.best[ql], local);

@@ -71,6 +71,9 @@ typedef int32_t perch_status;
  *                    an occluded one (in C_K, Eq. 3) iff the observed depth
  *                    d_obs > 0 and d_obs + m < d (and, when scoring by label,
  *                    the pixel's label differs from the object's, Sec. V-C).
+ *                    -1 turns occluder marking off, which is the variant
+ *                    PERCH 2.0-A of Sec. VI-A (rendered points are never
+ *                    removed by the observed depth).
  *   z_near_m         triangles with a vertex nearer than this are culled.
  *   jo_mode          0: J_o from nearest-neighbour marks (Sec. IV-A). Others reserved. */
 typedef struct perch_params {

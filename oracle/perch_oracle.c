@@ -61,7 +61,7 @@ typedef struct {
     float tau_c;              /* CIEDE2000 threshold                        */
     int32_t color_check;      /* 0/1                                        */
     int32_t stride;           /* image-space downsampling factor s >= 1     */
-    int32_t occ_margin;       /* occluder margin m, 0.1 mm units            */
+    int32_t occ_margin;       /* occluder margin m, 0.1 mm; < 0: no occluder marking (2.0-A) */
     float z_near;             /* metres                                     */
 } or_scene;
 
@@ -386,7 +386,7 @@ int64_t or_rendered_points(const or_scene *sc, const or_mesh *m, const float pos
             int32_t t = (int32_t)(key & 0xffffffffu);
             /* C6: occluders -- the observed surface is nearer by more than m */
             int64_t dobs = sc->depth[i];
-            if (dobs > 0 && dobs + sc->occ_margin < d &&
+            if (sc->occ_margin >= 0 && dobs > 0 && dobs + sc->occ_margin < d &&
                 (label < 0 || sc->labels == NULL || sc->labels[i] != label))
                 continue;
             or_tri o;

@@ -569,7 +569,7 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
         return fail(c, PERCH_E_INVALID, "perch_set_observation: bad intrinsics");
     const perch_params& p = *params;
     if (!finite(p.delta_m) || p.delta_m < 1e-4f || p.delta_m > 1.0f || !finite(p.tau_c) || p.tau_c < 0 ||
-        (p.color_check != 0 && p.color_check != 1) || p.stride < 1 || p.occ_margin_units < 0 ||
+        (p.color_check != 0 && p.color_check != 1) || p.stride < 1 || p.occ_margin_units < -1 ||
         !finite(p.z_near_m) || p.z_near_m <= 0 || p.jo_mode != 0)
         return fail(c, PERCH_E_INVALID, "perch_set_observation: parameters out of range");
     const float cell = p.delta_m * perch::kCellGrow;

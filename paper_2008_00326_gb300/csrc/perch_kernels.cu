@@ -857,7 +857,8 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                         if (tri >= 0) {
                             int pix = v * sc.W + u;
                             unsigned dobs = __ldg(&sc.depth[pix]);
-                            bool occluded = dobs > 0 && (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
+                            bool occluded = sc.occ_margin >= 0 && dobs > 0 &&
+                                            (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
                                             (J.label < 0 || __ldg(&sc.labels[pix]) != J.label);
                             if (!occluded) {
                                 TriSetup o;

@@ -135,6 +135,17 @@ def test_sixdof_reduced_labels(ctx, oracle, mark_bits):
         ctx.set_launch_config(256, 8192)
 
 
+def test_variant_without_occluder_marking(ctx, oracle):
+    """PERCH 2.0-A: occluder marking off (occ_margin_units = -1)."""
+    sc = scenes.tabletop_3obj(W=320, H=240, grid_half=3, n_yaw=4, tri_scale=0.25)
+    sc.params.occ_margin_units = -1
+    sid, mids = _load(ctx, sc)
+    for req in sc.requests:
+        got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
+        want, band = oracle.score(*_oracle(oracle, sc, req), req.poses, label=req.label, roi=req.roi)
+        assert_within_band(got, want, band, f"2.0-A mesh {req.mesh_index}")
+
+
 @pytest.mark.parametrize("stride", [2, 3])
 def test_stride(ctx, oracle, stride):
     sc = scenes.tabletop_small()

@@ -169,6 +169,19 @@ def test_occluders_remove_hidden_points(oracle):
     assert tuple(costs[0]) == (0, 0)            # label 3 owns no pixel: V empty, all hidden
 
 
+def test_variant_without_occluder_marking(oracle):
+    """PERCH 2.0-A (Sec. VI-A): with occluder marking off nothing is hidden."""
+    box = scenes.box_mesh(0.06, 0.08, 0.12, 2, 2, 2)
+    om = oracle.OracleMesh.from_mesh(box)
+    pose = _pose(np.eye(3), (0.0, 0.0, 0.5))
+    sc_on = _wall_scene(oracle, 3000, delta=0.01, occ_margin=100)
+    sc_off = _wall_scene(oracle, 3000, delta=0.01, occ_margin=-1)
+    keys, _ = oracle.render_keys(sc_off, om, pose)
+    n_vis = int(np.sum(keys != EMPTY))
+    assert tuple(oracle.score(sc_on, om, pose[None])[0][0]) == (0, 0)
+    assert tuple(oracle.score(sc_off, om, pose[None])[0][0]) == (0, n_vis)
+
+
 def test_admissible_cylinder_count(oracle):
     W, H, f = 64, 48, 60.0
     sc = _wall_scene(oracle, 5000, W=W, H=H, f=f, delta=0.01)

@@ -75,7 +75,12 @@ typedef int32_t perch_status;
  *                    PERCH 2.0-A of Sec. VI-A (rendered points are never
  *                    removed by the observed depth).
  *   z_near_m         triangles with a vertex nearer than this are culled.
- *   jo_mode          0: J_o from nearest-neighbour marks (Sec. IV-A). Others reserved. */
+ *   jo_mode          0: J_o as the J_o kernel of Sec. IV-A computes it -- an observed
+ *                    point of V(O) is an inlier iff it is the nearest neighbour of a
+ *                    rendered point it explains;
+ *                    1: J_o as Eq. 3 writes it with the distance test of Eq. 2 -- an
+ *                    observed point of V(O) is an inlier iff some rendered point of
+ *                    R \ C lies within delta (colour is not used for J_o). */
 typedef struct perch_params {
     float delta_m;
     float tau_c;

@@ -39,7 +39,7 @@ class _Scene(C.Structure):
                 ("cx", C.c_float), ("cy", C.c_float), ("depth", C.c_void_p), ("rgb", C.c_void_p),
                 ("labels", C.c_void_p), ("delta", C.c_float), ("tau_c", C.c_float),
                 ("color_check", C.c_int32), ("stride", C.c_int32), ("occ_margin", C.c_int32),
-                ("z_near", C.c_float)]
+                ("z_near", C.c_float), ("jo_mode", C.c_int32)]
 
 
 class _Mesh(C.Structure):
@@ -80,20 +80,20 @@ class OracleScene:
     """An observation plus scoring parameters, held as contiguous arrays."""
 
     def __init__(self, depth, rgb, labels, fx, fy, cx, cy, delta=0.01, tau_c=12.5,
-                 color_check=0, stride=1, occ_margin=100, z_near=0.05):
+                 color_check=0, stride=1, occ_margin=100, z_near=0.05, jo_mode=0):
         self.depth = np.ascontiguousarray(depth, np.uint16)
         self.rgb = np.ascontiguousarray(rgb, np.uint8)
         self.labels = None if labels is None else np.ascontiguousarray(labels, np.int32)
         H, W = self.depth.shape
         self.W, self.H = W, H
         self.s = _Scene(W, H, fx, fy, cx, cy, _ptr(self.depth), _ptr(self.rgb), _ptr(self.labels),
-                        delta, tau_c, color_check, stride, occ_margin, z_near)
+                        delta, tau_c, color_check, stride, occ_margin, z_near, jo_mode)
 
     @classmethod
     def from_scene(cls, sc, **over):
         p = sc.params
         kw = dict(delta=p.delta_m, tau_c=p.tau_c, color_check=p.color_check, stride=p.stride,
-                  occ_margin=p.occ_margin_units, z_near=p.z_near_m)
+                  occ_margin=p.occ_margin_units, z_near=p.z_near_m, jo_mode=p.jo_mode)
         kw.update(over)
         return cls(sc.depth, sc.rgb, sc.labels, sc.fx, sc.fy, sc.cx, sc.cy, **kw)
 

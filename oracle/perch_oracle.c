@@ -63,6 +63,7 @@ typedef struct {
     int32_t stride;           /* image-space downsampling factor s >= 1     */
     int32_t occ_margin;       /* occluder margin m, 0.1 mm; < 0: no occluder marking (2.0-A) */
     float z_near;             /* metres                                     */
+    int32_t jo_mode;          /* 0: NN marks (Sec. IV-A kernel); 1: Eq. 3 with Eq. 2 */
 } or_scene;
 
 typedef struct {
@@ -523,8 +524,21 @@ int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t 
                     if (!in_volume(sc, m, P, label, roi, Ipix[j], Ixyz + 3 * j))
                         continue;
                     wk[6]++;
-                    if (!mark[j])
+                    if (sc->jo_mode == 1) {
+                        /* Eq. 3 as written, with OUTLIER of Eq. 2: is any rendered
+                         * point of R \ C within delta of p? */
+                        const float *p = Ixyz + 3 * j;
+                        int near = 0;
+                        for (int64_t k = 0; k < L && !near; k++) {
+                            const float *q = Rxyz + 3 * k;
+                            float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
+                            near = ((dx * dx + dy * dy) + dz * dz) <= delta2;
+                        }
+                        if (!near)
+                            Jo++;
+                    } else if (!mark[j]) {
                         Jo++;
+                    }
                 }
                 costs[2 * h] = Jo;
                 costs[2 * h + 1] = Jr;

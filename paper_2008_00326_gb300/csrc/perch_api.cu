@@ -570,7 +570,7 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     const perch_params& p = *params;
     if (!finite(p.delta_m) || p.delta_m < 1e-4f || p.delta_m > 1.0f || !finite(p.tau_c) || p.tau_c < 0 ||
         (p.color_check != 0 && p.color_check != 1) || p.stride < 1 || p.occ_margin_units < -1 ||
-        !finite(p.z_near_m) || p.z_near_m <= 0 || p.jo_mode != 0)
+        !finite(p.z_near_m) || p.z_near_m <= 0 || (p.jo_mode != 0 && p.jo_mode != 1))
         return fail(c, PERCH_E_INVALID, "perch_set_observation: parameters out of range");
     const float cell = p.delta_m * perch::kCellGrow;
     const double zmax = 65535.0 / 10000.0;
@@ -628,6 +628,7 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     d.color_check = p.color_check;
     d.stride = p.stride;
     d.occ_margin = p.occ_margin_units;
+    d.jo_mode = p.jo_mode;
     d.depth = (const uint16_t*)s.depth;
     d.labels = (const int32_t*)s.labels;
     d.lab = (const float4*)s.lab;

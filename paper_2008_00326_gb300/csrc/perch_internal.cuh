@@ -18,10 +18,11 @@ struct DevScene {
     float fx, fy, cx, cy;
     float delta, delta2, cell, tau_c, z_near;
     int color_check, stride, occ_margin;
+    int jo_mode;              // 0: NN marks (Sec. IV-A kernel); 1: Eq. 3 with the Eq. 2 test
     const uint16_t* depth;    // H*W
     const int32_t* labels;    // H*W or nullptr
     const float4* lab;        // H*W: (L, a, b, 0)
-    const float4* pts;        // n_pts, grouped by hash cell: (x, y, z, pixel index bits)
+    const float4* pts;        // n_pts, grouped by hash cell: (x, y, z, (v << 16 | u) bits)
     const uint4* table;       // hash slots: (key lo, key hi, start, count)
     uint32_t table_mask;
     int n_pts;

@@ -295,7 +295,9 @@ __global__ void k_obs_scatter(DevScene sc, const int32_t* slot_of_pixel, const u
     int u = i % sc.W, v = i / sc.W;
     float3 p = back_project(sc, u, v, sc.depth[i]);
     uint32_t pos = start[slot] + atomicAdd(&cursor[slot], 1u);
-    pts[pos] = make_float4(p.x, p.y, p.z, __int_as_float(i));
+    // the pixel as (v << 16 | u): ordered like the index v W + u, and its
+    // coordinates come back without a division
+    pts[pos] = make_float4(p.x, p.y, p.z, __uint_as_float(((uint32_t)v << 16) | (uint32_t)u));
 }
 
 cudaError_t launch_build(const DevScene& sc, const BuildBuffers& b, uint32_t cap,
@@ -524,8 +526,15 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
 // lane's own result: the nearest observed point within delta (smallest FP32
 // squared distance, ties to the lowest pixel index) or kEmptyKey.  All 32
 // lanes must call it.
+// Admissible band of the marks bitset (used by jo_mode 1, where every
+// observed point within delta of a rendered point is marked).
+struct MarkBand {
+    uint32_t* marks;
+    int u0, u1, v0, v1, vw;
+};
+
 __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float qx, float qy,
-                                          float qz, WarpProbe& W, int lane)
+                                          float qz, WarpProbe& W, int lane, const MarkBand& mb)
 {
     int cx = 0, cy = 0, cz = 0;
     unsigned long long key = kEmptyKey;
@@ -584,6 +593,14 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
                         unsigned long long key =
                             ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
                         local = key < local ? key : local;
+                        if (sc.jo_mode == 1) {
+                            const uint32_t pw = __float_as_uint(c.w);
+                            const int pu = (int)(pw & 0xFFFFu), pv = (int)(pw >> 16);
+                            if (pu >= mb.u0 && pu < mb.u1 && pv >= mb.v0 && pv < mb.v1) {
+                                const int bit = (pv - mb.v0) * mb.vw + (pu - mb.u0);
+                                atomicOr(&mb.marks[bit >> 5], 1u << (bit & 31));
+                            }
+                        }
                     }
                 }
                 if (local != kEmptyKey) atomicMin(&W.best[ql], local);
@@ -832,6 +849,7 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
             const int nbx = (nu + 7) / 8, nby = (nv + 3) / 4;
             const int nblocks = nbx * nby;
             KeptPoint* wq = S.kept + warp * kWarpQueue;
+            const MarkBand mband = {S.marks, vbox[0], vbox[2], mv0, mv1, vw};
             int wq_head = 0, wq_count = 0;
             for (;;) {
                 int blk = 0;
@@ -897,19 +915,19 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                     if (valid) kq = wq[(wq_head + lane) % kWarpQueue];
                     wq_head = (wq_head + nb) % kWarpQueue;
                     wq_count -= nb;
-                    const unsigned long long nn = probe_batch(sc, valid, kq.x, kq.y, kq.z, WP, lane);
+                    const unsigned long long nn = probe_batch(sc, valid, kq.x, kq.y, kq.z, WP, lane, mband);
                     if (valid) {
                         bool explained = nn != kEmptyKey;
                         const int pnn = (int)(uint32_t)nn;
+                        const int pu = pnn & 0xFFFF, pv = pnn >> 16;
                         if (explained && sc.color_check) {
-                            float4 lp = __ldg(&sc.lab[pnn]);
+                            float4 lp = __ldg(&sc.lab[pv * sc.W + pu]);
                             float3 lq = srgb8_to_lab(kq.rgb & 255, (kq.rgb >> 8) & 255, (kq.rgb >> 16) & 255);
                             if (ciede2000(lq, make_float3(lp.x, lp.y, lp.z)) > sc.tau_c) explained = false;
                         }
                         if (!explained) {
                             if (count_jr) ++jr_local;
-                        } else {
-                            int pu = pnn % sc.W, pv = pnn / sc.W;
+                        } else if (sc.jo_mode == 0) {
                             if (pu >= vbox[0] && pu < vbox[2] && pv >= mv0 && pv < mv1) {
                                 int bit = (pv - mv0) * vw + (pu - vbox[0]);
                                 atomicOr(&S.marks[bit >> 5], 1u << (bit & 31));

@@ -146,6 +146,27 @@ def test_variant_without_occluder_marking(ctx, oracle):
         assert_within_band(got, want, band, f"2.0-A mesh {req.mesh_index}")
 
 
+@pytest.mark.parametrize("colour", [0, 1])
+def test_eq3_exact_jo(ctx, oracle, colour):
+    """jo_mode 1: J_o as Eq. 3 writes it, with the distance test of Eq. 2."""
+    sc = scenes.tabletop_3obj(W=320, H=240, grid_half=3, n_yaw=4, tri_scale=0.25)
+    sc.params.jo_mode = 1
+    sc.params.color_check = colour
+    sid, mids = _load(ctx, sc)
+    for req in sc.requests:
+        got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
+        want, band = oracle.score(*_oracle(oracle, sc, req), req.poses, label=req.label, roi=req.roi)
+        assert np.array_equal(got[:, 0], want[:, 0])
+        assert_within_band(got, want, band, f"jo_mode 1 mesh {req.mesh_index}")
+    sc6 = scenes.sixdof_5obj(n_hyp=16, W=320, H=240, tri_scale=0.1)
+    sc6.params.jo_mode = 1
+    sid, mids = _load(ctx, sc6)
+    for req in sc6.requests:
+        got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
+        want, band = oracle.score(*_oracle(oracle, sc6, req), req.poses, label=req.label, roi=req.roi)
+        assert np.array_equal(got[:, 0], want[:, 0])
+
+
 @pytest.mark.parametrize("stride", [2, 3])
 def test_stride(ctx, oracle, stride):
     sc = scenes.tabletop_small()

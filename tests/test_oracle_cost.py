@@ -93,6 +93,37 @@ def test_costs_match_kdtree(oracle, small, colour):
             assert abs(got[0] - want[0]) <= amb and abs(got[1] - want[1]) <= amb
 
 
+def test_eq3_jo_matches_kdtree(oracle, small):
+    """jo_mode 1 (Eq. 3 as written, Eq. 2 test): J_o = points of I cap V with
+    no rendered point within delta, checked with scipy's k-d tree."""
+    from scipy.spatial import cKDTree
+    sc = small
+    osc = oracle.OracleScene.from_scene(sc, jo_mode=1, color_check=0)
+    mesh = sc.meshes[0]
+    om = oracle.OracleMesh.from_mesh(mesh)
+    req = sc.requests[0]
+    pick = np.unique(np.concatenate([[req.gt_index], np.arange(0, len(req.poses), 97)]))
+    costs, _ = oracle.score(osc, om, req.poses[pick])
+    costs0, _ = oracle.score(oracle.OracleScene.from_scene(sc, color_check=0), om, req.poses[pick])
+    assert np.array_equal(costs[:, 1], costs0[:, 1])            # J_r does not depend on the mode
+    I, _, _ = oracle.observed_points(osc)
+    for n, h in enumerate(pick):
+        pose = req.poses[h]
+        keys, _ = oracle.render_keys(osc, om, pose)
+        q, _, _ = oracle.rendered_points(osc, om, pose, keys)
+        R = pose.reshape(3, 4)[:, :3].astype(np.float64)
+        t = pose.reshape(3, 4)[:, 3].astype(np.float64)
+        pl = (I.astype(np.float64) - t) @ R
+        inside = ((pl[:, 0] ** 2 + pl[:, 1] ** 2) <= mesh.vol_radius ** 2) & (pl[:, 2] >= 0) & \
+                 (pl[:, 2] <= mesh.vol_height)
+        if len(q):
+            d, _ = cKDTree(q.astype(np.float64)).query(I[inside].astype(np.float64), k=1)
+        else:
+            d = np.full(int(inside.sum()), np.inf)
+        assert np.min(np.abs(d - sc.params.delta_m)) > 1e-6
+        assert costs[n, 0] == int(np.sum(d > sc.params.delta_m)), h
+
+
 def _observation_from_render(oracle, sc, pose):
     """Noise-free observation made by the oracle's own renderer at `pose`."""
     blank = oracle.OracleScene(np.zeros((sc.H, sc.W), np.uint16), np.zeros((sc.H, sc.W, 3), np.uint8),
@@ -117,6 +148,9 @@ def test_ground_truth_pose_is_minimal(oracle):
     costs, band = oracle.score(osc, om, req.poses)
     J = costs.sum(1)
     assert tuple(costs[req.gt_index]) == (0, 0)
+    osc1 = oracle.OracleScene(depth, rgb, None, sc.fx, sc.fy, sc.cx, sc.cy, delta=0.01,
+                              color_check=1, tau_c=12.5, jo_mode=1)
+    assert tuple(oracle.score(osc1, om, req.poses[req.gt_index][None])[0][0]) == (0, 0)
     # with the colour check on, the box's 180-degree twin no longer ties
     assert np.sum(J == 0) == 1
     assert oracle.best(costs) == (req.gt_index, 0)

@@ -533,6 +533,37 @@ struct MarkBand {
     int u0, u1, v0, v1, vw;
 };
 
+// Candidates j, j + k, ... of a group's runs against query q: the minimum
+// (d2 bits << 32 | pixel) within delta, or kEmptyKey.  MARK (jo_mode 1) also
+// marks every observed point within delta that lies in the admissible band.
+template <bool MARK>
+__device__ __forceinline__ unsigned long long scan_candidates(const DevScene& sc, const float4 q,
+                                                              const int2* runs, int T, int j, int k,
+                                                              const MarkBand& mb)
+{
+    unsigned long long local = kEmptyKey;
+    int r = 0;
+    for (int ci = j; ci < T; ci += k) {
+        while (runs[r].y <= ci) ++r;
+        const float4 c = __ldg(&sc.pts[runs[r].x + ci]);
+        float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
+        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+        if (d2 <= sc.delta2) {
+            unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
+            local = key < local ? key : local;
+            if (MARK) {
+                const uint32_t pw = __float_as_uint(c.w);
+                const int pu = (int)(pw & 0xFFFFu), pv = (int)(pw >> 16);
+                if (pu >= mb.u0 && pu < mb.u1 && pv >= mb.v0 && pv < mb.v1) {
+                    const int bit = (pv - mb.v0) * mb.vw + (pu - mb.u0);
+                    atomicOr(&mb.marks[bit >> 5], 1u << (bit & 31));
+                }
+            }
+        }
+    }
+    return local;
+}
+
 __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float qx, float qy,
                                           float qz, WarpProbe& W, int lane, const MarkBand& mb)
 {
@@ -581,28 +612,9 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
             const int k = 32 / G;
             if (lane < G * k) {
                 const int ql = W.qlist[g][lane / k];
-                const float4 q = W.q[ql];
-                unsigned long long local = kEmptyKey;
-                int r = 0;
-                for (int ci = lane % k; ci < T; ci += k) {
-                    while (W.runs[g][r].y <= ci) ++r;
-                    const float4 c = __ldg(&sc.pts[W.runs[g][r].x + ci]);
-                    float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
-                    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-                    if (d2 <= sc.delta2) {
-                        unsigned long long key =
-                            ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(c.w);
-                        local = key < local ? key : local;
-                        if (sc.jo_mode == 1) {
-                            const uint32_t pw = __float_as_uint(c.w);
-                            const int pu = (int)(pw & 0xFFFFu), pv = (int)(pw >> 16);
-                            if (pu >= mb.u0 && pu < mb.u1 && pv >= mb.v0 && pv < mb.v1) {
-                                const int bit = (pv - mb.v0) * mb.vw + (pu - mb.u0);
-                                atomicOr(&mb.marks[bit >> 5], 1u << (bit & 31));
-                            }
-                        }
-                    }
-                }
+                const unsigned long long local =
+                    sc.jo_mode == 1 ? scan_candidates<true>(sc, W.q[ql], W.runs[g], T, lane % k, k, mb)
+                                    : scan_candidates<false>(sc, W.q[ql], W.runs[g], T, lane % k, k, mb);
                 if (local != kEmptyKey) atomicMin(&W.best[ql], local);
             }
         }

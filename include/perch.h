@@ -307,6 +307,34 @@ PERCH_API perch_status perch_ticket_times(perch_server *srv, uint64_t ticket, in
 /* Finish every queued request, stop the threads and free the server. */
 PERCH_API perch_status perch_server_stop(perch_server *srv);
 
+/* ---- 6-DoF pose proposals (Sec. V-B, Eq. 5 and Eq. 6) ------------------------
+ * The hypothesis set H(O) = H_r x H_t of one object, generated on the device:
+ *   H_r: M viewpoints v_i on the unit sphere -- a Fibonacci lattice
+ *        (y_i = 1 - (2i+1)/M, azimuth i times the golden angle), the closest
+ *        thing to M equidistant points -- times N in-plane angles
+ *        theta_k = 2 pi k / N.  v_i is the direction from the object to the
+ *        camera in the object frame; R_view(v_i) turns it onto the camera's
+ *        -z axis (camera right = forward x object z, or x object y when
+ *        forward is parallel to z), and R = Rz(theta_k) R_view(v_i) rotates
+ *        about the optical axis.
+ *   H_t: the centre (uc, vc) of the object's 2-D box back-projected at K
+ *        depths z_j evenly spaced from z_min to z_max (K = 1: their mean),
+ *        z_min / z_max = the nearest / farthest observed depth among pixels of
+ *        the box whose label is `label`; t = c_j - R m, c_j the back-projected
+ *        centre and m the centre of the mesh's bounding box.
+ *   poses receives M*N*K poses (12 float32 each), ordered ((i N + k) K + j).
+ *   bbox = {u0, v0, u1, v1} (half-open, clipped to the image); needs labels.
+ *   z_range (int32[2], may be NULL) receives z_min, z_max in 0.1 mm units
+ *   (both 0 when no pixel of the box carries the label: the poses then sit at
+ *   depth 0 and every triangle is culled).
+ * cuda_stream NULL: poses and z_range are HOST pointers, synchronous;
+ * otherwise DEVICE pointers enqueued on that stream.
+ * Limits: 1 <= M, N, K and M*N*K <= 2^26. */
+PERCH_API perch_status perch_pose_proposals(perch_ctx *ctx, int32_t scene_id, int32_t mesh_id,
+                                            int32_t label, const int32_t *bbox, int32_t M,
+                                            int32_t N, int32_t K, float *poses, int32_t *z_range,
+                                            void *cuda_stream);
+
 /* Debug view of the rasteriser used by perch_score_hypotheses: the z-buffer of
  * one pose as 64-bit keys (depth << 32) | triangle id, 0xFFFFFFFFFFFFFFFF where
  * nothing is covered.  keys is a HOST buffer of W*H uint64 of the scene; the

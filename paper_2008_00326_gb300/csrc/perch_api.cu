@@ -866,6 +866,46 @@ perch_status perch_set_launch_config(perch_ctx* c, int32_t threads, int32_t zbuf
     return PERCH_OK;
 }
 
+perch_status perch_pose_proposals(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t label,
+                                  const int32_t* bbox, int32_t M, int32_t N, int32_t K, float* poses,
+                                  int32_t* z_range, void* cuda_stream)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (!bbox || !poses) return fail(c, PERCH_E_INVALID, "null bbox or poses");
+    if (M < 1 || N < 1 || K < 1 || (long long)M * N * K > (1ll << 26))
+        return fail(c, PERCH_E_INVALID, "proposal counts out of range");
+    auto si = c->scenes.find(scene_id);
+    if (si == c->scenes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown scene %d", scene_id);
+    auto mi = c->meshes.find(mesh_id);
+    if (mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
+    if (label < 0 || !si->second.labels) return fail(c, PERCH_E_INVALID, "proposals need a label and labels");
+    DeviceGuard g(c->device);
+    perch::ProposalArgs a{};
+    a.sc = si->second.ds;
+    a.label = label;
+    clip_roi(c, si->second, bbox, a.box);
+    a.M = M; a.N = N; a.K = K;
+    for (int k = 0; k < 3; ++k) a.centre[k] = 0.5f * (mi->second.dm.lo[k] + mi->second.dm.hi[k]);
+    const long long n = (long long)M * N * K;
+    perch_status st = ensure_stage(c, (size_t)n * 48 + 64);
+    if (st != PERCH_OK) return st;
+    a.zr = (unsigned*)((char*)c->stage + (size_t)n * 48);
+    if (cuda_stream) {
+        a.poses = poses;
+        a.z_out = z_range;
+        cudaError_t e = perch::launch_proposals(a, (cudaStream_t)cuda_stream);
+        return e ? cuda_fail(c, e, "perch_pose_proposals") : PERCH_OK;
+    }
+    a.poses = (float*)c->stage;
+    a.z_out = (int32_t*)(a.zr + 2);
+    cudaError_t e = perch::launch_proposals(a, c->stream);
+    if (!e) e = cudaMemcpyAsync(poses, a.poses, n * 48, cudaMemcpyDeviceToHost, c->stream);
+    if (!e && z_range) e = cudaMemcpyAsync(z_range, a.z_out, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return e ? cuda_fail(c, e, "perch_pose_proposals") : PERCH_OK;
+}
+
 perch_status perch_debug_render_keys(perch_ctx* c, int32_t scene_id, int32_t mesh_id,
                                      const int32_t* roi, const float* pose, uint64_t* keys)
 {

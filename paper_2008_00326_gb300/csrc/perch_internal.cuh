@@ -115,4 +115,17 @@ cudaError_t launch_best(const BestArgs& a, cudaStream_t s);
 
 cudaError_t init_device_tables(cudaStream_t s);
 
+// 6-DoF pose proposals (Sec. V-B): z range of a labelled box, then the poses.
+struct ProposalArgs {
+    DevScene sc;
+    int label;
+    int box[4];
+    int M, N, K;
+    float centre[3];          // object-frame centre of the mesh's bounding box
+    unsigned* zr;             // device: [z_min, z_max] (0.1 mm), reduced by the first kernel
+    int32_t* z_out;           // optional copy of zr (device), or nullptr
+    float* poses;             // device, M*N*K*12
+};
+cudaError_t launch_proposals(const ProposalArgs& a, cudaStream_t s);
+
 }  // namespace perch

@@ -1199,6 +1199,99 @@ cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, c
 }
 
 // ---------------------------------------------------------------------------
+// 6-DoF pose proposals (Sec. V-B, Eq. 5 and Eq. 6)
+// ---------------------------------------------------------------------------
+
+__global__ void k_mask_depth_range(ProposalArgs a)
+{
+    const int bw = a.box[2] - a.box[0], bh = a.box[3] - a.box[1];
+    unsigned lo = 0xFFFFFFFFu, hi = 0u;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bw * bh; i += gridDim.x * blockDim.x) {
+        const int u = a.box[0] + i % bw, v = a.box[1] + i / bw;
+        const int pix = v * a.sc.W + u;
+        const unsigned d = a.sc.depth[pix];
+        if (d != 0 && a.sc.labels[pix] == a.label) {
+            lo = min(lo, d);
+            hi = max(hi, d);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0 && hi != 0u) {
+        atomicMin(&a.zr[0], lo);
+        atomicMax(&a.zr[1], hi);
+    }
+}
+
+__global__ void k_proposals(ProposalArgs a)
+{
+    const long long total = (long long)a.M * a.N * a.K;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx == 0 && a.z_out) {
+        const bool any = a.zr[1] != 0u;
+        a.z_out[0] = any ? (int32_t)a.zr[0] : 0;
+        a.z_out[1] = any ? (int32_t)a.zr[1] : 0;
+    }
+    if (idx >= total) return;
+    const int j = (int)(idx % a.K);
+    const int k = (int)((idx / a.K) % a.N);
+    const int i = (int)(idx / ((long long)a.K * a.N));
+    // viewpoint i of the Fibonacci lattice (object frame, towards the camera)
+    const float golden = 2.39996322972865332f;          // pi (3 - sqrt 5)
+    const float y = 1.0f - (2.0f * i + 1.0f) / (float)a.M;
+    const float rad = sqrtf(fmaxf(0.0f, 1.0f - y * y));
+    const float phi = golden * (float)i;
+    const float vx = rad * cosf(phi), vy = y, vz = rad * sinf(phi);
+    // camera axes in the object frame: forward = -v, right, down
+    const float fx = -vx, fy = -vy, fz = -vz;
+    float rx = fy * 1.0f - fz * 0.0f, ry = fz * 0.0f - fx * 1.0f, rz = 0.0f;   // forward x (0,0,1)
+    float rn = sqrtf(rx * rx + ry * ry + rz * rz);
+    if (rn < 1e-6f) {                                   // forward parallel to z: use (0,1,0)
+        rx = fy * 0.0f - fz * 1.0f;
+        ry = fz * 0.0f - fx * 0.0f;
+        rz = fx * 1.0f - fy * 0.0f;
+        rn = sqrtf(rx * rx + ry * ry + rz * rz);
+    }
+    rx /= rn; ry /= rn; rz /= rn;
+    const float dx = fy * rz - fz * ry, dy = fz * rx - fx * rz, dz = fx * ry - fy * rx;
+    // in-plane rotation about the optical axis
+    const float th = 6.28318530717958648f * (float)k / (float)a.N;
+    const float c = cosf(th), s = sinf(th);
+    const float R[9] = {c * rx - s * dx, c * ry - s * dy, c * rz - s * dz,
+                        s * rx + c * dx, s * ry + c * dy, s * rz + c * dz,
+                        fx, fy, fz};
+    // translation: the box centre back-projected at depth z_j
+    const bool any = a.zr[1] != 0u;
+    const float zmin = any ? (float)a.zr[0] / 10000.0f : 0.0f;
+    const float zmax = any ? (float)a.zr[1] / 10000.0f : 0.0f;
+    const float z = a.K > 1 ? zmin + (zmax - zmin) * (float)j / (float)(a.K - 1) : 0.5f * (zmin + zmax);
+    const float uc = 0.5f * (float)(a.box[0] + a.box[2] - 1), vc = 0.5f * (float)(a.box[1] + a.box[3] - 1);
+    const float cxp = (uc - a.sc.cx) * z / a.sc.fx, cyp = (vc - a.sc.cy) * z / a.sc.fy;
+    float* out = a.poses + 12 * idx;
+    const float m0 = a.centre[0], m1 = a.centre[1], m2 = a.centre[2];
+    out[0] = R[0]; out[1] = R[1]; out[2] = R[2];
+    out[3] = cxp - (R[0] * m0 + R[1] * m1 + R[2] * m2);
+    out[4] = R[3]; out[5] = R[4]; out[6] = R[5];
+    out[7] = cyp - (R[3] * m0 + R[4] * m1 + R[5] * m2);
+    out[8] = R[6]; out[9] = R[7]; out[10] = R[8];
+    out[11] = z - (R[6] * m0 + R[7] * m1 + R[8] * m2);
+}
+
+cudaError_t launch_proposals(const ProposalArgs& a, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(a.zr, 0xFF, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.zr + 1, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int area = (a.box[2] - a.box[0]) * (a.box[3] - a.box[1]);
+    if (area > 0) k_mask_depth_range<<<min(1024, (area + 255) / 256), 256, 0, s>>>(a);
+    const long long total = (long long)a.M * a.N * a.K;
+    k_proposals<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // argmin of J = J_o + J_r (warp shuffles, then the last block reduces the partials)
 // ---------------------------------------------------------------------------
 

@@ -28,7 +28,7 @@ EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_
            "perch_debug_render_keys", "perch_best_noalloc", "perch_score_batch",
            "perch_batch_graph_create", "perch_batch_graph_launch", "perch_batch_graph_destroy",
            "perch_autotune", "perch_server_start", "perch_submit", "perch_poll", "perch_wait",
-           "perch_ticket_times", "perch_server_stop")
+           "perch_ticket_times", "perch_server_stop", "perch_pose_proposals")
 
 
 class PerchError(RuntimeError):
@@ -171,6 +171,7 @@ def load(path: str | None = None):
         "perch_wait": ([P, U64, I64], I32),
         "perch_ticket_times": ([P, U64, P, P], I32),
         "perch_server_stop": ([P], I32),
+        "perch_pose_proposals": ([P, I32, I32, I32, P, I32, I32, I32, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -346,6 +347,23 @@ def perch_autotune(ctx, items, poses, costs):
     _check(ctx, load().perch_autotune(ctx, items, len(items), _ptr_of(poses), _ptr_of(costs),
                                        C.byref(t), C.byref(z)))
     return t.value, z.value
+
+
+def perch_pose_proposals(ctx, scene_id, mesh_id, label, bbox, M, N, K, poses=None, z_range=None,
+                         stream=None):
+    """Host mode: returns (poses (M*N*K,12) float32, (z_min, z_max)).  Device
+    mode: poses/z_range torch CUDA tensors filled on `stream`."""
+    keep, pbox = _roi(bbox)
+    if stream is None:
+        out = np.empty((M * N * K, 12), np.float32)
+        zr = np.zeros(2, np.int32)
+        _check(ctx, load().perch_pose_proposals(ctx, scene_id, mesh_id, label, pbox, M, N, K,
+                                                 out.ctypes.data, zr.ctypes.data, None))
+        return out, (int(zr[0]), int(zr[1]))
+    _check(ctx, load().perch_pose_proposals(ctx, scene_id, mesh_id, label, pbox, M, N, K, _ptr_of(poses),
+                                             None if z_range is None else _ptr_of(z_range),
+                                             getattr(stream, "cuda_stream", stream)))
+    return poses
 
 
 def perch_set_launch_config(ctx, threads, zbuf_words, mark_bits=0):

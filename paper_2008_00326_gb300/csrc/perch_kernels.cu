@@ -772,15 +772,12 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
             if (threadIdx.x == 0) *S.next_batch = 0;
             __syncthreads();
             // ---- raster: a warp sets up 32 triangles (one per lane), stages
-            // them in shared memory and spreads (triangle, row, 16-pixel
-            // segment) items of their boxes evenly over its lanes (a prefix
-            // sum of item counts, then a binary search per item).  An item
-            // first narrows its segment to the triangle's span on that row
-            // (a superset computed from the edge functions, so thin triangles
-            // cost no more than their width) and tests those pixels exactly.
+            // them in shared memory and spreads the pixels of their boxes
+            // evenly over its lanes (a prefix sum of the box areas, then a
+            // binary search per pixel for its triangle)
             for (int base = warp * 32; base < J.m.n_tris; base += NT) {
                 const int t = base + lane;
-                int items = 0;
+                int area = 0;
                 TriSetup o;
                 if (t < J.m.n_tris && get_triangle<VC>(sc, J.m, P, vc, t, o)) {
                     int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
@@ -788,21 +785,20 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                     int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
                     int v0 = max(ceil16(ymin), tv0), v1 = min(floor16(ymax), tv1 - 1);
                     if (u0 <= u1 && v0 <= v1) {
-                        const int bw = u1 - u0 + 1;
-                        items = (v1 - v0 + 1) * ((bw + 15) >> 4);
+                        area = (u1 - u0 + 1) * (v1 - v0 + 1);
                         TriStage& e = TS[lane];
                         for (int k = 0; k < 3; ++k) { e.x[k] = o.x[k]; e.y[k] = o.y[k]; e.iz[k] = o.iz[k]; }
                         e.A = o.A;
                         e.tri = t;
                         e.u0 = u0;
                         e.v0 = v0;
-                        e.bw = bw;
+                        e.bw = u1 - u0 + 1;
                         e.owns = (owns(o.x[2] - o.x[1], o.y[2] - o.y[1]) ? 1 : 0) |
                                  (owns(o.x[0] - o.x[2], o.y[0] - o.y[2]) ? 2 : 0) |
                                  (owns(o.x[1] - o.x[0], o.y[1] - o.y[0]) ? 4 : 0);
                     }
                 }
-                int incl = items;
+                int incl = area;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
                     int x = __shfl_up_sync(0xffffffffu, incl, off);
@@ -812,7 +808,7 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                 __syncwarp();
                 for (int f0 = 0; f0 < total; f0 += 32) {
                     const int f = f0 + lane;
-                    // the triangle j whose item range holds f: incl[j-1] <= f < incl[j]
+                    // the triangle j whose pixel range holds f: incl[j-1] <= f < incl[j]
                     int j = 0;
 #pragma unroll
                     for (int step = 16; step >= 1; step >>= 1) {
@@ -822,50 +818,19 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                     const int excl = __shfl_sync(0xffffffffu, incl, j > 0 ? j - 1 : 0);
                     if (f >= total) continue;
                     const TriStage& e = TS[j];
-                    const int nseg = (e.bw + 15) >> 4;
                     const int local = f - (j > 0 ? excl : 0);
-                    const int row = local / nseg;
-                    const int seg = local - row * nseg;
-                    const int v = e.v0 + row;
-                    const int us = e.u0 + 16 * seg;
-                    int lo = us, hi = min(us + 15, e.u0 + e.bw - 1);
-                    const int sy = 16 * v, sx = 16 * us;
-                    int w0 = edge_fn(e.x[1], e.y[1], e.x[2], e.y[2], sx, sy);
-                    int w1 = edge_fn(e.x[2], e.y[2], e.x[0], e.y[0], sx, sy);
-                    int w2 = edge_fn(e.x[0], e.y[0], e.x[1], e.y[1], sx, sy);
-                    const int a0 = -16 * (e.y[2] - e.y[1]), a1 = -16 * (e.y[0] - e.y[2]), a2 = -16 * (e.y[1] - e.y[0]);
-                    // narrow [lo, hi] to a superset of {u : w_i(u) >= 0 for all i}
-                    bool empty = false;
-                    {
-                        const int wv[3] = {w0, w1, w2}, av[3] = {a0, a1, a2};
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) {
-                            if (av[i] == 0) {
-                                empty = empty || wv[i] < 0;
-                            } else {
-                                float tcut = (float)(-wv[i]) / (float)av[i];
-                                tcut = fminf(fmaxf(tcut, -1.0e6f), 1.0e6f);
-                                const int c = (int)floorf(tcut);
-                                if (av[i] > 0) lo = max(lo, us + c - 1);
-                                else hi = min(hi, us + c + 1);
-                            }
-                        }
-                    }
-                    if (empty || lo > hi) continue;
-                    w0 += a0 * (lo - us);
-                    w1 += a1 * (lo - us);
-                    w2 += a2 * (lo - us);
-                    const int zrow = (v - tv0) * tw - tu0;
-                    for (int u = lo; u <= hi; ++u) {
-                        const bool cov = (w0 > 0 || (w0 == 0 && (e.owns & 1))) &&
-                                         (w1 > 0 || (w1 == 0 && (e.owns & 2))) &&
-                                         (w2 > 0 || (w2 == 0 && (e.owns & 4)));
-                        unsigned d;
-                        if (cov && sample_depth(w0, w1, w2, e.iz, e.A, d)) zmin<K32>(zbuf, zrow + u, d, e.tri, a.err);
-                        w0 += a0;
-                        w1 += a1;
-                        w2 += a2;
-                    }
+                    const int dv = local / e.bw;
+                    const int u = e.u0 + (local - dv * e.bw), v = e.v0 + dv;
+                    const int sx = 16 * u, sy = 16 * v;
+                    const int w0 = edge_fn(e.x[1], e.y[1], e.x[2], e.y[2], sx, sy);
+                    const int w1 = edge_fn(e.x[2], e.y[2], e.x[0], e.y[0], sx, sy);
+                    const int w2 = edge_fn(e.x[0], e.y[0], e.x[1], e.y[1], sx, sy);
+                    const bool cov = (w0 > 0 || (w0 == 0 && (e.owns & 1))) &&
+                                     (w1 > 0 || (w1 == 0 && (e.owns & 2))) &&
+                                     (w2 > 0 || (w2 == 0 && (e.owns & 4)));
+                    unsigned d;
+                    if (cov && sample_depth(w0, w1, w2, e.iz, e.A, d))
+                        zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, e.tri, a.err);
                 }
                 __syncwarp();
             }

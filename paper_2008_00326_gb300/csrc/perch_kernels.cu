@@ -437,6 +437,7 @@ __device__ __forceinline__ void zmin(uint32_t* zbuf, int idx, unsigned d, int tr
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
 constexpr int kChunk = 1;         // consecutive hypotheses a block takes per counter fetch (measured: 1 is best)
 constexpr int kGroups = 1;        // distinct query cells looked up together per warp
+constexpr int kCellCache = 64;    // per-warp cache of recent 27-cell lookups (direct mapped)
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
     float x, y, z;
@@ -451,6 +452,7 @@ struct __align__(16) WarpProbe {
     unsigned char qlist[kGroups][32];  // per group: the lanes of its queries, in lane order
     float4 q[32];                 // query of each lane
     unsigned long long best[32];  // nearest-neighbour key of each lane's query
+    uint4 cache[kCellCache];      // recent cell lookups: (key lo, key hi, start, count)
 };
 
 // Per-warp scratch: the radius search and the rasteriser's triangle stage
@@ -472,35 +474,43 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
                                              const int* gz, int ng, WarpProbe& W, int lane)
 {
     const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-    unsigned long long key[kGroups];
-    uint32_t h[kGroups];
-    uint4 e[kGroups];
-#pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-        if (g < ng && lane < 27) {
-            key[g] = cell_key(gx[g] + dx, gy[g] + dy, gz[g] + dz);
-            h[g] = hash_slot(key[g], sc.table_mask);
-            e[g] = __ldg(&sc.table[h[g]]);
-        }
-    }
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) {
         if (g >= ng) break;
         uint32_t start = 0, cnt = 0;
+        bool hit = false;
+        unsigned long long key = kEmptyKey;
+        uint32_t cs = 0;
         if (lane < 27) {
-            uint4 x = e[g];
-            uint32_t slot = h[g];
-            for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
-                unsigned long long k = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
-                if (k == key[g]) {
-                    start = x.z;
-                    cnt = x.w;
-                    break;
+            key = cell_key(gx[g] + dx, gy[g] + dy, gz[g] + dz);
+            // neighbouring query cells share most of their 27 neighbours: look in
+            // the warp's cache of recent lookups before going to the table
+            cs = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 58) & (kCellCache - 1);
+            const uint4 c = W.cache[cs];
+            hit = ((unsigned long long)c.x | ((unsigned long long)c.y << 32)) == key;
+            if (hit) {
+                start = c.z;
+                cnt = c.w;
+            } else {
+                uint32_t slot = hash_slot(key, sc.table_mask);
+                for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
+                    const uint4 x = __ldg(&sc.table[slot]);
+                    unsigned long long k = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+                    if (k == key) {
+                        start = x.z;
+                        cnt = x.w;
+                        break;
+                    }
+                    if (k == kEmptyKey) break;
+                    slot = (slot + 1) & sc.table_mask;
                 }
-                if (k == kEmptyKey) break;
-                slot = (slot + 1) & sc.table_mask;
-                x = __ldg(&sc.table[slot]);
             }
+        }
+        // fill the cache: one writer per cache slot among the lanes that missed
+        const unsigned miss = __ballot_sync(0xffffffffu, lane < 27 && !hit);
+        if (lane < 27 && !hit) {
+            const unsigned same = __match_any_sync(miss, cs);
+            if (lane == __ffs(same) - 1) W.cache[cs] = make_uint4((uint32_t)key, (uint32_t)(key >> 32), start, cnt);
         }
         uint32_t incl = cnt;
 #pragma unroll
@@ -862,6 +872,9 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
             const int nblocks = nbx * nby;
             KeptPoint* wq = S.kept + warp * kWarpQueue;
             const MarkBand mband = {S.marks, vbox[0], vbox[2], mv0, mv1, vw};
+            // the raster stage shared these bytes: start with an empty lookup cache
+            for (int i = lane; i < kCellCache; i += 32) WP.cache[i] = make_uint4(~0u, ~0u, 0u, 0u);
+            __syncwarp();
             int wq_head = 0, wq_count = 0;
             for (;;) {
                 int blk = 0;

@@ -272,10 +272,10 @@ def batched_leg(P, torch, dev, n_scenes=64):
             "identical_costs": same}
 
 
-def served_leg(P, dev, rates=(5, 20, 50, 100, 200), max_requests=120, window_s=2.0, seed=9):
-    """Poisson request traces mixing the three workloads; serial plain path vs
-    the continuous-batching server.  Latency = submission (arrival) to results."""
-    import threading
+def served_leg(P, dev, seed=9):
+    """Poisson request traces; serial plain path vs the continuous-batching
+    server.  Latency = submission (arrival) to results.  Two mixes: all three
+    workloads (large searches), and the two small ones only."""
     from paper_2008_00326_gb300 import scenes
     ctx = P.Context(dev.index or 0)
     kinds = []
@@ -283,6 +283,18 @@ def served_leg(P, dev, rates=(5, 20, 50, 100, 200), max_requests=120, window_s=2
         sid = ctx.set_observation(sc)
         mids = [ctx.load_mesh(m) for m in sc.meshes]
         kinds.append([(sid, mids[r.mesh_index], r.label, r.roi, r.poses) for r in sc.requests])
+    mixed = _served_rates(P, ctx, kinds, (5, 20, 50, 100, 200), 120, seed)
+    small = _served_rates(P, ctx, [kinds[0], kinds[2]], (50, 200, 500, 1000), 300, seed + 1)
+    ctx.close()
+    return {"server": {"slots": 2, "max_batch_hypotheses": 1 << 16},
+            "mixed": {"mix": "uniform over tabletop_small (968 hyp), one tabletop_3obj object "
+                             "(29,584 hyp), one sixdof_5obj object (4,096 hyp); scenes resident",
+                      "rates": mixed},
+            "small": {"mix": "uniform over tabletop_small (968 hyp) and one sixdof_5obj object "
+                             "(4,096 hyp); scenes resident", "rates": small}}
+
+
+def _served_rates(P, ctx, kinds, rates, max_requests, seed, window_s=2.0):
     rng = np.random.default_rng(seed)
     out = []
     for rate in rates:
@@ -290,7 +302,7 @@ def served_leg(P, dev, rates=(5, 20, 50, 100, 200), max_requests=120, window_s=2
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
         trace = []
         for _ in range(n):
-            group = kinds[int(rng.integers(0, 3))]
+            group = kinds[int(rng.integers(0, len(kinds)))]
             trace.append(group[int(rng.integers(0, len(group)))])
         hyps = sum(len(t[4]) for t in trace)
         # serial plain path: requests scored one at a time in arrival order
@@ -327,10 +339,7 @@ def served_leg(P, dev, rates=(5, 20, 50, 100, 200), max_requests=120, window_s=2
                     "hyp_s": hyps / span}
         out.append({"rate_req_s": rate, "requests": n, "hypotheses": hyps,
                     "plain_serial": stats(lat, span_plain), "served": stats(slat, span_served)})
-    ctx.close()
-    return {"mix": "uniform over tabletop_small (968 hyp), one tabletop_3obj object (29,584 hyp), "
-                   "one sixdof_5obj object (4,096 hyp); scenes resident",
-            "server": {"slots": 2, "max_batch_hypotheses": 1 << 16}, "rates": out}
+    return out
 
 
 def main():

@@ -234,12 +234,15 @@ typedef struct perch_work_item {
 PERCH_API perch_status perch_score_batch(perch_ctx *ctx, const perch_work_item *items, int32_t n_items,
                                          const float *poses, int32_t *costs, void *cuda_stream);
 
-/* A batch captured once as a CUDA graph (counter reset + persistent launch)
- * and replayed: the item list, the device pose/cost arrays and the launch
- * shape are fixed at creation; the caller refills the pose array between
- * replays.  The graph owns its scratch, so replays of one graph must be
- * ordered (one stream), while different graphs and the context may run
- * concurrently.  poses/costs are DEVICE pointers. */
+/* A batch built once as a CUDA graph and replayed: one counter-reset node and
+ * one persistent single-item scoring kernel per item, all independent, each
+ * with a grid proportional to its item's share of the hypotheses, so a single
+ * graph launch runs every search concurrently (items read their scene and
+ * mesh from the kernel parameters, the fastest path).  The item list, the
+ * device pose/cost arrays and the launch shape are fixed at creation; the
+ * caller refills the pose array between replays.  The graph owns its scratch,
+ * so replays of one graph must be ordered (one stream), while different graphs
+ * and the context may run concurrently.  poses/costs are DEVICE pointers. */
 typedef struct perch_batch_graph perch_batch_graph;
 PERCH_API perch_status perch_batch_graph_create(perch_ctx *ctx, const perch_work_item *items,
                                                 int32_t n_items, const float *poses,

@@ -957,64 +957,65 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
     long long total;
     perch_status st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
     if (st != PERCH_OK) return st;
-    if (total == 0 || total > 0xFFFFFFF0ll) return fail(c, PERCH_E_INVALID, "batch of %lld hypotheses", total);
+    if (total == 0) return fail(c, PERCH_E_INVALID, "empty batch");
     perch::ScoreConfig cfg;
     if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
-    const int grid = perch::score_grid(cfg, mw);
-    if (grid <= 0) {
+    const int resident = perch::score_grid(cfg, mw);
+    if (resident <= 0) {
         cudaGetLastError();
         return fail(c, PERCH_E_CUDA, "scoring kernel does not fit on the device");
     }
     perch_batch_graph* G = new (std::nothrow) perch_batch_graph();
     if (!G) return fail(c, PERCH_E_NOMEM, "graph handle");
     G->ctx = c;
-    int max_verts = 0;
-    bool small_images = true;
-    for (const auto& j : jobs) {
-        max_verts = std::max(max_verts, j.m.n_verts);
-        small_images = small_images && j.sc.W <= 1023 && j.sc.H <= 1023;
+    // One single-job kernel per item, all independent: each gets a persistent
+    // grid proportional to its share of the hypotheses (at least one block),
+    // its own counter and its own vertex-cache slots, so the whole batch runs
+    // concurrently from one graph launch without per-item tails.
+    const size_t nj = jobs.size();
+    std::vector<int> grid(nj);
+    std::vector<long long> vstride(nj), voff(nj);
+    long long vtotal = 0;
+    for (size_t j = 0; j < nj; ++j) {
+        long long gj = (long long)((double)resident * (double)jobs[j].n / (double)total + 0.5);
+        gj = std::max(1ll, std::min(gj, jobs[j].n));
+        grid[j] = (int)gj;
+        const bool small = jobs[j].sc.W <= 1023 && jobs[j].sc.H <= 1023;
+        vstride[j] = small ? ((long long)jobs[j].m.n_verts + 31) / 32 * 32 : 0;
+        voff[j] = vtotal;
+        vtotal += (long long)grid[j] * vstride[j];
     }
-    const long long vstride = small_images ? ((long long)max_verts + 31) / 32 * 32 : 0;
-    const size_t jb = ((jobs.size() * sizeof(perch::Job)) + 15) & ~(size_t)15;
-    std::vector<char> table(jb + jobs.size() * sizeof(long long));
-    std::memcpy(table.data(), jobs.data(), jobs.size() * sizeof(perch::Job));
-    long long* ends = (long long*)(table.data() + jb);
-    long long acc = 0;
-    for (size_t i = 0; i < jobs.size(); ++i) ends[i] = (acc += jobs[i].n);
     void* p = nullptr;
-    if ((st = dalloc(c, 16, &p)) == PERCH_OK) G->next = (unsigned*)p;
-    if (st == PERCH_OK && vstride > 0)
-        st = dalloc(c, (size_t)grid * vstride * sizeof(unsigned long long), &G->vcache);
-    if (st == PERCH_OK) st = dalloc(c, table.size(), &G->table);
+    if ((st = dalloc(c, std::max<size_t>(16, nj * sizeof(unsigned)), &p)) == PERCH_OK) G->next = (unsigned*)p;
+    if (st == PERCH_OK && vtotal > 0) st = dalloc(c, (size_t)vtotal * sizeof(unsigned long long), &G->vcache);
     cudaError_t e = cudaSuccess;
-    if (st == PERCH_OK) {
-        e = cudaMemcpyAsync(G->table, table.data(), table.size(), cudaMemcpyHostToDevice, c->stream);
-        if (!e) e = cudaStreamSynchronize(c->stream);
-    }
-    cudaStream_t cs = nullptr;
-    if (st == PERCH_OK && !e) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (st == PERCH_OK) e = cudaGraphCreate(&G->graph, 0);
+    cudaGraphNode_t reset = nullptr;
     if (st == PERCH_OK && !e) {
+        cudaMemsetParams mp{};
+        mp.dst = G->next;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = nj;
+        mp.height = 1;
+        mp.pitch = 0;
+        e = cudaGraphAddMemsetNode(&reset, G->graph, nullptr, 0, &mp);
+    }
+    for (size_t j = 0; j < nj && st == PERCH_OK && !e; ++j) {
         perch::ScoreArgs a{};
-        a.job0 = jobs[0];
-        a.jobs = (const perch::Job*)G->table;
-        a.job_end = (const long long*)((char*)G->table + jb);
-        a.n_jobs = (int)jobs.size();
-        a.n = total;
+        a.job0 = jobs[j];
+        a.n_jobs = 1;
+        a.n = jobs[j].n;
         a.zcap_words = cfg.zcap_words;
         a.mark_words = mw;
         a.err = c->d_err;
-        a.next = G->next;
-        a.vcache = (unsigned long long*)G->vcache;
-        a.vstride = vstride;
-        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (!e) {
-            cudaError_t le = perch::launch_score(a, cfg, grid, cs);
-            e = cudaStreamEndCapture(cs, &G->graph);
-            if (!e) e = le;
-        }
-        if (!e) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+        a.next = G->next + j;
+        a.vcache = vstride[j] ? (unsigned long long*)G->vcache + voff[j] : nullptr;
+        a.vstride = vstride[j];
+        cudaGraphNode_t node;
+        e = perch::add_score_node(G->graph, &reset, 1, a, cfg, grid[j], &node);
     }
-    if (cs) cudaStreamDestroy(cs);
+    if (st == PERCH_OK && !e) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
     if (st == PERCH_OK && e) st = cuda_fail(c, e, "perch_batch_graph_create");
     if (st != PERCH_OK) {
         perch_batch_graph_destroy(G);

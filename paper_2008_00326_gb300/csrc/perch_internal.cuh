@@ -80,6 +80,10 @@ size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words);
 // Blocks of the persistent scoring kernel that fit on the device at once.
 int score_grid(const ScoreConfig& cfg, int mark_words);
 cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s);
+// Add a single-job scoring kernel node (a.n_jobs must be 1) to graph g after
+// the given dependencies; the caller resets *a.next before the node runs.
+cudaError_t add_score_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                           const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaGraphNode_t* out);
 
 // Observation build (voxel hash over I).
 struct BuildBuffers {

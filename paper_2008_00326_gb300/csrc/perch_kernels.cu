@@ -1200,6 +1200,37 @@ static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, i
     return cudaGetLastError();
 }
 
+template <int NT>
+static cudaError_t add_score_node_nt(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                                     const ScoreArgs& a, const ScoreConfig& cfg, int grid,
+                                     cudaGraphNode_t* out)
+{
+    const size_t smem = score_smem_bytes(cfg, a.mark_words);
+    cudaError_t e = cudaFuncSetAttribute(k_score<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    ScoreArgs copy = a;
+    void* args[] = {&copy};
+    cudaKernelNodeParams kp{};
+    kp.func = (void*)k_score<NT, true>;
+    kp.gridDim = dim3((unsigned)(a.n < grid ? a.n : grid));
+    kp.blockDim = dim3(NT);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+}
+
+cudaError_t add_score_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                           const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaGraphNode_t* out)
+{
+    if (a.n_jobs != 1 || a.n <= 0 || a.n > 0xFFFFFFF0ll) return cudaErrorInvalidValue;
+    switch (cfg.threads) {
+    case 128: return add_score_node_nt<128>(g, deps, ndeps, a, cfg, grid, out);
+    case 512: return add_score_node_nt<512>(g, deps, ndeps, a, cfg, grid, out);
+    default: return add_score_node_nt<256>(g, deps, ndeps, a, cfg, grid, out);
+    }
+}
+
 cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;

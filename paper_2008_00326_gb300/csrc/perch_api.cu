@@ -41,27 +41,21 @@ struct SceneRec {
     void* table = nullptr;
 };
 
-// Everything one chain of scoring launches needs besides its inputs: the
-// hypothesis counter, the per-block vertex caches, and a small ring of
-// job-table uploads (pinned host staging + device table + an event each), so
-// that consecutive asynchronous launches need not wait for each other on the
-// host.  Launches that share a ScoreScratch are ordered on the GPU through
-// `last` (they share the counter and the caches).
-constexpr int kStageRing = 4;
-
-struct JobStage {
-    void* host = nullptr;          // pinned
-    void* dev = nullptr;
-    size_t bytes = 0;
-    cudaEvent_t done = nullptr;
-};
+// Everything one chain of scoring launches needs besides its inputs: one
+// hypothesis counter per job followed by the vertex-cache slot mask (zeroed
+// together before each run), the vertex-cache pool, and the side streams a
+// multi-job run spreads its launches over.  Runs that share a ScoreScratch
+// are ordered on the GPU through `last`.
+constexpr int kSideStreams = 4;
 
 struct ScoreScratch {
-    unsigned* next = nullptr;      // device counter
+    unsigned* next = nullptr;      // device: counters, then slot mask
+    size_t next_words = 0;
     void* vcache = nullptr;
     size_t vcache_bytes = 0;
-    JobStage stage[kStageRing];
-    int turn = 0;
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kSideStreams] = {};
     cudaEvent_t last = nullptr;
 };
 
@@ -107,9 +101,8 @@ struct perch_ctx {
 
 struct perch_batch_graph {
     perch_ctx* ctx = nullptr;
-    unsigned* next = nullptr;              // the graph's own hypothesis counter
-    void* vcache = nullptr;                // and vertex caches
-    void* table = nullptr;                 // device job table (uploaded at creation)
+    unsigned* next = nullptr;              // the graph's own counters and slot mask
+    void* vcache = nullptr;                // and vertex-cache pool
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -247,16 +240,14 @@ perch_status fit_config(perch_ctx* c, int mark_words, perch::ScoreConfig* cfg)
 
 perch_status scratch_init(perch_ctx* c, ScoreScratch& X)
 {
-    void* p = nullptr;
-    perch_status st = dalloc(c, 16, &p);
-    if (st != PERCH_OK) return st;
-    X.next = (unsigned*)p;
     cudaError_t e = cudaEventCreateWithFlags(&X.last, cudaEventDisableTiming);
-    for (int i = 0; i < kStageRing && e == cudaSuccess; ++i)
-        e = cudaEventCreateWithFlags(&X.stage[i].done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(X.last, c->stream);
-    for (int i = 0; i < kStageRing && e == cudaSuccess; ++i) e = cudaEventRecord(X.stage[i].done, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "scratch events");
+    if (!e) e = cudaEventCreateWithFlags(&X.fork, cudaEventDisableTiming);
+    for (int i = 0; i < kSideStreams && !e; ++i) {
+        e = cudaStreamCreateWithFlags(&X.side[i], cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreateWithFlags(&X.join[i], cudaEventDisableTiming);
+    }
+    if (!e) e = cudaEventRecord(X.last, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "scratch streams");
     return PERCH_OK;
 }
 
@@ -265,13 +256,11 @@ void scratch_free(perch_ctx* c, ScoreScratch& X)
     if (X.last) cudaEventSynchronize(X.last);
     dfree(c, X.next);
     dfree(c, X.vcache);
-    for (int i = 0; i < kStageRing; ++i) {
-        if (X.stage[i].done) cudaEventSynchronize(X.stage[i].done);
-        if (X.stage[i].host) cudaFreeHost(X.stage[i].host);
-        dfree(c, X.stage[i].dev);
-        if (X.stage[i].done) cudaEventDestroy(X.stage[i].done);
-        X.stage[i] = JobStage{};
+    for (int i = 0; i < kSideStreams; ++i) {
+        if (X.side[i]) cudaStreamDestroy(X.side[i]);
+        if (X.join[i]) cudaEventDestroy(X.join[i]);
     }
+    if (X.fork) cudaEventDestroy(X.fork);
     if (X.last) cudaEventDestroy(X.last);
     X = ScoreScratch{};
 }
@@ -305,8 +294,11 @@ perch_status make_job(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t l
     return PERCH_OK;
 }
 
-// Upload the job table to the next ring slot and launch the persistent scorer
-// over it on stream st, after every earlier launch that used X.
+// Launch the persistent scorer once per job, on stream st after every
+// earlier run that used X.  Each launch gets the whole resident grid; with
+// several jobs the launches go round-robin over X's side streams, so the
+// blocks of job j+1 start on the SMs that job j's blocks leave at its tail,
+// and every job keeps its fields in the parameter bank.
 perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Job>& jobs,
                       int mark_words, const perch::ScoreConfig& cfg_in, cudaStream_t st,
                       unsigned long long* dump)
@@ -315,12 +307,12 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
     int max_verts = 0;
     bool small_images = true;
     for (const auto& j : jobs) {
+        if (j.n > 0xFFFFFFF0ll) return fail(c, PERCH_E_INVALID, "more than 2^32 hypotheses in one item");
         total += j.n;
         max_verts = std::max(max_verts, j.m.n_verts);
         small_images = small_images && j.sc.W <= 1023 && j.sc.H <= 1023;
     }
     if (total == 0) return PERCH_OK;
-    if (total > 0xFFFFFFF0ll) return fail(c, PERCH_E_INVALID, "more than 2^32 hypotheses in one launch");
     perch::ScoreConfig cfg = cfg_in;
     perch_status stt = fit_config(c, mark_words, &cfg);
     if (stt != PERCH_OK) return stt;
@@ -329,7 +321,8 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
         cudaGetLastError();
         return fail(c, PERCH_E_CUDA, "scoring kernel does not fit on the device");
     }
-    // vertex caches: one slot per block, used when snapped coordinates fit in int16
+    // vertex caches: a pool of one slot per resident block, used when snapped
+    // coordinates fit in int16
     long long vstride = 0;
     if (small_images) {
         vstride = ((long long)max_verts + 31) / 32 * 32;
@@ -343,49 +336,44 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
             X.vcache_bytes = need;
         }
     }
-    // job table: jobs followed by their inclusive prefix sums
-    JobStage& S = X.stage[X.turn];
-    X.turn = (X.turn + 1) % kStageRing;
-    const size_t jb = ((jobs.size() * sizeof(perch::Job)) + 15) & ~(size_t)15;
-    const size_t bytes = jb + jobs.size() * sizeof(long long);
-    cudaError_t e = cudaEventSynchronize(S.done);
-    if (e != cudaSuccess) return cuda_fail(c, e, "job staging");
-    if (bytes > S.bytes) {
-        if (S.host) cudaFreeHost(S.host);
-        S.host = nullptr;
-        dfree(c, S.dev);
-        S.dev = nullptr;
-        S.bytes = 0;
-        size_t want = std::max(bytes, (size_t)4096);
-        if (cudaMallocHost(&S.host, want) != cudaSuccess) {
-            cudaGetLastError();
-            S.host = nullptr;
-            return fail(c, PERCH_E_NOMEM, "pinned job staging");
-        }
-        if ((stt = dalloc(c, want, &S.dev)) != PERCH_OK) return stt;
-        S.bytes = want;
+    const size_t nj = jobs.size();
+    const size_t mask_words = ((size_t)grid + 31) / 32;
+    const size_t words = nj + mask_words;
+    if (words > X.next_words) {
+        cudaEventSynchronize(X.last);
+        dfree(c, X.next);
+        X.next = nullptr;
+        X.next_words = 0;
+        void* p = nullptr;
+        if ((stt = dalloc(c, std::max<size_t>(words, 64) * sizeof(unsigned), &p)) != PERCH_OK) return stt;
+        X.next = (unsigned*)p;
+        X.next_words = std::max<size_t>(words, 64);
     }
-    std::memcpy(S.host, jobs.data(), jobs.size() * sizeof(perch::Job));
-    long long* ends = (long long*)((char*)S.host + jb);
-    long long acc = 0;
-    for (size_t i = 0; i < jobs.size(); ++i) ends[i] = (acc += jobs[i].n);
     perch::ScoreArgs a{};
-    a.job0 = jobs[0];
-    a.jobs = (const perch::Job*)S.dev;
-    a.job_end = (const long long*)((char*)S.dev + jb);
-    a.n_jobs = (int)jobs.size();
-    a.n = total;
     a.zcap_words = cfg.zcap_words;
     a.mark_words = mark_words;
     a.dump = dump;
     a.err = c->d_err;
-    a.next = X.next;
-    a.vcache = (unsigned long long*)X.vcache;
+    a.vcache = vstride ? (unsigned long long*)X.vcache : nullptr;
     a.vstride = vstride;
-    e = cudaStreamWaitEvent(st, X.last, 0);
-    if (!e && jobs.size() > 1) e = cudaMemcpyAsync(S.dev, S.host, bytes, cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaEventRecord(S.done, st);
-    if (!e) e = perch::launch_score(a, cfg, grid, st);
+    a.vmask = X.next + nj;
+    a.vslots = grid;
+    cudaError_t e = cudaStreamWaitEvent(st, X.last, 0);
+    if (!e) e = cudaMemsetAsync(X.next, 0, words * sizeof(unsigned), st);
+    const bool fan = nj > 1;
+    const int nside = (int)std::min<size_t>(nj, kSideStreams);
+    if (!e && fan) e = cudaEventRecord(X.fork, st);
+    for (int k = 0; k < nside && fan && !e; ++k) e = cudaStreamWaitEvent(X.side[k], X.fork, 0);
+    for (size_t j = 0; j < nj && !e; ++j) {
+        a.job = jobs[j];
+        a.n = jobs[j].n;
+        a.next = X.next + j;
+        e = perch::launch_score(a, cfg, grid, fan ? X.side[j % kSideStreams] : st);
+    }
+    for (int k = 0; k < nside && fan && !e; ++k) {
+        e = cudaEventRecord(X.join[k], X.side[k]);
+        if (!e) e = cudaStreamWaitEvent(st, X.join[k], 0);
+    }
     if (!e) e = cudaEventRecord(X.last, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "scoring launch");
     return PERCH_OK;
@@ -968,26 +956,22 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
     perch_batch_graph* G = new (std::nothrow) perch_batch_graph();
     if (!G) return fail(c, PERCH_E_NOMEM, "graph handle");
     G->ctx = c;
-    // One single-job kernel per item, all independent: each gets a persistent
-    // grid proportional to its share of the hypotheses (at least one block),
-    // its own counter and its own vertex-cache slots, so the whole batch runs
-    // concurrently from one graph launch without per-item tails.
+    // One kernel node per item, each with the whole resident grid, its own
+    // counter and the shared vertex-cache pool; node j follows node j - 4,
+    // mirroring the side-stream round robin of the direct launch.
     const size_t nj = jobs.size();
-    std::vector<int> grid(nj);
-    std::vector<long long> vstride(nj), voff(nj);
-    long long vtotal = 0;
-    for (size_t j = 0; j < nj; ++j) {
-        long long gj = (long long)((double)resident * (double)jobs[j].n / (double)total + 0.5);
-        gj = std::max(1ll, std::min(gj, jobs[j].n));
-        grid[j] = (int)gj;
-        const bool small = jobs[j].sc.W <= 1023 && jobs[j].sc.H <= 1023;
-        vstride[j] = small ? ((long long)jobs[j].m.n_verts + 31) / 32 * 32 : 0;
-        voff[j] = vtotal;
-        vtotal += (long long)grid[j] * vstride[j];
+    int max_verts = 0;
+    bool small_images = true;
+    for (const auto& j : jobs) {
+        max_verts = std::max(max_verts, j.m.n_verts);
+        small_images = small_images && j.sc.W <= 1023 && j.sc.H <= 1023;
     }
+    const long long vstride = small_images ? ((long long)max_verts + 31) / 32 * 32 : 0;
+    const size_t words = nj + ((size_t)resident + 31) / 32;
     void* p = nullptr;
-    if ((st = dalloc(c, std::max<size_t>(16, nj * sizeof(unsigned)), &p)) == PERCH_OK) G->next = (unsigned*)p;
-    if (st == PERCH_OK && vtotal > 0) st = dalloc(c, (size_t)vtotal * sizeof(unsigned long long), &G->vcache);
+    if ((st = dalloc(c, words * sizeof(unsigned), &p)) == PERCH_OK) G->next = (unsigned*)p;
+    if (st == PERCH_OK && vstride > 0)
+        st = dalloc(c, (size_t)resident * vstride * sizeof(unsigned long long), &G->vcache);
     cudaError_t e = cudaSuccess;
     if (st == PERCH_OK) e = cudaGraphCreate(&G->graph, 0);
     cudaGraphNode_t reset = nullptr;
@@ -996,24 +980,30 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
         mp.dst = G->next;
         mp.value = 0;
         mp.elementSize = 4;
-        mp.width = nj;
+        mp.width = words;
         mp.height = 1;
         mp.pitch = 0;
         e = cudaGraphAddMemsetNode(&reset, G->graph, nullptr, 0, &mp);
     }
+    std::vector<cudaGraphNode_t> nodes(nj, nullptr);
     for (size_t j = 0; j < nj && st == PERCH_OK && !e; ++j) {
+        if (jobs[j].n == 0) {
+            if (j >= 4) nodes[j] = nodes[j - 4];
+            continue;
+        }
         perch::ScoreArgs a{};
-        a.job0 = jobs[j];
-        a.n_jobs = 1;
+        a.job = jobs[j];
         a.n = jobs[j].n;
         a.zcap_words = cfg.zcap_words;
         a.mark_words = mw;
         a.err = c->d_err;
         a.next = G->next + j;
-        a.vcache = vstride[j] ? (unsigned long long*)G->vcache + voff[j] : nullptr;
-        a.vstride = vstride[j];
-        cudaGraphNode_t node;
-        e = perch::add_score_node(G->graph, &reset, 1, a, cfg, grid[j], &node);
+        a.vcache = vstride ? (unsigned long long*)G->vcache : nullptr;
+        a.vstride = vstride;
+        a.vmask = G->next + nj;
+        a.vslots = resident;
+        cudaGraphNode_t dep = (j >= 4 && nodes[j - 4]) ? nodes[j - 4] : reset;
+        e = perch::add_score_node(G->graph, &dep, 1, a, cfg, resident, &nodes[j]);
     }
     if (st == PERCH_OK && !e) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
     if (st == PERCH_OK && e) st = cuda_fail(c, e, "perch_batch_graph_create");
@@ -1044,7 +1034,6 @@ perch_status perch_batch_graph_destroy(perch_batch_graph* G)
     if (G->graph) cudaGraphDestroy(G->graph);
     dfree(c, G->next);
     dfree(c, G->vcache);
-    dfree(c, G->table);
     delete G;
     return PERCH_OK;
 }

@@ -48,21 +48,20 @@ struct Job {
     long long n;
 };
 
-// One scoring launch over a list of work items.  Hypothesis h of the launch
-// belongs to the first job j with h < job_end[j].
+// One scoring launch: the hypotheses of one job.  Launches that may run at
+// the same time (the jobs of one batch) share the vertex-cache pool.
 struct ScoreArgs {
-    Job job0;                 // the job of a single-job launch (read from the parameter bank)
-    const Job* jobs;          // n_jobs (device); unused when n_jobs == 1
-    const long long* job_end; // n_jobs inclusive prefix sums of Job::n (device)
-    int n_jobs;
-    long long n;              // total hypotheses
+    Job job;                  // read from the parameter bank
+    long long n;              // hypotheses (= job.n)
     int zcap_words;           // z-buffer capacity in 32-bit words
     int mark_words;           // marks bitset capacity in 32-bit words
     unsigned long long* dump; // debug: W*H 64-bit keys, or nullptr
     int* err;                 // device error word (bit flags)
-    unsigned* next;           // hypothesis counter, zeroed by the launcher
-    unsigned long long* vcache;  // per-block vertex cache slots, or nullptr
-    long long vstride;        // vertices per slot
+    unsigned* next;           // hypothesis counter, zeroed before the launch
+    unsigned long long* vcache;  // vertex-cache pool: vslots slots of vstride vertices, or nullptr
+    long long vstride;
+    unsigned* vmask;          // (vslots + 31) / 32 words, bit set = slot in use; zero when idle
+    int vslots;
 };
 
 // Error bits written by kernels into the context's error word.
@@ -79,9 +78,11 @@ struct ScoreConfig {
 size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words);
 // Blocks of the persistent scoring kernel that fit on the device at once.
 int score_grid(const ScoreConfig& cfg, int mark_words);
+// Launch the persistent scorer with min(grid, a.n) blocks; *a.next must be
+// zero when it starts.
 cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s);
-// Add a single-job scoring kernel node (a.n_jobs must be 1) to graph g after
-// the given dependencies; the caller resets *a.next before the node runs.
+// Add a scoring kernel node to graph g after the given dependencies; the
+// caller resets *a.next before the node runs.
 cudaError_t add_score_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                            const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaGraphNode_t* out);
 

@@ -435,7 +435,6 @@ __device__ __forceinline__ void zmin(uint32_t* zbuf, int idx, unsigned d, int tr
 // ---- resolve queue and per-warp cell groups -------------------------------
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
-constexpr int kChunk = 1;         // consecutive hypotheses a block takes per counter fetch (measured: 1 is best)
 constexpr int kGroups = 1;        // distinct query cells looked up together per warp
 constexpr int kCellCache = 64;    // per-warp cache of recent 27-cell lookups (direct mapped)
 
@@ -1092,18 +1091,43 @@ __host__ __device__ inline SmemLayout smem_layout(int zcap_words, int mark_words
     return L;
 }
 
-// Persistent scoring kernel: each block repeatedly takes the next hypothesis
-// index from a device counter (zero at launch) and scores it.  SINGLE: one job,
-// read from the kernel parameters; otherwise the job holding the hypothesis is
-// found in the job table and copied to shared memory.
-template <int NT, bool SINGLE>
+// Claim one vertex-cache slot from a pool of nslots (bit set = in use).
+// Blocks of every scoring kernel that runs at the same time with the same
+// launch shape draw from one pool sized for the device's resident blocks, so
+// a free slot exists; should none be found the block runs without the cache
+// (same results).  Bounded: every failed attempt adds a bit to `seen`.
+__device__ int claim_vslot(unsigned* mask, int nslots)
+{
+    const int words = (nslots + 31) >> 5;
+    for (int k = 0; k < words; ++k) {
+        const int w = (int)((blockIdx.x + k) % words);
+        const int rem = nslots - 32 * w;
+        const unsigned valid = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+        unsigned seen = *(volatile unsigned*)&mask[w];
+        while (~seen & valid) {
+            const int b = __ffs(~seen & valid) - 1;
+            const unsigned prev = atomicOr(&mask[w], 1u << b);
+            if (!(prev & (1u << b))) {
+                __threadfence();    // the previous holder's writes precede ours
+                return 32 * w + b;
+            }
+            seen |= prev | (1u << b);
+        }
+    }
+    return -1;
+}
+
+// Persistent scoring kernel over one job: each block repeatedly takes the
+// next hypothesis index from a device counter (zero at launch) and scores
+// it.  The job is read from the kernel parameters, so its fields are
+// constant-bank operands.
+template <int NT>
 __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
-    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_job_idx;
-    __shared__ long long s_h, s_local;
-    __shared__ Job s_job;
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_slot;
+    __shared__ long long s_h;
     __shared__ int s_red[3][NT / 32];
 
     SmemLayout L = smem_layout(a.zcap_words, a.mark_words, NT);
@@ -1114,43 +1138,20 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.probe = reinterpret_cast<WarpProbe*>(smem + L.probe);
     S.stage = reinterpret_cast<TriStage*>(smem + L.probe);
     S.next_batch = &s_next;
-    unsigned long long* vc = a.vcache ? a.vcache + (size_t)blockIdx.x * a.vstride : nullptr;
-    if (SINGLE) {
-        // kChunk consecutive hypotheses per fetch: neighbouring poses touch the
-        // same observed cells, so the block's L1 keeps serving them
-        for (;;) {
-            if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.next, (unsigned)kChunk);
-            __syncthreads();
-            const long long h0 = s_h;
-            if (h0 >= a.n) break;
-            const long long h1 = min(h0 + kChunk, a.n);
-            for (long long h = h0; h < h1; ++h)
-                score_one<NT>(a, a.job0, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
-        }
-        return;
-    }
-    int cur = -1;
+    if (threadIdx.x == 0) s_slot = a.vcache ? claim_vslot(a.vmask, a.vslots) : -1;
+    __syncthreads();
+    unsigned long long* vc = s_slot >= 0 ? a.vcache + (size_t)s_slot * a.vstride : nullptr;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const long long h = (long long)atomicAdd(a.next, 1u);
-            s_h = h;
-            if (h < a.n) {
-                // the job holding h: binary search of the inclusive prefix sums
-                int lo = 0, hi = a.n_jobs - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (a.job_end[mid] > h) hi = mid;
-                    else lo = mid + 1;
-                }
-                s_job_idx = lo;
-                if (lo != cur) s_job = a.jobs[lo];
-                s_local = h - (a.job_end[lo] - s_job.n);
-            }
-        }
+        if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.next, 1u);
         __syncthreads();
-        if (s_h >= a.n) break;
-        cur = s_job_idx;
-        score_one<NT>(a, s_job, s_local, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+        const long long h = s_h;
+        if (h >= a.n) break;
+        score_one<NT>(a, a.job, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+    }
+    // every thread has passed the barrier after its last use of the slot
+    if (threadIdx.x == 0 && s_slot >= 0) {
+        __threadfence();
+        atomicAnd(&a.vmask[s_slot >> 5], ~(1u << (s_slot & 31)));
     }
 }
 
@@ -1159,16 +1160,15 @@ size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
     return smem_layout(cfg.zcap_words, mark_words, cfg.threads).total;
 }
 
-template <int NT, bool SINGLE>
+template <int NT>
 static int score_grid_nt(size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_score<NT, SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT, SINGLE>, NT, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT>, NT, smem) != cudaSuccess)
         return -1;
     return max(1, per) * max(1, sms);
 }
@@ -1176,27 +1176,20 @@ static int score_grid_nt(size_t smem)
 int score_grid(const ScoreConfig& cfg, int mark_words)
 {
     size_t smem = score_smem_bytes(cfg, mark_words);
-    int g1, g2;
     switch (cfg.threads) {
-    case 128: g1 = score_grid_nt<128, true>(smem); g2 = score_grid_nt<128, false>(smem); break;
-    case 512: g1 = score_grid_nt<512, true>(smem); g2 = score_grid_nt<512, false>(smem); break;
-    default: g1 = score_grid_nt<256, true>(smem); g2 = score_grid_nt<256, false>(smem); break;
+    case 128: return score_grid_nt<128>(smem);
+    case 512: return score_grid_nt<512>(smem);
+    default: return score_grid_nt<256>(smem);
     }
-    return min(g1, g2);
 }
 
 template <int NT>
 static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s)
 {
-    size_t smem = score_smem_bytes(cfg, a.mark_words);
-    const bool single = a.n_jobs == 1;
-    cudaError_t e = single ? cudaFuncSetAttribute(k_score<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                           : cudaFuncSetAttribute(k_score<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = score_smem_bytes(cfg, a.mark_words);
+    cudaError_t e = cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.next, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-    int g = (int)(a.n < grid ? a.n : grid);
-    if (single) k_score<NT, true><<<g, NT, smem, s>>>(a);
-    else k_score<NT, false><<<g, NT, smem, s>>>(a);
+    k_score<NT><<<(unsigned)(a.n < grid ? a.n : grid), NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1206,13 +1199,12 @@ static cudaError_t add_score_node_nt(cudaGraph_t g, const cudaGraphNode_t* deps,
                                      cudaGraphNode_t* out)
 {
     const size_t smem = score_smem_bytes(cfg, a.mark_words);
-    cudaError_t e = cudaFuncSetAttribute(k_score<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ScoreArgs copy = a;
     void* args[] = {&copy};
     cudaKernelNodeParams kp{};
-    kp.func = (void*)k_score<NT, true>;
+    kp.func = (void*)k_score<NT>;
     kp.gridDim = dim3((unsigned)(a.n < grid ? a.n : grid));
     kp.blockDim = dim3(NT);
     kp.sharedMemBytes = (unsigned)smem;
@@ -1223,7 +1215,7 @@ static cudaError_t add_score_node_nt(cudaGraph_t g, const cudaGraphNode_t* deps,
 cudaError_t add_score_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                            const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaGraphNode_t* out)
 {
-    if (a.n_jobs != 1 || a.n <= 0 || a.n > 0xFFFFFFF0ll) return cudaErrorInvalidValue;
+    if (a.n <= 0 || a.n > 0xFFFFFFF0ll || grid <= 0) return cudaErrorInvalidValue;
     switch (cfg.threads) {
     case 128: return add_score_node_nt<128>(g, deps, ndeps, a, cfg, grid, out);
     case 512: return add_score_node_nt<512>(g, deps, ndeps, a, cfg, grid, out);
@@ -1234,6 +1226,7 @@ cudaError_t add_score_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd
 cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
+    if (grid <= 0) return cudaErrorInvalidValue;
     if (a.n > 0xFFFFFFF0ll) return cudaErrorInvalidValue;   // the counter is 32-bit
     switch (cfg.threads) {
     case 128: return launch_score_nt<128>(a, cfg, grid, s);

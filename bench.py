@@ -507,7 +507,7 @@ def main():
         "config": {"workload": desc, "hypotheses_per_step": n_step, "l2": "flushed between steps (512 MiB write)",
                    "launch": {"threads": 256, "zbuf_words": 16384}},
         "latency_ms": {"search_p50": lat[len(lat) // 2], "search_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                       "what": "one object's 29,584-hypothesis search (score + argmin), device-timed"},
+                       "what": f"one object's {len(reqs[0].poses):,}-hypothesis search (score + argmin), device-timed"},
         "e2e": {"value": world * n_step / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": a.steps * 2 * len(reqs),

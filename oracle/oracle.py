@@ -68,6 +68,14 @@ def lib():
         L.or_ciede2000.argtypes = [P, P, P]
         L.or_ciede2000.restype = C.c_float
         L.or_num_threads.restype = C.c_int
+        L.or_gicp.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, C.c_int32]
+        L.or_triangle_normal.argtypes = [P, C.c_int32, P]
+        L.or_observed_normal.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, P]
+        L.or_gicp_terms.argtypes = [P, P, P, P, P, P, C.c_float, P]
+        L.or_gicp_quantise.argtypes = [C.c_float]
+        L.or_gicp_quantise.restype = C.c_int64
+        L.or_gicp_solve.argtypes = [P, P]
+        L.or_gicp_rotation.argtypes = [P, P]
         _lib = L
     return _lib
 
@@ -183,6 +191,72 @@ def ciede2000(lab1, lab2):
     gap = C.c_float()
     v = lib().or_ciede2000(_ptr(a), _ptr(b), C.byref(gap))
     return float(v), float(gap.value)
+
+
+class _GicpParams(C.Structure):
+    _fields_ = [("max_iters", C.c_int32), ("epsilon", C.c_float), ("normal_jump", C.c_int32),
+                ("min_corr", C.c_int32), ("stop_rot", C.c_float), ("stop_trans", C.c_float)]
+
+
+GICP_DEFAULTS = dict(max_iters=10, epsilon=1e-3, normal_jump=200, min_corr=6, stop_rot=1e-5,
+                     stop_trans=1e-5)
+GICP_NVAL = 28
+
+
+def gicp(scene: OracleScene, mesh: OracleMesh, poses, label=-1, roi=None, threads=0, **params):
+    """Refine poses by M2M GICP: (poses_out (n,12) float32, info (n,2) int32 =
+    [updates applied, correspondences of the last iteration])."""
+    kw = dict(GICP_DEFAULTS)
+    kw.update(params)
+    gp = _GicpParams(**kw)
+    poses = np.ascontiguousarray(poses, np.float32).reshape(-1, 12)
+    n = poses.shape[0]
+    roi = np.asarray(roi if roi is not None else (0, 0, scene.W, scene.H), np.int32)
+    out = np.zeros((n, 12), np.float32)
+    info = np.zeros((n, 2), np.int32)
+    rc = lib().or_gicp(C.byref(scene.s), C.byref(mesh.m), label, _ptr(roi), _ptr(poses), n,
+                       C.byref(gp), _ptr(out), _ptr(info), threads)
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return out, info
+
+
+def triangle_normal(mesh: OracleMesh, t):
+    out = np.empty(3, np.float32)
+    lib().or_triangle_normal(C.byref(mesh.m), int(t), _ptr(out))
+    return out
+
+
+def observed_normal(scene: OracleScene, u, v, normal_jump=200):
+    out = np.empty(3, np.float32)
+    lib().or_observed_normal(C.byref(scene.s), int(normal_jump), int(u), int(v), _ptr(out))
+    return out
+
+
+def gicp_terms(Rf, tf, a, na, b, nb, eps=1e-3):
+    """(ok, terms[28]) of one correspondence."""
+    arrs = [np.ascontiguousarray(x, np.float32).reshape(-1) for x in (Rf, tf, a, na, b, nb)]
+    out = np.zeros(GICP_NVAL, np.float32)
+    ok = lib().or_gicp_terms(*[_ptr(x) for x in arrs], C.c_float(eps), _ptr(out))
+    return bool(ok), out
+
+
+def gicp_quantise(x):
+    return int(lib().or_gicp_quantise(C.c_float(x)))
+
+
+def gicp_solve(S):
+    S = np.ascontiguousarray(S, np.int64).reshape(GICP_NVAL)
+    xi = np.zeros(6, np.float64)
+    ok = lib().or_gicp_solve(_ptr(S), _ptr(xi))
+    return bool(ok), xi
+
+
+def gicp_rotation(w):
+    w = np.ascontiguousarray(w, np.float64).reshape(3)
+    R = np.zeros(9, np.float64)
+    lib().or_gicp_rotation(_ptr(w), _ptr(R))
+    return R.reshape(3, 3)
 
 
 def num_threads():

@@ -39,6 +39,9 @@
  * interpolation; occluder margin m; nearest-neighbour ties to the lowest pixel
  * index; V(h) is the object's inscribed cylinder about its z axis, or
  * labels == object label inside the ROI when labels are used (Sec. V-C).
+ *
+ * The last section refines hypotheses by M2M GICP (Sec. IV-A) before they
+ * are rendered again; its readings are listed there.
  */
 #include <math.h>
 #include <stdint.h>
@@ -583,4 +586,380 @@ int or_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* M2M GICP refinement (Sec. IV-A "Parallel M2M GICP"; Sec. III-A: local   */
+/* ICP adjusts each successor's pose before it is rendered again)          */
+/* ---------------------------------------------------------------------- */
+/*
+ * Source: the rendered cloud R \ C of the hypothesis at its input pose (the
+ * kept points of the scorer), each point carrying the unit normal of the
+ * triangle it was rendered from.  Target: the observed cloud I with a normal
+ * per pixel from central differences of the depth image.  GICP models every
+ * point as a Gaussian flattened along its surface normal,
+ * C(n) = I - (1 - eps) n n^T (a zero normal gives C = I), and minimises
+ * sum_i r_i^T (C_b + R C_a R^T)^-1 r_i over a rigid increment by
+ * Gauss-Newton, with r = b - (R a + t) for the nearest observed point b
+ * within delta of the moved source point.
+ *
+ * Readings (the paper names the method and its GPU parts only): covariances
+ * from the exact surface (mesh triangle) and from image-space neighbours;
+ * a fixed correspondence radius delta (the hash radius of the observation);
+ * the increment linearised as (I + [w]x) p + v; per-correspondence terms in
+ * binary32 in the order written, quantised to integer multiples of 2^-24
+ * and summed exactly in int64 (so that any summation order gives the same
+ * sums); the 6x6 system solved by Cholesky in binary64; the rotation update
+ * from the quaternion (1, w/2) normalised (rational operations and one square
+ * root).  Iteration stops after max_iters updates, when a step is below the
+ * thresholds, with fewer than min_corr correspondences, or when the system
+ * is not positive definite.
+ */
+
+#define OR_GICP_NVAL 28        /* H upper triangle (21), g (6), sum r^T M r (1) */
+#define OR_GICP_SCALE 16777216.0f
+#define OR_GICP_LIMIT 1048576.0f   /* |term| bound: a point beyond it is skipped */
+
+typedef struct {
+    int32_t max_iters;
+    float epsilon;            /* plane regulariser of the covariances     */
+    int32_t normal_jump;      /* max |d_neighbour - d_centre|, 0.1 mm     */
+    int32_t min_corr;
+    float stop_rot;           /* radians                                  */
+    float stop_trans;         /* metres                                   */
+} or_gicp_params;
+
+/* Unit normal of mesh triangle t in the object frame (vertex order as
+ * stored): normalise((v1 - v0) x (v2 - v0)); zero for a degenerate one. */
+void or_triangle_normal(const or_mesh *m, int32_t t, float n[3])
+{
+    const float *a = m->verts + 3 * m->tris[3 * t + 0];
+    const float *b = m->verts + 3 * m->tris[3 * t + 1];
+    const float *c = m->verts + 3 * m->tris[3 * t + 2];
+    float e1x = b[0] - a[0], e1y = b[1] - a[1], e1z = b[2] - a[2];
+    float e2x = c[0] - a[0], e2y = c[1] - a[1], e2z = c[2] - a[2];
+    float cx = e1y * e2z - e1z * e2y;
+    float cy = e1z * e2x - e1x * e2z;
+    float cz = e1x * e2y - e1y * e2x;
+    float len2 = (cx * cx + cy * cy) + cz * cz;
+    if (!(len2 > 0.0f)) {
+        n[0] = n[1] = n[2] = 0.0f;
+        return;
+    }
+    float inv = 1.0f / sqrtf(len2);
+    n[0] = cx * inv;
+    n[1] = cy * inv;
+    n[2] = cz * inv;
+}
+
+/* Normal of the observed surface at pixel (u, v): the cross product of the
+ * central differences P(u+1,v) - P(u-1,v) and P(u,v+1) - P(u,v-1) of the
+ * back-projected depth, normalised.  Zero when the pixel or one of its four
+ * neighbours is outside the image, has no depth, or differs from the centre
+ * depth by more than normal_jump. */
+void or_observed_normal(const or_scene *sc, int32_t normal_jump, int64_t u, int64_t v, float n[3])
+{
+    n[0] = n[1] = n[2] = 0.0f;
+    if (u < 1 || v < 1 || u + 1 >= sc->W || v + 1 >= sc->H)
+        return;
+    int64_t W = sc->W;
+    int64_t dc = sc->depth[v * W + u];
+    int64_t du[4] = {u - 1, u + 1, u, u};
+    int64_t dv[4] = {v, v, v - 1, v + 1};
+    float P[4][3];
+    if (dc == 0)
+        return;
+    for (int k = 0; k < 4; k++) {
+        int64_t d = sc->depth[dv[k] * W + du[k]];
+        if (d == 0 || llabs(d - dc) > normal_jump)
+            return;
+        back_project(sc, du[k], dv[k], d, P[k]);
+    }
+    float ax = P[1][0] - P[0][0], ay = P[1][1] - P[0][1], az = P[1][2] - P[0][2];
+    float bx = P[3][0] - P[2][0], by = P[3][1] - P[2][1], bz = P[3][2] - P[2][2];
+    float cx = ay * bz - az * by;
+    float cy = az * bx - ax * bz;
+    float cz = ax * by - ay * bx;
+    float len2 = (cx * cx + cy * cy) + cz * cz;
+    if (!(len2 > 0.0f))
+        return;
+    float inv = 1.0f / sqrtf(len2);
+    n[0] = cx * inv;
+    n[1] = cy * inv;
+    n[2] = cz * inv;
+}
+
+/* The 28 binary32 terms of one correspondence: source point a with normal na
+ * moved by (Rf, tf) to p, matched to observed b with normal nb.  Returns 0
+ * (no terms) when the combined covariance is not positive or a term exceeds
+ * the bound.  Term order: H(0,0..5), H(1,1..5), ..., H(5,5), g(0..5), r^T M r. */
+int or_gicp_terms(const float Rf[9], const float tf[3], const float a[3], const float na[3],
+                  const float b[3], const float nb[3], float eps, float out[OR_GICP_NVAL])
+{
+    float p0 = ((Rf[0] * a[0] + Rf[1] * a[1]) + Rf[2] * a[2]) + tf[0];
+    float p1 = ((Rf[3] * a[0] + Rf[4] * a[1]) + Rf[5] * a[2]) + tf[1];
+    float p2 = ((Rf[6] * a[0] + Rf[7] * a[1]) + Rf[8] * a[2]) + tf[2];
+    float m0 = (Rf[0] * na[0] + Rf[1] * na[1]) + Rf[2] * na[2];
+    float m1 = (Rf[3] * na[0] + Rf[4] * na[1]) + Rf[5] * na[2];
+    float m2 = (Rf[6] * na[0] + Rf[7] * na[1]) + Rf[8] * na[2];
+    float e = 1.0f - eps;
+    /* C = 2 I - e (nb nb^T + m m^T) */
+    float c00 = 2.0f - e * (nb[0] * nb[0] + m0 * m0);
+    float c11 = 2.0f - e * (nb[1] * nb[1] + m1 * m1);
+    float c22 = 2.0f - e * (nb[2] * nb[2] + m2 * m2);
+    float c01 = -(e * (nb[0] * nb[1] + m0 * m1));
+    float c02 = -(e * (nb[0] * nb[2] + m0 * m2));
+    float c12 = -(e * (nb[1] * nb[2] + m1 * m2));
+    /* M = C^-1 by the adjugate */
+    float a00 = c11 * c22 - c12 * c12;
+    float a01 = c02 * c12 - c01 * c22;
+    float a02 = c01 * c12 - c02 * c11;
+    float a11 = c00 * c22 - c02 * c02;
+    float a12 = c01 * c02 - c00 * c12;
+    float a22 = c00 * c11 - c01 * c01;
+    float det = (c00 * a00 + c01 * a01) + c02 * a02;
+    if (!(det > 0.0f))
+        return 0;
+    float id = 1.0f / det;
+    float M[3][3];
+    M[0][0] = a00 * id; M[0][1] = a01 * id; M[0][2] = a02 * id;
+    M[1][0] = M[0][1];  M[1][1] = a11 * id; M[1][2] = a12 * id;
+    M[2][0] = M[0][2];  M[2][1] = M[1][2];  M[2][2] = a22 * id;
+    float r[3] = {b[0] - p0, b[1] - p1, b[2] - p2};
+    /* Jacobian of r w.r.t. (w, v): [ [p]x , -I ]; MA = M [p]x */
+    float MA[3][3];
+    for (int i = 0; i < 3; i++) {
+        MA[i][0] = M[i][1] * p2 - M[i][2] * p1;
+        MA[i][1] = M[i][2] * p0 - M[i][0] * p2;
+        MA[i][2] = M[i][0] * p1 - M[i][1] * p0;
+    }
+    /* [p]x^T M [p]x */
+    float AMA[3][3];
+    for (int j = 0; j < 3; j++) {
+        AMA[0][j] = p2 * MA[1][j] - p1 * MA[2][j];
+        AMA[1][j] = p0 * MA[2][j] - p2 * MA[0][j];
+        AMA[2][j] = p1 * MA[0][j] - p0 * MA[1][j];
+    }
+    float Mr[3];
+    for (int i = 0; i < 3; i++)
+        Mr[i] = (M[i][0] * r[0] + M[i][1] * r[1]) + M[i][2] * r[2];
+    float H[6][6];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            H[i][j] = AMA[i][j];
+            H[i][3 + j] = -MA[j][i];
+            H[3 + i][3 + j] = M[i][j];
+        }
+    int k = 0;
+    for (int i = 0; i < 6; i++)
+        for (int j = i; j < 6; j++)
+            out[k++] = H[i][j];
+    out[k++] = p2 * Mr[1] - p1 * Mr[2];
+    out[k++] = p0 * Mr[2] - p2 * Mr[0];
+    out[k++] = p1 * Mr[0] - p0 * Mr[1];
+    out[k++] = -Mr[0];
+    out[k++] = -Mr[1];
+    out[k++] = -Mr[2];
+    out[k++] = (r[0] * Mr[0] + r[1] * Mr[1]) + r[2] * Mr[2];
+    for (int i = 0; i < OR_GICP_NVAL; i++)
+        if (!(fabsf(out[i]) < OR_GICP_LIMIT))
+            return 0;
+    return 1;
+}
+
+/* Quantise a term to an integer multiple of 2^-24 (ties to even). */
+int64_t or_gicp_quantise(float x)
+{
+    return (int64_t)llrintf(x * OR_GICP_SCALE);
+}
+
+/* Solve the 6x6 system of the quantised sums: H xi = -g by Cholesky in
+ * binary64.  Returns 0 when H is not positive definite. */
+int or_gicp_solve(const int64_t S[OR_GICP_NVAL], double xi[6])
+{
+    double H[6][6], g[6], L[6][6], y[6];
+    int k = 0;
+    for (int i = 0; i < 6; i++)
+        for (int j = i; j < 6; j++) {
+            H[i][j] = (double)S[k++] / 16777216.0;
+            H[j][i] = H[i][j];
+        }
+    for (int i = 0; i < 6; i++)
+        g[i] = (double)S[k++] / 16777216.0;
+    for (int j = 0; j < 6; j++) {
+        double s = H[j][j];
+        for (int q = 0; q < j; q++)
+            s = s - L[j][q] * L[j][q];
+        if (!(s > 0.0))
+            return 0;
+        L[j][j] = sqrt(s);
+        for (int i = j + 1; i < 6; i++) {
+            double t = H[i][j];
+            for (int q = 0; q < j; q++)
+                t = t - L[i][q] * L[j][q];
+            L[i][j] = t / L[j][j];
+        }
+    }
+    for (int i = 0; i < 6; i++) {
+        double t = -g[i];
+        for (int q = 0; q < i; q++)
+            t = t - L[i][q] * y[q];
+        y[i] = t / L[i][i];
+    }
+    for (int i = 5; i >= 0; i--) {
+        double t = y[i];
+        for (int q = i + 1; q < 6; q++)
+            t = t - L[q][i] * xi[q];
+        xi[i] = t / L[i][i];
+    }
+    return 1;
+}
+
+/* Rotation of the quaternion (1, w/2) normalised: the rotation about w by
+ * 2 atan(|w| / 2).  Row-major 3x3. */
+void or_gicp_rotation(const double w[3], double R[9])
+{
+    double hx = w[0] * 0.5, hy = w[1] * 0.5, hz = w[2] * 0.5;
+    double nrm = sqrt(((1.0 + hx * hx) + hy * hy) + hz * hz);
+    double qw = 1.0 / nrm, qx = hx / nrm, qy = hy / nrm, qz = hz / nrm;
+    R[0] = 1.0 - 2.0 * (qy * qy + qz * qz);
+    R[1] = 2.0 * (qx * qy - qw * qz);
+    R[2] = 2.0 * (qx * qz + qw * qy);
+    R[3] = 2.0 * (qx * qy + qw * qz);
+    R[4] = 1.0 - 2.0 * (qx * qx + qz * qz);
+    R[5] = 2.0 * (qy * qz - qw * qx);
+    R[6] = 2.0 * (qx * qz - qw * qy);
+    R[7] = 2.0 * (qy * qz + qw * qx);
+    R[8] = 1.0 - 2.0 * (qx * qx + qy * qy);
+}
+
+/* Brute-force nearest observed point of p within delta (Eq. 2's search):
+ * index into the observed list (pixel order, ties to the lowest), or -1. */
+static int64_t nearest_within(const float *Ixyz, int64_t nI, const float p[3], float delta2)
+{
+    float best = INFINITY;
+    int64_t bj = -1;
+    for (int64_t j = 0; j < nI; j++) {
+        const float *q = Ixyz + 3 * j;
+        float dx = p[0] - q[0], dy = p[1] - q[1], dz = p[2] - q[2];
+        float d2 = (dx * dx + dy * dy) + dz * dz;
+        if (d2 < best) { best = d2; bj = j; }
+    }
+    return (bj >= 0 && best <= delta2) ? bj : -1;
+}
+
+/* Refine n hypotheses.  poses_out (n*12) receives the refined poses, info
+ * (n*2, may be NULL) the number of updates applied and the correspondences
+ * of the last iteration evaluated.  Returns 0, or -2 on allocation failure. */
+int or_gicp(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t roi[4],
+            const float *poses, int64_t n, const or_gicp_params *gp, float *poses_out,
+            int32_t *info, int32_t n_threads)
+{
+    int64_t WH = (int64_t)sc->W * sc->H;
+    float *Ixyz = malloc(sizeof(float) * 3 * (WH + 1));
+    int32_t *Ipix = malloc(sizeof(int32_t) * (WH + 1));
+    float *Inrm = malloc(sizeof(float) * 3 * (WH + 1));
+    if (!Ixyz || !Ipix || !Inrm) {
+        free(Ixyz); free(Ipix); free(Inrm);
+        return -2;
+    }
+    int64_t nI = or_observed_points(sc, Ixyz, NULL, Ipix);
+    for (int64_t j = 0; j < nI; j++)
+        or_observed_normal(sc, gp->normal_jump, Ipix[j] % sc->W, Ipix[j] / sc->W, Inrm + 3 * j);
+    float delta2 = sc->delta * sc->delta;
+    int rc = 0;
+#ifdef _OPENMP
+    if (n_threads > 0)
+        omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+#pragma omp parallel
+    {
+        uint64_t *keys = malloc(sizeof(uint64_t) * WH);
+        float *Rxyz = malloc(sizeof(float) * 3 * WH);
+        float *Rnrm = malloc(sizeof(float) * 3 * WH);
+        int32_t *Rpix = malloc(sizeof(int32_t) * WH);
+        int ok = keys && Rxyz && Rnrm && Rpix;
+        if (!ok) {
+#pragma omp atomic write
+            rc = -2;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t h = 0; h < n; h++) {
+            if (!ok)
+                continue;
+            const float *P = poses + 12 * h;
+            or_render_keys(sc, m, P, roi, keys, NULL);
+            int64_t L = or_rendered_points(sc, m, P, label, keys, Rxyz, NULL, Rpix);
+            for (int64_t k = 0; k < L; k++) {
+                float no[3];
+                or_triangle_normal(m, (int32_t)(keys[Rpix[k]] & 0xffffffffu), no);
+                float *nc = Rnrm + 3 * k;
+                nc[0] = (P[0] * no[0] + P[1] * no[1]) + P[2] * no[2];
+                nc[1] = (P[4] * no[0] + P[5] * no[1]) + P[6] * no[2];
+                nc[2] = (P[8] * no[0] + P[9] * no[1]) + P[10] * no[2];
+            }
+            double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, t[3] = {0, 0, 0};
+            int32_t updates = 0, last_corr = 0;
+            for (int32_t it = 0; it < gp->max_iters; it++) {
+                float Rf[9], tf[3];
+                for (int i = 0; i < 9; i++) Rf[i] = (float)R[i];
+                for (int i = 0; i < 3; i++) tf[i] = (float)t[i];
+                int64_t S[OR_GICP_NVAL] = {0};
+                int32_t corr = 0;
+                for (int64_t k = 0; k < L; k++) {
+                    const float *a = Rxyz + 3 * k;
+                    float p[3];
+                    p[0] = ((Rf[0] * a[0] + Rf[1] * a[1]) + Rf[2] * a[2]) + tf[0];
+                    p[1] = ((Rf[3] * a[0] + Rf[4] * a[1]) + Rf[5] * a[2]) + tf[1];
+                    p[2] = ((Rf[6] * a[0] + Rf[7] * a[1]) + Rf[8] * a[2]) + tf[2];
+                    int64_t j = nearest_within(Ixyz, nI, p, delta2);
+                    if (j < 0)
+                        continue;
+                    float terms[OR_GICP_NVAL];
+                    if (!or_gicp_terms(Rf, tf, a, Rnrm + 3 * k, Ixyz + 3 * j, Inrm + 3 * j,
+                                       gp->epsilon, terms))
+                        continue;
+                    for (int i = 0; i < OR_GICP_NVAL; i++)
+                        S[i] += or_gicp_quantise(terms[i]);
+                    corr++;
+                }
+                last_corr = corr;
+                double xi[6];
+                if (corr < gp->min_corr || !or_gicp_solve(S, xi))
+                    break;
+                double dR[9], R2[9], t2[3];
+                or_gicp_rotation(xi, dR);
+                for (int i = 0; i < 3; i++) {
+                    for (int j = 0; j < 3; j++)
+                        R2[3 * i + j] = (dR[3 * i] * R[j] + dR[3 * i + 1] * R[3 + j]) + dR[3 * i + 2] * R[6 + j];
+                    t2[i] = ((dR[3 * i] * t[0] + dR[3 * i + 1] * t[1]) + dR[3 * i + 2] * t[2]) + xi[3 + i];
+                }
+                memcpy(R, R2, sizeof(R));
+                memcpy(t, t2, sizeof(t));
+                updates++;
+                double sr = (double)gp->stop_rot, st = (double)gp->stop_trans;
+                if ((xi[0] * xi[0] + xi[1] * xi[1]) + xi[2] * xi[2] < sr * sr &&
+                    (xi[3] * xi[3] + xi[4] * xi[4]) + xi[5] * xi[5] < st * st)
+                    break;
+            }
+            /* refined pose = increment o input pose */
+            float *Q = poses_out + 12 * h;
+            for (int i = 0; i < 3; i++) {
+                for (int j = 0; j < 3; j++)
+                    Q[4 * i + j] = (float)((R[3 * i] * (double)P[j] + R[3 * i + 1] * (double)P[4 + j])
+                                           + R[3 * i + 2] * (double)P[8 + j]);
+                Q[4 * i + 3] = (float)(((R[3 * i] * (double)P[3] + R[3 * i + 1] * (double)P[7])
+                                        + R[3 * i + 2] * (double)P[11]) + t[i]);
+            }
+            if (info) {
+                info[2 * h] = updates;
+                info[2 * h + 1] = last_corr;
+            }
+        }
+        free(keys); free(Rxyz); free(Rnrm); free(Rpix);
+    }
+    free(Ixyz); free(Ipix); free(Inrm);
+    return rc;
 }

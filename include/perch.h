@@ -338,6 +338,54 @@ PERCH_API perch_status perch_pose_proposals(perch_ctx *ctx, int32_t scene_id, in
                                             int32_t N, int32_t K, float *poses, int32_t *z_range,
                                             void *cuda_stream);
 
+/* ---- M2M GICP refinement (Sec. IV-A "Parallel M2M GICP"; Sec. III-A) ------------
+ * Each hypothesis' pose is adjusted by generalised ICP before it is scored
+ * (rendered again) with perch_score_hypotheses:
+ *   source  = the hypothesis' rendered cloud R \ C at the input pose (visible,
+ *             not occluded, on the scene's stride lattice, inside the ROI),
+ *             each point with the camera-frame normal of its mesh triangle;
+ *   target  = the observed cloud I of the scene, each point with the normal of
+ *             the cross product of the depth image's central differences
+ *             (zero at the border, next to a pixel without depth, or where a
+ *             neighbour's depth differs by more than normal_max_jump_units);
+ *   model   = every point a Gaussian flattened along its normal,
+ *             C(n) = I - (1 - epsilon) n n^T (zero normal: C = I);
+ *   step    = Gauss-Newton on sum r^T (C_b + R C_a R^T)^-1 r, r = b - (R a + t),
+ *             b the nearest observed point within the scene's delta (the
+ *             correspondence radius: set up a separate observation with the
+ *             radius wanted), the increment linearised as (I + [w]x) p + v;
+ *             the rotation update is the quaternion (1, w/2) normalised.
+ * The per-correspondence terms are binary32, rounded to multiples of 2^-24 and
+ * summed exactly in 64-bit integers; the 6x6 system is solved by Cholesky in
+ * binary64.  So the result does not depend on the order of the sums: it is
+ * bit-identical from run to run and to a sequential evaluation of the same
+ * definitions.  A hypothesis stops after max_iterations updates, after a step
+ * below both stop thresholds (that step is applied), with fewer than
+ * min_correspondences matches, or when the system is not positive definite.
+ * poses_out (n*12) receives R_inc R_0 | R_inc t_0 + t_inc rounded to binary32;
+ * info (n*2 int32, may be NULL) the updates applied and the matches of the
+ * last iteration evaluated, or (-1, source points) for a hypothesis whose
+ * source cloud exceeded max_source_points (its pose is returned unchanged and
+ * the call reports PERCH_E_INVALID when it synchronises).
+ * cuda_stream NULL: poses, poses_out and info are HOST pointers, synchronous;
+ * otherwise DEVICE pointers enqueued on that stream (no host synchronisation).
+ * poses and poses_out may be the same array. */
+typedef struct {
+    int32_t max_iterations;          /* default 10; 0 returns the poses unchanged   */
+    float epsilon;                   /* default 1e-3, in (0, 1)                     */
+    int32_t normal_max_jump_units;   /* default 200 (2 cm), >= 0                     */
+    int32_t min_correspondences;     /* default 6, >= 1                              */
+    float stop_rotation_rad;         /* default 1e-5                                 */
+    float stop_translation_m;        /* default 1e-5                                 */
+    int32_t max_source_points;       /* per hypothesis; 0 = min(65536, ROI lattice)  */
+} perch_gicp_params;
+
+PERCH_API perch_status perch_default_gicp_params(perch_gicp_params *p);
+PERCH_API perch_status perch_refine_hypotheses(perch_ctx *ctx, int32_t scene_id, int32_t mesh_id,
+                                               int32_t label, const int32_t *roi, const float *poses,
+                                               int64_t n, const perch_gicp_params *params,
+                                               float *poses_out, int32_t *info, void *cuda_stream);
+
 /* Debug view of the rasteriser used by perch_score_hypotheses: the z-buffer of
  * one pose as 64-bit keys (depth << 32) | triangle id, 0xFFFFFFFFFFFFFFFF where
  * nothing is covered.  keys is a HOST buffer of W*H uint64 of the scene; the

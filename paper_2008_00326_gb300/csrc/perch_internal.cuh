@@ -65,7 +65,7 @@ struct ScoreArgs {
 };
 
 // Error bits written by kernels into the context's error word.
-enum : int { kErrKeyRange = 1, kErrMarkCap = 2, kErrHashFull = 4 };
+enum : int { kErrKeyRange = 1, kErrMarkCap = 2, kErrHashFull = 4, kErrSourceCap = 8, kErrNoSlot = 16 };
 
 // Launch configuration of the scoring kernel (chosen by the host; the
 // autotuner searches over these).
@@ -85,6 +85,33 @@ cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, c
 // caller resets *a.next before the node runs.
 cudaError_t add_score_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                            const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaGraphNode_t* out);
+
+// M2M GICP refinement (Sec. IV-A): one launch refines the hypotheses of one
+// job; each block holds its hypothesis' source cloud in a slot of `src`.
+struct GicpArgs {
+    Job job;                  // poses = input poses (device); costs unused
+    long long n;
+    int zcap_words;
+    int* err;
+    unsigned* next;           // hypothesis counter, zeroed before the launch
+    unsigned* smask;          // slot mask, (slots + 31) / 32 words, zero when idle
+    int slots;
+    float4* src;              // slots x src_cap x (point, normal)
+    int src_cap;
+    unsigned long long* vcache;  // slots x vstride vertex records, or nullptr
+    long long vstride;
+    const float4* nrm;        // observed normal per pixel (H*W)
+    int max_iters, min_corr;
+    float epsilon, stop_rot, stop_trans;
+    float* poses_out;         // n*12 (device)
+    int32_t* info;            // n*2 (device) or nullptr
+};
+
+size_t gicp_smem_bytes(int zcap_words);
+int gicp_grid(int zcap_words);
+cudaError_t launch_gicp(const GicpArgs& a, int grid, cudaStream_t s);
+// Observed normal per pixel from central differences of the depth image.
+cudaError_t launch_obs_normals(const DevScene& sc, int normal_jump, float4* nrm, cudaStream_t s);
 
 // Observation build (voxel hash over I).
 struct BuildBuffers {

@@ -751,6 +751,78 @@ __device__ __forceinline__ bool get_triangle(const DevScene& sc, const DevMesh& 
     return setup_triangle(sc, m, P, t, o);
 }
 
+// Rasterise every triangle of mesh m at pose P into the z-buffer tile
+// [tu0,tu1) x [tv0,tv1) (row pitch tw).  A warp sets up 32 triangles (one per
+// lane), stages them in shared memory (TS, 32 entries per warp) and spreads
+// the pixels of their boxes evenly over its lanes (a prefix sum of the box
+// areas, then a binary search per pixel for its triangle).  No barrier inside.
+template <int NT, bool K32, bool VC>
+__device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& mesh, const float* P,
+                                            const unsigned long long* vc, TriStage* TS, uint32_t* zbuf,
+                                            int tu0, int tv0, int tu1, int tv1, int tw, int* err)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = warp * 32; base < mesh.n_tris; base += NT) {
+        const int t = base + lane;
+        int area = 0;
+        TriSetup o;
+        if (t < mesh.n_tris && get_triangle<VC>(sc, mesh, P, vc, t, o)) {
+            int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
+            int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
+            int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
+            int v0 = max(ceil16(ymin), tv0), v1 = min(floor16(ymax), tv1 - 1);
+            if (u0 <= u1 && v0 <= v1) {
+                area = (u1 - u0 + 1) * (v1 - v0 + 1);
+                TriStage& e = TS[lane];
+                for (int k = 0; k < 3; ++k) { e.x[k] = o.x[k]; e.y[k] = o.y[k]; e.iz[k] = o.iz[k]; }
+                e.A = o.A;
+                e.tri = t;
+                e.u0 = u0;
+                e.v0 = v0;
+                e.bw = u1 - u0 + 1;
+                e.owns = (owns(o.x[2] - o.x[1], o.y[2] - o.y[1]) ? 1 : 0) |
+                         (owns(o.x[0] - o.x[2], o.y[0] - o.y[2]) ? 2 : 0) |
+                         (owns(o.x[1] - o.x[0], o.y[1] - o.y[0]) ? 4 : 0);
+            }
+        }
+        int incl = area;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int x = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += x;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        for (int f0 = 0; f0 < total; f0 += 32) {
+            const int f = f0 + lane;
+            // the triangle j whose pixel range holds f: incl[j-1] <= f < incl[j]
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+                if (v <= f) j += step;
+            }
+            const int excl = __shfl_sync(0xffffffffu, incl, j > 0 ? j - 1 : 0);
+            if (f >= total) continue;
+            const TriStage& e = TS[j];
+            const int local = f - (j > 0 ? excl : 0);
+            const int dv = local / e.bw;
+            const int u = e.u0 + (local - dv * e.bw), v = e.v0 + dv;
+            const int sx = 16 * u, sy = 16 * v;
+            const int w0 = edge_fn(e.x[1], e.y[1], e.x[2], e.y[2], sx, sy);
+            const int w1 = edge_fn(e.x[2], e.y[2], e.x[0], e.y[0], sx, sy);
+            const int w2 = edge_fn(e.x[0], e.y[0], e.x[1], e.y[1], sx, sy);
+            const bool cov = (w0 > 0 || (w0 == 0 && (e.owns & 1))) &&
+                             (w1 > 0 || (w1 == 0 && (e.owns & 2))) &&
+                             (w2 > 0 || (w2 == 0 && (e.owns & 4)));
+            unsigned d;
+            if (cov && sample_depth(w0, w1, w2, e.iz, e.A, d))
+                zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, e.tri, err);
+        }
+        __syncwarp();
+    }
+}
+
 // Rasterise, resolve and radius-search the pixel box rbox in z-buffer tiles.
 // J_r is accumulated when count_jr; marks are set for nearest neighbours that
 // fall in rows [mv0, mv1) of the admissible box vbox.
@@ -780,69 +852,7 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
             for (int i = threadIdx.x; i < words; i += NT) zbuf[i] = empty32;
             if (threadIdx.x == 0) *S.next_batch = 0;
             __syncthreads();
-            // ---- raster: a warp sets up 32 triangles (one per lane), stages
-            // them in shared memory and spreads the pixels of their boxes
-            // evenly over its lanes (a prefix sum of the box areas, then a
-            // binary search per pixel for its triangle)
-            for (int base = warp * 32; base < J.m.n_tris; base += NT) {
-                const int t = base + lane;
-                int area = 0;
-                TriSetup o;
-                if (t < J.m.n_tris && get_triangle<VC>(sc, J.m, P, vc, t, o)) {
-                    int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
-                    int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
-                    int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
-                    int v0 = max(ceil16(ymin), tv0), v1 = min(floor16(ymax), tv1 - 1);
-                    if (u0 <= u1 && v0 <= v1) {
-                        area = (u1 - u0 + 1) * (v1 - v0 + 1);
-                        TriStage& e = TS[lane];
-                        for (int k = 0; k < 3; ++k) { e.x[k] = o.x[k]; e.y[k] = o.y[k]; e.iz[k] = o.iz[k]; }
-                        e.A = o.A;
-                        e.tri = t;
-                        e.u0 = u0;
-                        e.v0 = v0;
-                        e.bw = u1 - u0 + 1;
-                        e.owns = (owns(o.x[2] - o.x[1], o.y[2] - o.y[1]) ? 1 : 0) |
-                                 (owns(o.x[0] - o.x[2], o.y[0] - o.y[2]) ? 2 : 0) |
-                                 (owns(o.x[1] - o.x[0], o.y[1] - o.y[0]) ? 4 : 0);
-                    }
-                }
-                int incl = area;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    int x = __shfl_up_sync(0xffffffffu, incl, off);
-                    if (lane >= off) incl += x;
-                }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                __syncwarp();
-                for (int f0 = 0; f0 < total; f0 += 32) {
-                    const int f = f0 + lane;
-                    // the triangle j whose pixel range holds f: incl[j-1] <= f < incl[j]
-                    int j = 0;
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
-                        if (v <= f) j += step;
-                    }
-                    const int excl = __shfl_sync(0xffffffffu, incl, j > 0 ? j - 1 : 0);
-                    if (f >= total) continue;
-                    const TriStage& e = TS[j];
-                    const int local = f - (j > 0 ? excl : 0);
-                    const int dv = local / e.bw;
-                    const int u = e.u0 + (local - dv * e.bw), v = e.v0 + dv;
-                    const int sx = 16 * u, sy = 16 * v;
-                    const int w0 = edge_fn(e.x[1], e.y[1], e.x[2], e.y[2], sx, sy);
-                    const int w1 = edge_fn(e.x[2], e.y[2], e.x[0], e.y[0], sx, sy);
-                    const int w2 = edge_fn(e.x[0], e.y[0], e.x[1], e.y[1], sx, sy);
-                    const bool cov = (w0 > 0 || (w0 == 0 && (e.owns & 1))) &&
-                                     (w1 > 0 || (w1 == 0 && (e.owns & 2))) &&
-                                     (w2 > 0 || (w2 == 0 && (e.owns & 4)));
-                    unsigned d;
-                    if (cov && sample_depth(w0, w1, w2, e.iz, e.A, d))
-                        zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, e.tri, a.err);
-                }
-                __syncwarp();
-            }
+            raster_tile<NT, K32, VC>(sc, J.m, P, vc, TS, zbuf, tu0, tv0, tu1, tv1, tw, a.err);
             __syncthreads();
             if (a.dump) {
                 for (int i = threadIdx.x; i < tpx; i += NT) {
@@ -1233,6 +1243,486 @@ cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, c
     case 512: return launch_score_nt<512>(a, cfg, grid, s);
     default: return launch_score_nt<256>(a, cfg, grid, s);
     }
+}
+
+// ---------------------------------------------------------------------------
+// M2M GICP refinement (Sec. IV-A "Parallel M2M GICP")
+// ---------------------------------------------------------------------------
+//
+// Per hypothesis (one block): render the mesh at the input pose, keep the
+// visible, unoccluded pixels on the stride lattice as the source cloud (each
+// with the camera-frame normal of its triangle), then iterate Gauss-Newton
+// steps of the GICP objective against the observed cloud: every source point
+// moved by the current increment is matched to its nearest observed point
+// within delta (the radius search of the scorer), contributes 28 binary32
+// terms (the 6x6 normal matrix's upper triangle, the gradient and r^T M r)
+// that are rounded to multiples of 2^-24 and summed exactly in int64, and
+// thread 0 solves the system in binary64 and updates the increment.  The
+// fixed-point sums make the result independent of the summation order.
+
+constexpr int kGicpTerms = 28;
+constexpr int kGicpThreads = 256;
+constexpr float kGicpScale = 16777216.0f;    // 2^24
+constexpr float kGicpLimit = 1048576.0f;     // a correspondence with a larger |term| is skipped
+
+__device__ __forceinline__ float3 cross_rn(float3 a, float3 b)
+{
+    return make_float3(__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)),
+                       __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+                       __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+
+__device__ __forceinline__ float3 unit_or_zero(float3 c)
+{
+    const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(c.x, c.x), __fmul_rn(c.y, c.y)), __fmul_rn(c.z, c.z));
+    if (!(len2 > 0.0f)) return make_float3(0.0f, 0.0f, 0.0f);
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(len2));
+    return make_float3(__fmul_rn(c.x, inv), __fmul_rn(c.y, inv), __fmul_rn(c.z, inv));
+}
+
+__device__ __forceinline__ float3 sub_rn(float4 a, float4 b)
+{
+    return make_float3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+
+// Object-frame unit normal of triangle t, vertex order as stored.
+__device__ __forceinline__ float3 triangle_normal(const DevMesh& m, int t)
+{
+    const int4 tv = __ldg(&m.tris[t]);
+    const float4 a = __ldg(&m.verts[tv.x]), b = __ldg(&m.verts[tv.y]), c = __ldg(&m.verts[tv.z]);
+    return unit_or_zero(cross_rn(sub_rn(b, a), sub_rn(c, a)));
+}
+
+// R v for the 3x3 rotation stored row-major with row pitch `pitch`.
+__device__ __forceinline__ float3 rotate_rn(const float* R, int pitch, float x, float y, float z)
+{
+    return make_float3(
+        __fadd_rn(__fadd_rn(__fmul_rn(R[0], x), __fmul_rn(R[1], y)), __fmul_rn(R[2], z)),
+        __fadd_rn(__fadd_rn(__fmul_rn(R[pitch], x), __fmul_rn(R[pitch + 1], y)), __fmul_rn(R[pitch + 2], z)),
+        __fadd_rn(__fadd_rn(__fmul_rn(R[2 * pitch], x), __fmul_rn(R[2 * pitch + 1], y)),
+                  __fmul_rn(R[2 * pitch + 2], z)));
+}
+
+__global__ void k_obs_normals(DevScene sc, int jump, float4* nrm)
+{
+    const int n = sc.W * sc.H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int u = i % sc.W, v = i / sc.W;
+        float3 nv = make_float3(0.0f, 0.0f, 0.0f);
+        const int dc = sc.depth[i];
+        if (dc != 0 && u >= 1 && v >= 1 && u + 1 < sc.W && v + 1 < sc.H) {
+            const int nu[4] = {u - 1, u + 1, u, u}, nvv[4] = {v, v, v - 1, v + 1};
+            float3 P[4];
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int d = sc.depth[nvv[k] * sc.W + nu[k]];
+                if (d == 0 || abs(d - dc) > jump) ok = false;
+                else P[k] = back_project(sc, nu[k], nvv[k], (unsigned)d);
+            }
+            if (ok) {
+                const float3 a = make_float3(__fsub_rn(P[1].x, P[0].x), __fsub_rn(P[1].y, P[0].y),
+                                             __fsub_rn(P[1].z, P[0].z));
+                const float3 b = make_float3(__fsub_rn(P[3].x, P[2].x), __fsub_rn(P[3].y, P[2].y),
+                                             __fsub_rn(P[3].z, P[2].z));
+                nv = unit_or_zero(cross_rn(a, b));
+            }
+        }
+        nrm[i] = make_float4(nv.x, nv.y, nv.z, 0.0f);
+    }
+}
+
+cudaError_t launch_obs_normals(const DevScene& sc, int normal_jump, float4* nrm, cudaStream_t s)
+{
+    const int n = sc.W * sc.H;
+    if (n <= 0) return cudaSuccess;
+    k_obs_normals<<<(n + 255) / 256, 256, 0, s>>>(sc, normal_jump, nrm);
+    return cudaGetLastError();
+}
+
+// The 28 terms of one correspondence: p = Rf a + tf (already moved), m = Rf na,
+// observed b with normal nb.  False (no terms) when the combined covariance is
+// not positive or a term is out of bounds.
+__device__ __forceinline__ bool gicp_terms(const float* Rf, float3 p, float4 na, float3 b, float4 nb,
+                                           float eps, float* out)
+{
+    const float3 m = rotate_rn(Rf, 3, na.x, na.y, na.z);
+    const float e = __fsub_rn(1.0f, eps);
+    // C = 2 I - e (nb nb^T + m m^T)
+    const float c00 = __fsub_rn(2.0f, __fmul_rn(e, __fadd_rn(__fmul_rn(nb.x, nb.x), __fmul_rn(m.x, m.x))));
+    const float c11 = __fsub_rn(2.0f, __fmul_rn(e, __fadd_rn(__fmul_rn(nb.y, nb.y), __fmul_rn(m.y, m.y))));
+    const float c22 = __fsub_rn(2.0f, __fmul_rn(e, __fadd_rn(__fmul_rn(nb.z, nb.z), __fmul_rn(m.z, m.z))));
+    const float c01 = -__fmul_rn(e, __fadd_rn(__fmul_rn(nb.x, nb.y), __fmul_rn(m.x, m.y)));
+    const float c02 = -__fmul_rn(e, __fadd_rn(__fmul_rn(nb.x, nb.z), __fmul_rn(m.x, m.z)));
+    const float c12 = -__fmul_rn(e, __fadd_rn(__fmul_rn(nb.y, nb.z), __fmul_rn(m.y, m.z)));
+    // M = C^-1 (adjugate over determinant)
+    const float a00 = __fsub_rn(__fmul_rn(c11, c22), __fmul_rn(c12, c12));
+    const float a01 = __fsub_rn(__fmul_rn(c02, c12), __fmul_rn(c01, c22));
+    const float a02 = __fsub_rn(__fmul_rn(c01, c12), __fmul_rn(c02, c11));
+    const float a11 = __fsub_rn(__fmul_rn(c00, c22), __fmul_rn(c02, c02));
+    const float a12 = __fsub_rn(__fmul_rn(c01, c02), __fmul_rn(c00, c12));
+    const float a22 = __fsub_rn(__fmul_rn(c00, c11), __fmul_rn(c01, c01));
+    const float det = __fadd_rn(__fadd_rn(__fmul_rn(c00, a00), __fmul_rn(c01, a01)), __fmul_rn(c02, a02));
+    if (!(det > 0.0f)) return false;
+    const float id = __fdiv_rn(1.0f, det);
+    float M[3][3];
+    M[0][0] = __fmul_rn(a00, id); M[0][1] = __fmul_rn(a01, id); M[0][2] = __fmul_rn(a02, id);
+    M[1][1] = __fmul_rn(a11, id); M[1][2] = __fmul_rn(a12, id); M[2][2] = __fmul_rn(a22, id);
+    M[1][0] = M[0][1]; M[2][0] = M[0][2]; M[2][1] = M[1][2];
+    const float r[3] = {__fsub_rn(b.x, p.x), __fsub_rn(b.y, p.y), __fsub_rn(b.z, p.z)};
+    // Jacobian of r with respect to (w, v) is [ [p]x , -I ]; MA = M [p]x
+    float MA[3][3], AMA[3][3], Mr[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        MA[i][0] = __fsub_rn(__fmul_rn(M[i][1], p.z), __fmul_rn(M[i][2], p.y));
+        MA[i][1] = __fsub_rn(__fmul_rn(M[i][2], p.x), __fmul_rn(M[i][0], p.z));
+        MA[i][2] = __fsub_rn(__fmul_rn(M[i][0], p.y), __fmul_rn(M[i][1], p.x));
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        AMA[0][j] = __fsub_rn(__fmul_rn(p.z, MA[1][j]), __fmul_rn(p.y, MA[2][j]));
+        AMA[1][j] = __fsub_rn(__fmul_rn(p.x, MA[2][j]), __fmul_rn(p.z, MA[0][j]));
+        AMA[2][j] = __fsub_rn(__fmul_rn(p.y, MA[0][j]), __fmul_rn(p.x, MA[1][j]));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        Mr[i] = __fadd_rn(__fadd_rn(__fmul_rn(M[i][0], r[0]), __fmul_rn(M[i][1], r[1])), __fmul_rn(M[i][2], r[2]));
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int j = i; j < 6; ++j) {
+            float h;
+            if (i < 3 && j < 3) h = AMA[i][j];
+            else if (i < 3) h = -MA[j - 3][i];
+            else h = M[i - 3][j - 3];
+            out[k++] = h;
+        }
+    }
+    out[k++] = __fsub_rn(__fmul_rn(p.z, Mr[1]), __fmul_rn(p.y, Mr[2]));
+    out[k++] = __fsub_rn(__fmul_rn(p.x, Mr[2]), __fmul_rn(p.z, Mr[0]));
+    out[k++] = __fsub_rn(__fmul_rn(p.y, Mr[0]), __fmul_rn(p.x, Mr[1]));
+    out[k++] = -Mr[0];
+    out[k++] = -Mr[1];
+    out[k++] = -Mr[2];
+    out[k++] = __fadd_rn(__fadd_rn(__fmul_rn(r[0], Mr[0]), __fmul_rn(r[1], Mr[1])), __fmul_rn(r[2], Mr[2]));
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < kGicpTerms; ++i) ok = ok && fabsf(out[i]) < kGicpLimit;
+    return ok;
+}
+
+// H xi = -g from the fixed-point sums, by Cholesky in binary64 (one thread).
+__device__ bool gicp_solve(const unsigned long long* S, double* xi)
+{
+    double H[6][6], g[6], L[6][6], y[6];
+    int k = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) {
+            H[i][j] = __ddiv_rn(__ll2double_rn((long long)S[k++]), 16777216.0);
+            H[j][i] = H[i][j];
+        }
+    for (int i = 0; i < 6; ++i) g[i] = __ddiv_rn(__ll2double_rn((long long)S[k++]), 16777216.0);
+    for (int j = 0; j < 6; ++j) {
+        double s = H[j][j];
+        for (int q = 0; q < j; ++q) s = __dsub_rn(s, __dmul_rn(L[j][q], L[j][q]));
+        if (!(s > 0.0)) return false;
+        L[j][j] = __dsqrt_rn(s);
+        for (int i = j + 1; i < 6; ++i) {
+            double t = H[i][j];
+            for (int q = 0; q < j; ++q) t = __dsub_rn(t, __dmul_rn(L[i][q], L[j][q]));
+            L[i][j] = __ddiv_rn(t, L[j][j]);
+        }
+    }
+    for (int i = 0; i < 6; ++i) {
+        double t = -g[i];
+        for (int q = 0; q < i; ++q) t = __dsub_rn(t, __dmul_rn(L[i][q], y[q]));
+        y[i] = __ddiv_rn(t, L[i][i]);
+    }
+    for (int i = 5; i >= 0; --i) {
+        double t = y[i];
+        for (int q = i + 1; q < 6; ++q) t = __dsub_rn(t, __dmul_rn(L[q][i], xi[q]));
+        xi[i] = __ddiv_rn(t, L[i][i]);
+    }
+    return true;
+}
+
+// Apply the step xi to the increment (R, t): R <- dR R, t <- dR t + v, with
+// dR the rotation of the quaternion (1, w/2) normalised.  True when the step
+// is below the stopping thresholds.
+__device__ bool gicp_update(double* R, double* t, const double* xi, float stop_rot, float stop_trans)
+{
+    const double hx = __dmul_rn(xi[0], 0.5), hy = __dmul_rn(xi[1], 0.5), hz = __dmul_rn(xi[2], 0.5);
+    const double nrm = __dsqrt_rn(__dadd_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(hx, hx)), __dmul_rn(hy, hy)),
+                                            __dmul_rn(hz, hz)));
+    const double qw = __ddiv_rn(1.0, nrm), qx = __ddiv_rn(hx, nrm), qy = __ddiv_rn(hy, nrm), qz = __ddiv_rn(hz, nrm);
+    double d[9];
+    d[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(qy, qy), __dmul_rn(qz, qz))));
+    d[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(qx, qy), __dmul_rn(qw, qz)));
+    d[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(qx, qz), __dmul_rn(qw, qy)));
+    d[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(qx, qy), __dmul_rn(qw, qz)));
+    d[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qz, qz))));
+    d[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(qy, qz), __dmul_rn(qw, qx)));
+    d[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(qx, qz), __dmul_rn(qw, qy)));
+    d[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(qy, qz), __dmul_rn(qw, qx)));
+    d[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy))));
+    double R2[9], t2[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j)
+            R2[3 * i + j] = __dadd_rn(__dadd_rn(__dmul_rn(d[3 * i], R[j]), __dmul_rn(d[3 * i + 1], R[3 + j])),
+                                      __dmul_rn(d[3 * i + 2], R[6 + j]));
+        t2[i] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(d[3 * i], t[0]), __dmul_rn(d[3 * i + 1], t[1])),
+                                    __dmul_rn(d[3 * i + 2], t[2])), xi[3 + i]);
+    }
+    for (int i = 0; i < 9; ++i) R[i] = R2[i];
+    for (int i = 0; i < 3; ++i) t[i] = t2[i];
+    const double sr = (double)stop_rot, st = (double)stop_trans;
+    const double w2 = __dadd_rn(__dadd_rn(__dmul_rn(xi[0], xi[0]), __dmul_rn(xi[1], xi[1])), __dmul_rn(xi[2], xi[2]));
+    const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(xi[3], xi[3]), __dmul_rn(xi[4], xi[4])), __dmul_rn(xi[5], xi[5]));
+    return w2 < __dmul_rn(sr, sr) && v2 < __dmul_rn(st, st);
+}
+
+// Render the hypothesis in z-buffer tiles and append its source cloud
+// (visible, unoccluded pixels on the stride lattice) to src; *count ends as
+// the number of source points (entries past cap are not written).
+template <int NT, bool K32, bool VC>
+__device__ void gicp_source(const GicpArgs& a, const Job& J, const float* P, const unsigned long long* vc,
+                            const int* rbox, uint32_t* zbuf, char* probe, float4* src, int* count)
+{
+    const DevScene& sc = J.sc;
+    const int warp = threadIdx.x >> 5;
+    TriStage* TS = reinterpret_cast<TriStage*>(probe + warp * kWarpScratch);
+    const int s = sc.stride;
+    const int rw = rbox[2] - rbox[0], rh = rbox[3] - rbox[1];
+    if (rw <= 0 || rh <= 0) return;
+    const int cap_px = K32 ? a.zcap_words : a.zcap_words / 2;
+    const int tw = min(rw, cap_px);
+    const int th = max(1, cap_px / tw);
+    for (int tv0 = rbox[1]; tv0 < rbox[3]; tv0 += th) {
+        for (int tu0 = rbox[0]; tu0 < rbox[2]; tu0 += tw) {
+            const int tu1 = min(tu0 + tw, rbox[2]), tv1 = min(tv0 + th, rbox[3]);
+            const int words = K32 ? tw * (tv1 - tv0) : 2 * tw * (tv1 - tv0);
+            for (int i = threadIdx.x; i < words; i += NT) zbuf[i] = 0xFFFFFFFFu;
+            __syncthreads();
+            raster_tile<NT, K32, VC>(sc, J.m, P, vc, TS, zbuf, tu0, tv0, tu1, tv1, tw, a.err);
+            __syncthreads();
+            const int us0 = ((tu0 + s - 1) / s) * s, vs0 = ((tv0 + s - 1) / s) * s;
+            const int nu = us0 < tu1 ? (tu1 - 1 - us0) / s + 1 : 0;
+            const int nv = vs0 < tv1 ? (tv1 - 1 - vs0) / s + 1 : 0;
+            for (int k = threadIdx.x; k < nu * nv; k += NT) {
+                const int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
+                const int zi = (v - tv0) * tw + (u - tu0);
+                unsigned d = 0;
+                int tri = -1;
+                if (K32) {
+                    const uint32_t w = zbuf[zi];
+                    if (w != 0xFFFFFFFFu) { d = w >> 16; tri = (int)(w & 0xFFFFu); }
+                } else {
+                    const unsigned long long w = reinterpret_cast<unsigned long long*>(zbuf)[zi];
+                    if (w != kEmptyKey) { d = (unsigned)(w >> 32); tri = (int)(uint32_t)w; }
+                }
+                if (tri < 0) continue;
+                const int pix = v * sc.W + u;
+                const unsigned dobs = __ldg(&sc.depth[pix]);
+                const bool occluded = sc.occ_margin >= 0 && dobs > 0 &&
+                                      (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
+                                      (J.label < 0 || __ldg(&sc.labels[pix]) != J.label);
+                if (occluded) continue;
+                const float3 q = back_project(sc, u, v, d);
+                const float3 no = triangle_normal(J.m, tri);
+                const float3 nc = rotate_rn(P, 4, no.x, no.y, no.z);
+                const int idx = atomicAdd(count, 1);
+                if (idx < a.src_cap) {
+                    src[2 * (size_t)idx] = make_float4(q.x, q.y, q.z, 0.0f);
+                    src[2 * (size_t)idx + 1] = make_float4(nc.x, nc.y, nc.z, 0.0f);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__host__ __device__ inline size_t gicp_probe_offset(int zcap_words)
+{
+    return align16(sizeof(uint32_t) * (size_t)zcap_words);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 2) k_gicp(GicpArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float s_pose[12], s_Rf[9], s_tf[3];
+    __shared__ double s_R[9], s_t[3];
+    __shared__ unsigned long long s_sum[kGicpTerms];
+    __shared__ int s_rbox[4], s_k32, s_slot, s_nsrc, s_corr, s_done, s_updates, s_last;
+    __shared__ long long s_h;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Job& J = a.job;
+    const DevScene& sc = J.sc;
+    uint32_t* zbuf = reinterpret_cast<uint32_t*>(smem);
+    char* probe = reinterpret_cast<char*>(smem) + gicp_probe_offset(a.zcap_words);
+    WarpProbe& WP = *reinterpret_cast<WarpProbe*>(probe + warp * kWarpScratch);
+    if (threadIdx.x == 0) {
+        s_slot = claim_vslot(a.smask, a.slots);
+        if (s_slot < 0) atomicOr(a.err, kErrNoSlot);
+    }
+    __syncthreads();
+    if (s_slot < 0) return;
+    const unsigned long long* vc = a.vcache ? a.vcache + (size_t)s_slot * a.vstride : nullptr;
+    float4* src = a.src + (size_t)s_slot * 2 * (size_t)a.src_cap;
+    const MarkBand nomark = {nullptr, 0, 0, 0, 0, 0};
+    for (;;) {
+        if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.next, 1u);
+        __syncthreads();
+        const long long h = s_h;
+        if (h >= a.n) break;
+        if (threadIdx.x < 12) s_pose[threadIdx.x] = J.poses[h * 12 + threadIdx.x];
+        if (threadIdx.x == 0) s_nsrc = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float zmax;
+            project_box(sc, s_pose, J.m.lo, J.m.hi, J.roi[0], J.roi[1], J.roi[2], J.roi[3], s_rbox, &zmax);
+            s_k32 = (J.m.n_tris <= 65535 && zmax < 6.5f) ? 1 : 0;
+        }
+        if (vc) vertex_pass(sc, J.m, s_pose, const_cast<unsigned long long*>(vc), NT);
+        __syncthreads();
+        if (s_k32) {
+            if (vc) gicp_source<NT, true, true>(a, J, s_pose, vc, s_rbox, zbuf, probe, src, &s_nsrc);
+            else gicp_source<NT, true, false>(a, J, s_pose, vc, s_rbox, zbuf, probe, src, &s_nsrc);
+        } else {
+            if (vc) gicp_source<NT, false, true>(a, J, s_pose, vc, s_rbox, zbuf, probe, src, &s_nsrc);
+            else gicp_source<NT, false, false>(a, J, s_pose, vc, s_rbox, zbuf, probe, src, &s_nsrc);
+        }
+        const int nsrc = s_nsrc;
+        if (nsrc > a.src_cap) {
+            // the source cloud does not fit its slot: the pose is returned unchanged
+            if (threadIdx.x < 12) a.poses_out[h * 12 + threadIdx.x] = s_pose[threadIdx.x];
+            if (threadIdx.x == 0) {
+                atomicOr(a.err, kErrSourceCap);
+                if (a.info) { a.info[2 * h] = -1; a.info[2 * h + 1] = nsrc; }
+            }
+            __syncthreads();
+            continue;
+        }
+        // the raster stage used these bytes: start with an empty lookup cache
+        for (int i = lane; i < kCellCache; i += 32) WP.cache[i] = make_uint4(~0u, ~0u, 0u, 0u);
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < 9; ++i) { s_R[i] = (i % 4 == 0) ? 1.0 : 0.0; s_Rf[i] = (float)s_R[i]; }
+            for (int i = 0; i < 3; ++i) { s_t[i] = 0.0; s_tf[i] = 0.0f; }
+            s_done = 0;
+            s_updates = 0;
+            s_last = 0;
+        }
+        __syncthreads();
+        for (int it = 0; it < a.max_iters; ++it) {
+            if (threadIdx.x < kGicpTerms) s_sum[threadIdx.x] = 0ull;
+            if (threadIdx.x == 0) s_corr = 0;
+            __syncthreads();
+            long long acc = 0;
+            int corr = 0;
+            for (int base = warp * 32; base < nsrc; base += NT) {
+                const int i = base + lane;
+                const bool valid = i < nsrc;
+                float4 A = make_float4(0.f, 0.f, 0.f, 0.f), NA = A;
+                if (valid) { A = src[2 * (size_t)i]; NA = src[2 * (size_t)i + 1]; }
+                const float3 r0 = rotate_rn(s_Rf, 3, A.x, A.y, A.z);
+                const float3 p = make_float3(__fadd_rn(r0.x, s_tf[0]), __fadd_rn(r0.y, s_tf[1]),
+                                             __fadd_rn(r0.z, s_tf[2]));
+                const unsigned long long nn = probe_batch(sc, valid, p.x, p.y, p.z, WP, lane, nomark);
+                bool ok = valid && nn != kEmptyKey;
+                float terms[kGicpTerms];
+                if (ok) {
+                    const uint32_t pw = (uint32_t)nn;
+                    const int pu = (int)(pw & 0xFFFFu), pv = (int)(pw >> 16);
+                    const int pix = pv * sc.W + pu;
+                    const float3 b = back_project(sc, pu, pv, __ldg(&sc.depth[pix]));
+                    ok = gicp_terms(s_Rf, p, NA, b, __ldg(&a.nrm[pix]), a.epsilon, terms);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                corr += __popc(bal);
+                if (bal) {
+#pragma unroll
+                    for (int j = 0; j < kGicpTerms; ++j) {
+                        long long q = ok ? __float2ll_rn(__fmul_rn(terms[j], kGicpScale)) : 0ll;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+                        if (lane == j) acc += q;
+                    }
+                }
+            }
+            if (lane < kGicpTerms) atomicAdd(&s_sum[lane], (unsigned long long)acc);
+            if (lane == 0) atomicAdd(&s_corr, corr);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_last = s_corr;
+                double xi[6];
+                if (s_corr < a.min_corr || !gicp_solve(s_sum, xi)) {
+                    s_done = 1;
+                } else {
+                    if (gicp_update(s_R, s_t, xi, a.stop_rot, a.stop_trans)) s_done = 1;
+                    ++s_updates;
+                    for (int i = 0; i < 9; ++i) s_Rf[i] = __double2float_rn(s_R[i]);
+                    for (int i = 0; i < 3; ++i) s_tf[i] = __double2float_rn(s_t[i]);
+                }
+            }
+            __syncthreads();
+            if (s_done) break;
+        }
+        // refined pose = increment o input pose
+        if (threadIdx.x < 12) {
+            const int i = threadIdx.x / 4, j = threadIdx.x % 4;
+            const float* P = s_pose;
+            double x;
+            if (j < 3) {
+                x = __dadd_rn(__dadd_rn(__dmul_rn(s_R[3 * i], (double)P[j]), __dmul_rn(s_R[3 * i + 1], (double)P[4 + j])),
+                              __dmul_rn(s_R[3 * i + 2], (double)P[8 + j]));
+            } else {
+                x = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(s_R[3 * i], (double)P[3]),
+                                                  __dmul_rn(s_R[3 * i + 1], (double)P[7])),
+                                        __dmul_rn(s_R[3 * i + 2], (double)P[11])), s_t[i]);
+            }
+            a.poses_out[h * 12 + threadIdx.x] = __double2float_rn(x);
+        }
+        if (threadIdx.x == 0 && a.info) {
+            a.info[2 * h] = s_updates;
+            a.info[2 * h + 1] = s_last;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAnd(&a.smask[s_slot >> 5], ~(1u << (s_slot & 31)));
+    }
+}
+
+size_t gicp_smem_bytes(int zcap_words)
+{
+    return gicp_probe_offset(zcap_words) + kWarpScratch * (kGicpThreads / 32);
+}
+
+int gicp_grid(int zcap_words)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = gicp_smem_bytes(zcap_words);
+    if (cudaFuncSetAttribute(k_gicp<kGicpThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gicp<kGicpThreads>, kGicpThreads, smem) != cudaSuccess)
+        return -1;
+    return max(1, per) * max(1, sms);
+}
+
+cudaError_t launch_gicp(const GicpArgs& a, int grid, cudaStream_t s)
+{
+    if (a.n <= 0) return cudaSuccess;
+    if (a.n > 0xFFFFFFF0ll || grid <= 0 || grid > a.slots) return cudaErrorInvalidValue;
+    const size_t smem = gicp_smem_bytes(a.zcap_words);
+    cudaError_t e = cudaFuncSetAttribute(k_gicp<kGicpThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gicp<kGicpThreads><<<(unsigned)(a.n < grid ? a.n : grid), kGicpThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

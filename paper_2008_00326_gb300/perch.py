@@ -28,7 +28,8 @@ EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_
            "perch_debug_render_keys", "perch_best_noalloc", "perch_score_batch",
            "perch_batch_graph_create", "perch_batch_graph_launch", "perch_batch_graph_destroy",
            "perch_autotune", "perch_server_start", "perch_submit", "perch_poll", "perch_wait",
-           "perch_ticket_times", "perch_server_stop", "perch_pose_proposals")
+           "perch_ticket_times", "perch_server_stop", "perch_pose_proposals",
+           "perch_default_gicp_params", "perch_refine_hypotheses")
 
 
 class PerchError(RuntimeError):
@@ -130,6 +131,13 @@ class perch_params(C.Structure):
                 ("jo_mode", C.c_int32)]
 
 
+class perch_gicp_params(C.Structure):
+    _fields_ = [("max_iterations", C.c_int32), ("epsilon", C.c_float),
+                ("normal_max_jump_units", C.c_int32), ("min_correspondences", C.c_int32),
+                ("stop_rotation_rad", C.c_float), ("stop_translation_m", C.c_float),
+                ("max_source_points", C.c_int32)]
+
+
 _lib = None
 
 
@@ -172,6 +180,8 @@ def load(path: str | None = None):
         "perch_ticket_times": ([P, U64, P, P], I32),
         "perch_server_stop": ([P], I32),
         "perch_pose_proposals": ([P, I32, I32, I32, P, I32, I32, I32, P, P, P], I32),
+        "perch_default_gicp_params": ([P], I32),
+        "perch_refine_hypotheses": ([P, I32, I32, I32, P, P, I64, P, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -366,6 +376,39 @@ def perch_pose_proposals(ctx, scene_id, mesh_id, label, bbox, M, N, K, poses=Non
     return poses
 
 
+def perch_default_gicp_params(**over) -> perch_gicp_params:
+    p = perch_gicp_params()
+    st = load().perch_default_gicp_params(C.byref(p))
+    if st != PERCH_OK:
+        raise PerchError(st, "perch_default_gicp_params")
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def perch_refine_hypotheses(ctx, scene_id, mesh_id, label, roi, poses, params=None, poses_out=None,
+                            info=None, stream=None):
+    """M2M GICP refinement.  Host mode (stream None): poses numpy (n,12) ->
+    (refined poses (n,12) float32, info (n,2) int32).  Device mode: poses,
+    poses_out (and info, or None) torch CUDA tensors; enqueued on `stream`."""
+    keep, proi = _roi(roi)
+    gp = params if params is not None else perch_default_gicp_params()
+    if stream is None:
+        p, pp = _host(poses, np.float32)
+        n = p.size // 12
+        out = np.empty((n, 12), np.float32) if poses_out is None else poses_out
+        inf = np.empty((n, 2), np.int32) if info is None else info
+        _check(ctx, load().perch_refine_hypotheses(ctx, scene_id, mesh_id, label, proi, pp, n, C.byref(gp),
+                                                    out.ctypes.data, inf.ctypes.data, None))
+        return out, inf
+    n = poses.numel() // 12
+    _check(ctx, load().perch_refine_hypotheses(ctx, scene_id, mesh_id, label, proi, _ptr_of(poses), n,
+                                                C.byref(gp), _ptr_of(poses_out),
+                                                None if info is None else _ptr_of(info),
+                                                getattr(stream, "cuda_stream", stream)))
+    return poses_out
+
+
 def perch_set_launch_config(ctx, threads, zbuf_words, mark_bits=0):
     _check(ctx, load().perch_set_launch_config(ctx, threads, zbuf_words, mark_bits))
 
@@ -420,6 +463,9 @@ class Context:
 
     def best(self, costs, ids=None, **kw):
         return perch_best(self.ctx, costs, ids, **kw)
+
+    def refine(self, scene_id, mesh_id, label, roi, poses, params=None, **kw):
+        return perch_refine_hypotheses(self.ctx, scene_id, mesh_id, label, roi, poses, params, **kw)
 
     def set_launch_config(self, threads, zbuf_words, mark_bits=0):
         perch_set_launch_config(self.ctx, threads, zbuf_words, mark_bits)

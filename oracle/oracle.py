@@ -76,6 +76,7 @@ def lib():
         L.or_gicp_quantise.restype = C.c_int64
         L.or_gicp_solve.argtypes = [P, P]
         L.or_gicp_rotation.argtypes = [P, P]
+        L.or_score_tree.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, P, P, P, P, P, C.c_int32]
         _lib = L
     return _lib
 
@@ -257,6 +258,34 @@ def gicp_rotation(w):
     R = np.zeros(9, np.float64)
     lib().or_gicp_rotation(_ptr(w), _ptr(R))
     return R.reshape(3, 3)
+
+
+def empty_state(scene: OracleScene):
+    """Root of the Monotone Scene Generation tree: (depth u32, mark u8, vol u8) images."""
+    return (np.zeros((scene.H, scene.W), np.uint32), np.zeros((scene.H, scene.W), np.uint8),
+            np.zeros((scene.H, scene.W), np.uint8))
+
+
+def score_tree(scene: OracleScene, mesh: OracleMesh, poses, state, label=-1, roi=None, child=False,
+               threads=0):
+    """Edge costs of adding the object at each pose to `state`: (costs (n,2)
+    int32, (-1,-1) = refused, band (n,)[, child state]) -- child only for n == 1."""
+    poses = np.ascontiguousarray(poses, np.float32).reshape(-1, 12)
+    n = poses.shape[0]
+    roi = np.asarray(roi if roi is not None else (0, 0, scene.W, scene.H), np.int32)
+    pd, pm, pv = (np.ascontiguousarray(x) for x in state)
+    costs = np.zeros((n, 2), np.int32)
+    band = np.zeros(n, np.int32)
+    cd = cm = cv = None
+    if child:
+        assert n == 1
+        cd, cm, cv = np.zeros_like(pd), np.zeros_like(pm), np.zeros_like(pv)
+    rc = lib().or_score_tree(C.byref(scene.s), C.byref(mesh.m), label, _ptr(roi), _ptr(poses), n,
+                             _ptr(pd), _ptr(pm), _ptr(pv), _ptr(costs), _ptr(band), _ptr(cd), _ptr(cm),
+                             _ptr(cv), threads)
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return (costs, band, (cd, cm, cv)) if child else (costs, band)
 
 
 def num_threads():

@@ -963,3 +963,158 @@ int or_gicp(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t r
     free(Ixyz); free(Ipix); free(Inrm);
     return rc;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Monotone Scene Generation tree (Sec. III, Fig. 2; variant 2.0-B)        */
+/* ---------------------------------------------------------------------- */
+/*
+ * A state holds the objects placed so far as three per-pixel images:
+ *   depth  nearest rendered depth of the placed objects on the stride
+ *          lattice (0.1 mm, 0 = none): the composed rendered scene;
+ *   mark   observed pixels found as the nearest neighbour of an explained
+ *          rendered point of a placed object;
+ *   vol    observed pixels inside a placed object's admissible volume V
+ *          (already counted in J_o).
+ * Adding object O at pose h is an edge of the tree.  The edge is refused
+ * (costs -1, -1) when O occludes a placed object: some lattice pixel where O
+ * renders at depth d with state depth s > 0 and d + m < s (m = the occluder
+ * margin, or 0 when occluder marking is off).  Otherwise O's point cloud
+ * Delta R is its rendered lattice pixels not behind the state (s == 0 or
+ * d < s) and not behind the observed depth (the usual occluder rule), and
+ *   dJ_r = points of Delta R that are not explained (Eq. 2, Eq. 4),
+ *   dJ_o = observed points in V(O) \ vol that are marked neither in the
+ *          state nor by Delta R (Eq. 1 over the newly covered volume).
+ * The child state is the parent with O's visible lattice pixels composed
+ * into depth, Delta R's marks added to mark and V(O) added to vol.
+ * Readings: the occlusion test and the composition use the stride lattice;
+ * J_o uses the nearest-neighbour marks (jo_mode 0).
+ */
+int or_score_tree(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t roi[4],
+                  const float *poses, int64_t n, const uint32_t *p_depth, const uint8_t *p_mark,
+                  const uint8_t *p_vol, int32_t *costs, int32_t *band, uint32_t *c_depth,
+                  uint8_t *c_mark, uint8_t *c_vol, int32_t n_threads)
+{
+    int64_t WH = (int64_t)sc->W * sc->H;
+    int64_t s = sc->stride;
+    int32_t margin = sc->occ_margin > 0 ? sc->occ_margin : 0;
+    float *Ixyz = malloc(sizeof(float) * 3 * (WH + 1));
+    float *Ilab = malloc(sizeof(float) * 3 * (WH + 1));
+    int32_t *Ipix = malloc(sizeof(int32_t) * (WH + 1));
+    if (!Ixyz || !Ilab || !Ipix) {
+        free(Ixyz); free(Ilab); free(Ipix);
+        return -2;
+    }
+    int64_t nI = or_observed_points(sc, Ixyz, Ilab, Ipix);
+    float delta2 = sc->delta * sc->delta;
+    int write_child = c_depth && c_mark && c_vol && n == 1;
+    if (write_child) {
+        memcpy(c_depth, p_depth, sizeof(uint32_t) * WH);
+        memcpy(c_mark, p_mark, WH);
+        memcpy(c_vol, p_vol, WH);
+    }
+    int rc = 0;
+#ifdef _OPENMP
+    if (n_threads > 0)
+        omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+#pragma omp parallel
+    {
+        uint64_t *keys = malloc(sizeof(uint64_t) * WH);
+        float *Rxyz = malloc(sizeof(float) * 3 * WH);
+        uint8_t *Rrgb = malloc(3 * WH);
+        int32_t *Rpix = malloc(sizeof(int32_t) * WH);
+        uint8_t *mark = malloc(nI + 1);
+        int ok = keys && Rxyz && Rrgb && Rpix && mark;
+        if (!ok) {
+#pragma omp atomic write
+            rc = -2;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t h = 0; h < n; h++) {
+            if (!ok)
+                continue;
+            const float *P = poses + 12 * h;
+            or_render_keys(sc, m, P, roi, keys, NULL);
+            /* monotone test and composition over the rendered lattice pixels */
+            int occludes = 0;
+            for (int64_t i = 0; i < WH && !occludes; i++) {
+                int64_t u = i % sc->W, v = i / sc->W;
+                if (keys[i] == OR_EMPTY || u % s != 0 || v % s != 0)
+                    continue;
+                int64_t d = (int64_t)(keys[i] >> 32), sd = p_depth[i];
+                if (sd > 0 && d + margin < sd)
+                    occludes = 1;
+            }
+            if (occludes) {
+                costs[2 * h] = -1;
+                costs[2 * h + 1] = -1;
+                if (band) band[h] = 0;
+                continue;
+            }
+            int64_t L = or_rendered_points(sc, m, P, label, keys, Rxyz, Rrgb, Rpix);
+            memset(mark, 0, nI + 1);
+            int32_t Jr = 0, nband = 0;
+            for (int64_t k = 0; k < L; k++) {
+                int64_t i = Rpix[k];
+                int64_t d = (int64_t)(keys[i] >> 32), sd = p_depth[i];
+                if (sd > 0 && !(d < sd))
+                    continue;                       /* behind a placed object */
+                const float *q = Rxyz + 3 * k;
+                float best = INFINITY;
+                int64_t bj = -1;
+                for (int64_t j = 0; j < nI; j++) {
+                    const float *p = Ixyz + 3 * j;
+                    float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
+                    float d2 = (dx * dx + dy * dy) + dz * dz;
+                    if (d2 < best) { best = d2; bj = j; }
+                }
+                int explained = bj >= 0 && best <= delta2;
+                if (explained && sc->color_check) {
+                    float lq[3], gap;
+                    or_srgb_to_lab(Rrgb + 3 * k, lq);
+                    float dE = or_ciede2000(lq, Ilab + 3 * bj, &gap);
+                    if (fabsf(dE - sc->tau_c) <= 1e-3f || gap <= 1e-3f)
+                        nband++;
+                    if (dE > sc->tau_c)
+                        explained = 0;
+                }
+                if (explained)
+                    mark[bj] = 1;
+                else
+                    Jr++;
+            }
+            int32_t Jo = 0;
+            for (int64_t j = 0; j < nI; j++) {
+                int64_t i = Ipix[j];
+                if (p_vol[i] || !in_volume(sc, m, P, label, roi, i, Ixyz + 3 * j))
+                    continue;
+                if (!mark[j] && !p_mark[i])
+                    Jo++;
+            }
+            costs[2 * h] = Jo;
+            costs[2 * h + 1] = Jr;
+            if (band) band[h] = nband;
+            if (write_child) {
+                for (int64_t i = 0; i < WH; i++) {
+                    int64_t u = i % sc->W, v = i / sc->W;
+                    if (keys[i] == OR_EMPTY || u % s != 0 || v % s != 0)
+                        continue;
+                    uint32_t d = (uint32_t)(keys[i] >> 32);
+                    if (p_depth[i] == 0 || d < p_depth[i])
+                        c_depth[i] = d;
+                }
+                for (int64_t j = 0; j < nI; j++) {
+                    if (mark[j])
+                        c_mark[Ipix[j]] = 1;
+                    if (in_volume(sc, m, P, label, roi, Ipix[j], Ixyz + 3 * j))
+                        c_vol[Ipix[j]] = 1;
+                }
+            }
+        }
+        free(keys); free(Rxyz); free(Rrgb); free(Rpix); free(mark);
+    }
+    free(Ixyz); free(Ilab); free(Ipix);
+    return rc;
+}

@@ -386,6 +386,41 @@ PERCH_API perch_status perch_refine_hypotheses(perch_ctx *ctx, int32_t scene_id,
                                                int64_t n, const perch_gicp_params *params,
                                                float *poses_out, int32_t *info, void *cuda_stream);
 
+/* ---- Monotone Scene Generation tree search (Sec. III, Fig. 2; variant 2.0-B) -----
+ * The K object instances are placed one per tree level; a state is the set
+ * placed so far, kept on the device as its composed depth image (stride
+ * lattice), the observed pixels its rendered points explain, and the observed
+ * pixels inside its admissible volumes.  Adding object j at candidate pose h
+ * to a state is an edge, scored on the GPU for every remaining object and
+ * pose of every state of the level at once:
+ *   refused  if j would cover a placed object: a lattice pixel where j
+ *            renders at depth d, the state at s > 0 and d + m < s
+ *            (m = occ_margin_units, or 0 when occluder marking is off);
+ *   dJ_r     = j's visible rendered points (not behind the state, not behind
+ *              the observed depth) that are unexplained (Eq. 2, Eq. 4);
+ *   dJ_o     = observed points in V(j) not counted by an earlier object and
+ *              explained neither by the state nor by j (Eq. 1).
+ * The search keeps, level by level, the beam_width cheapest children ordered
+ * by (path cost, parent rank, object, pose index) and returns the cheapest
+ * goal: order[l] = the object placed at level l, pose_index[l] its pose
+ * (index into that object's poses), level_cost[l] = the path cost after
+ * level l.  A beam at least as wide as every level is an exhaustive search.
+ * edges_scored (may be NULL) receives the number of edges evaluated.
+ * Poses are HOST pointers; the call is synchronous.  Needs jo_mode 0.
+ * Status PERCH_E_NOTFOUND when every path is refused.  Limits: 1 <= K <= 64,
+ * 1 <= beam_width <= 4096. */
+typedef struct {
+    int32_t mesh_id;
+    int32_t label;                   /* -1: cylinder V; >= 0: labels == label */
+    int32_t roi[4];                  /* u0, v0, u1, v1; an empty box = whole image */
+    const float *poses;              /* HOST, n*12 */
+    int32_t n;
+} perch_tree_object;
+
+PERCH_API perch_status perch_tree_search(perch_ctx *ctx, int32_t scene_id, const perch_tree_object *objects,
+                                         int32_t K, int32_t beam_width, int32_t *order,
+                                         int32_t *pose_index, int64_t *level_cost, int64_t *edges_scored);
+
 /* Debug view of the rasteriser used by perch_score_hypotheses: the z-buffer of
  * one pose as 64-bit keys (depth << 32) | triangle id, 0xFFFFFFFFFFFFFFFF where
  * nothing is covered.  keys is a HOST buffer of W*H uint64 of the scene; the

@@ -37,6 +37,18 @@ struct DevMesh {
     float lo[3], hi[3];       // object-frame bounding box of the vertices
 };
 
+// A state of the Monotone Scene Generation tree (the objects placed so
+// far) as per-pixel images, for scoring the edges that add one more object.
+struct TreeState {
+    const uint32_t* depth;    // W*H composed depth of the placed objects (0 = none), or nullptr
+    const uint32_t* mark;     // W*H bits: observed pixels explained by a placed object
+    const uint32_t* vol;      // W*H bits: observed pixels already counted in J_o
+    uint32_t* out_depth;      // child state (pre-copied from the parent), or nullptr
+    uint32_t* out_mark;
+    uint32_t* out_vol;
+    int margin;               // occlusion margin (0.1 mm)
+};
+
 // One work item: n hypotheses of one mesh against one scene.
 struct Job {
     DevScene sc;
@@ -46,6 +58,7 @@ struct Job {
     const float* poses;       // n*12 (device)
     int32_t* costs;           // n*2 (device)
     long long n;
+    TreeState tree;           // tree.depth == nullptr: plain scoring
 };
 
 // One scoring launch: the hypotheses of one job.  Launches that may run at

@@ -677,6 +677,7 @@ struct ScoreSmem {
     WarpProbe* probe;             // per warp scratch of the radius search (aliases stage)
     TriStage* stage;              // per warp 32 staged triangles (aliases probe)
     int* next_batch;
+    int* refused;                 // tree edges: the object would occlude a placed one
 };
 
 // ---- per-hypothesis vertex cache (one slot of global scratch per block) ----
@@ -826,7 +827,7 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
 // Rasterise, resolve and radius-search the pixel box rbox in z-buffer tiles.
 // J_r is accumulated when count_jr; marks are set for nearest neighbours that
 // fall in rows [mv0, mv1) of the admissible box vbox.
-template <int NT, bool K32, bool VC>
+template <int NT, bool K32, bool VC, bool TREE>
 __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, const unsigned long long* vc,
                             const int* rbox, const ScoreSmem& S, const int* vbox, int mv0, int mv1,
                             bool count_jr, int& jr_local)
@@ -906,8 +907,18 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                             unsigned long long w = reinterpret_cast<unsigned long long*>(zbuf)[zi];
                             if (w != kEmptyKey) { d = (unsigned)(w >> 32); tri = (int)(uint32_t)w; }
                         }
+                        int pix = v * sc.W + u;
+                        if (TREE && tri >= 0) {
+                            // a placed object in front hides the pixel; one behind
+                            // by more than the margin refuses the edge
+                            const unsigned sd = __ldg(&J.tree.depth[pix]);
+                            if (sd != 0) {
+                                if ((unsigned long long)d + (unsigned)J.tree.margin < sd) *S.refused = 1;
+                                if (!(d < sd)) tri = -1;
+                            }
+                            if (tri >= 0 && J.tree.out_depth) J.tree.out_depth[pix] = d;
+                        }
                         if (tri >= 0) {
-                            int pix = v * sc.W + u;
                             unsigned dobs = __ldg(&sc.depth[pix]);
                             bool occluded = sc.occ_margin >= 0 && dobs > 0 &&
                                             (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
@@ -959,6 +970,10 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                             float3 lq = srgb8_to_lab(kq.rgb & 255, (kq.rgb >> 8) & 255, (kq.rgb >> 16) & 255);
                             if (ciede2000(lq, make_float3(lp.x, lp.y, lp.z)) > sc.tau_c) explained = false;
                         }
+                        if (TREE && explained && J.tree.out_mark) {
+                            const int npix = pv * sc.W + pu;
+                            atomicOr(&J.tree.out_mark[npix >> 5], 1u << (npix & 31));
+                        }
                         if (!explained) {
                             if (count_jr) ++jr_local;
                         } else if (sc.jo_mode == 0) {
@@ -979,13 +994,14 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
 }
 
 // Score hypothesis h (one block).  Writes costs[2h] = J_o, costs[2h+1] = J_r.
-template <int NT>
+template <int NT, bool TREE>
 __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const ScoreSmem& S, float* s_pose,
                           int* s_rbox, int* s_vbox, int* s_k32, int (*s_red)[NT / 32],
                           unsigned long long* vc)
 {
     const DevScene& sc = J.sc;
     if (threadIdx.x < 12) s_pose[threadIdx.x] = J.poses[h * 12 + threadIdx.x];
+    if (TREE && threadIdx.x == 0) *S.refused = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         float zmax;
@@ -1019,11 +1035,11 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = 0u;
         __syncthreads();
         if (*s_k32) {
-            if (use_vc) score_tiles<NT, true, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, true, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, true, true, TREE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, true, false, TREE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
         } else {
-            if (use_vc) score_tiles<NT, false, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, false, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, false, true, TREE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, false, false, TREE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
         }
         __syncthreads();
         // ---- J_o over the admissible set V(h), rows [mv0, mv1)
@@ -1047,9 +1063,15 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
                 in = __fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)) <= rr && q2 >= 0.0f && q2 <= J.m.vol_h;
             }
             if (in) {
+                if (TREE) {
+                    if (J.tree.out_vol) atomicOr(&J.tree.out_vol[pix >> 5], 1u << (pix & 31));
+                    if ((__ldg(&J.tree.vol[pix >> 5]) >> (pix & 31)) & 1u) continue;   // counted before
+                }
                 ++n_in;
                 int bit = (v - mv0) * vw + (u - s_vbox[0]);
-                n_marked += (S.marks[bit >> 5] >> (bit & 31)) & 1u;
+                unsigned mk = (S.marks[bit >> 5] >> (bit & 31)) & 1u;
+                if (TREE && !mk) mk = (__ldg(&J.tree.mark[pix >> 5]) >> (pix & 31)) & 1u;
+                n_marked += mk;
             }
         }
         __syncthreads();
@@ -1075,8 +1097,9 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
             z += __shfl_xor_sync(0xffffffffu, z, o);
         }
         if (lane == 0) {
-            J.costs[2 * h] = y - z;
-            J.costs[2 * h + 1] = x;
+            const bool refused = TREE && *S.refused;
+            J.costs[2 * h] = refused ? -1 : y - z;
+            J.costs[2 * h + 1] = refused ? -1 : x;
         }
     }
     __syncthreads();
@@ -1130,13 +1153,14 @@ __device__ int claim_vslot(unsigned* mask, int nslots)
 // Persistent scoring kernel over one job: each block repeatedly takes the
 // next hypothesis index from a device counter (zero at launch) and scores
 // it.  The job is read from the kernel parameters, so its fields are
-// constant-bank operands.
-template <int NT>
+// constant-bank operands.  TREE: the job's hypotheses are edges of the
+// Monotone Scene Generation tree from the state in job.tree.
+template <int NT, bool TREE>
 __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
-    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_slot;
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_slot, s_refused;
     __shared__ long long s_h;
     __shared__ int s_red[3][NT / 32];
 
@@ -1148,6 +1172,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.probe = reinterpret_cast<WarpProbe*>(smem + L.probe);
     S.stage = reinterpret_cast<TriStage*>(smem + L.probe);
     S.next_batch = &s_next;
+    S.refused = &s_refused;
     if (threadIdx.x == 0) s_slot = a.vcache ? claim_vslot(a.vmask, a.vslots) : -1;
     __syncthreads();
     unsigned long long* vc = s_slot >= 0 ? a.vcache + (size_t)s_slot * a.vstride : nullptr;
@@ -1156,7 +1181,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
         __syncthreads();
         const long long h = s_h;
         if (h >= a.n) break;
-        score_one<NT>(a, a.job, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+        score_one<NT, TREE>(a, a.job, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
     }
     // every thread has passed the barrier after its last use of the slot
     if (threadIdx.x == 0 && s_slot >= 0) {
@@ -1170,15 +1195,16 @@ size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
     return smem_layout(cfg.zcap_words, mark_words, cfg.threads).total;
 }
 
-template <int NT>
+template <int NT, bool TREE>
 static int score_grid_nt(size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_score<NT, TREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT>, NT, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT, TREE>, NT, smem) != cudaSuccess)
         return -1;
     return max(1, per) * max(1, sms);
 }
@@ -1186,10 +1212,11 @@ static int score_grid_nt(size_t smem)
 int score_grid(const ScoreConfig& cfg, int mark_words)
 {
     size_t smem = score_smem_bytes(cfg, mark_words);
+    // the plain and the tree kernels share the vertex-cache pool: size for the smaller
     switch (cfg.threads) {
-    case 128: return score_grid_nt<128>(smem);
-    case 512: return score_grid_nt<512>(smem);
-    default: return score_grid_nt<256>(smem);
+    case 128: return min(score_grid_nt<128, false>(smem), score_grid_nt<128, true>(smem));
+    case 512: return min(score_grid_nt<512, false>(smem), score_grid_nt<512, true>(smem));
+    default: return min(score_grid_nt<256, false>(smem), score_grid_nt<256, true>(smem));
     }
 }
 
@@ -1197,9 +1224,16 @@ template <int NT>
 static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaStream_t s)
 {
     const size_t smem = score_smem_bytes(cfg, a.mark_words);
-    cudaError_t e = cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_score<NT><<<(unsigned)(a.n < grid ? a.n : grid), NT, smem, s>>>(a);
+    const unsigned g = (unsigned)(a.n < grid ? a.n : grid);
+    if (a.job.tree.depth) {
+        cudaError_t e = cudaFuncSetAttribute(k_score<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_score<NT, true><<<g, NT, smem, s>>>(a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_score<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_score<NT, false><<<g, NT, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -1209,12 +1243,12 @@ static cudaError_t add_score_node_nt(cudaGraph_t g, const cudaGraphNode_t* deps,
                                      cudaGraphNode_t* out)
 {
     const size_t smem = score_smem_bytes(cfg, a.mark_words);
-    cudaError_t e = cudaFuncSetAttribute(k_score<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_score<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ScoreArgs copy = a;
     void* args[] = {&copy};
     cudaKernelNodeParams kp{};
-    kp.func = (void*)k_score<NT>;
+    kp.func = (void*)k_score<NT, false>;
     kp.gridDim = dim3((unsigned)(a.n < grid ? a.n : grid));
     kp.blockDim = dim3(NT);
     kp.sharedMemBytes = (unsigned)smem;
@@ -1225,7 +1259,7 @@ static cudaError_t add_score_node_nt(cudaGraph_t g, const cudaGraphNode_t* deps,
 cudaError_t add_score_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                            const ScoreArgs& a, const ScoreConfig& cfg, int grid, cudaGraphNode_t* out)
 {
-    if (a.n <= 0 || a.n > 0xFFFFFFF0ll || grid <= 0) return cudaErrorInvalidValue;
+    if (a.n <= 0 || a.n > 0xFFFFFFF0ll || grid <= 0 || a.job.tree.depth) return cudaErrorInvalidValue;
     switch (cfg.threads) {
     case 128: return add_score_node_nt<128>(g, deps, ndeps, a, cfg, grid, out);
     case 512: return add_score_node_nt<512>(g, deps, ndeps, a, cfg, grid, out);

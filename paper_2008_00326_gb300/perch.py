@@ -29,7 +29,7 @@ EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_
            "perch_batch_graph_create", "perch_batch_graph_launch", "perch_batch_graph_destroy",
            "perch_autotune", "perch_server_start", "perch_submit", "perch_poll", "perch_wait",
            "perch_ticket_times", "perch_server_stop", "perch_pose_proposals",
-           "perch_default_gicp_params", "perch_refine_hypotheses")
+           "perch_default_gicp_params", "perch_refine_hypotheses", "perch_tree_search")
 
 
 class PerchError(RuntimeError):
@@ -138,6 +138,11 @@ class perch_gicp_params(C.Structure):
                 ("max_source_points", C.c_int32)]
 
 
+class perch_tree_object(C.Structure):
+    _fields_ = [("mesh_id", C.c_int32), ("label", C.c_int32), ("roi", C.c_int32 * 4),
+                ("poses", C.c_void_p), ("n", C.c_int32)]
+
+
 _lib = None
 
 
@@ -182,6 +187,7 @@ def load(path: str | None = None):
         "perch_pose_proposals": ([P, I32, I32, I32, P, I32, I32, I32, P, P, P], I32),
         "perch_default_gicp_params": ([P], I32),
         "perch_refine_hypotheses": ([P, I32, I32, I32, P, P, I64, P, P, P, P], I32),
+        "perch_tree_search": ([P, I32, P, I32, I32, P, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -407,6 +413,30 @@ def perch_refine_hypotheses(ctx, scene_id, mesh_id, label, roi, poses, params=No
                                                 None if info is None else _ptr_of(info),
                                                 getattr(stream, "cuda_stream", stream)))
     return poses_out
+
+
+def perch_tree_search(ctx, scene_id, objects, beam_width):
+    """Monotone Scene Generation tree search.  objects: list of (mesh_id, label,
+    roi or None, poses (n,12)).  Returns (order, pose_index, level_cost, edges)."""
+    K = len(objects)
+    arr = (perch_tree_object * K)()
+    keep = []
+    for k, (mid, label, roi, poses) in enumerate(objects):
+        p = np.ascontiguousarray(poses, np.float32).reshape(-1, 12)
+        keep.append(p)
+        arr[k].mesh_id = mid
+        arr[k].label = label
+        for i, x in enumerate(roi if roi is not None else (0, 0, 0, 0)):
+            arr[k].roi[i] = int(x)
+        arr[k].poses = p.ctypes.data
+        arr[k].n = p.shape[0]
+    order = np.zeros(K, np.int32)
+    pidx = np.zeros(K, np.int32)
+    lc = np.zeros(K, np.int64)
+    edges = C.c_int64()
+    _check(ctx, load().perch_tree_search(ctx, scene_id, arr, K, beam_width, order.ctypes.data,
+                                          pidx.ctypes.data, lc.ctypes.data, C.byref(edges)))
+    return order.tolist(), pidx.tolist(), lc.tolist(), edges.value
 
 
 def perch_set_launch_config(ctx, threads, zbuf_words, mark_bits=0):

@@ -344,6 +344,35 @@ def refine_leg(P, torch, dev, n_hyp=4096, reps=3):
             "best_translation_error_mm": {"scored_as_proposed": err_raw, "refined": err_ref}}
 
 
+def tree_leg(P, torch, dev, beam=4):
+    """Variant 2.0-B (Sec. III, Sec. VI-A): the Monotone Scene Generation tree
+    over the bench workload's three objects and 29,584 poses each, against
+    the parallel per-object search of PERCH 2.0 on the same poses."""
+    sc, desc = _workload(21)
+    ctx = P.Context(dev.index or 0)
+    sid = ctx.set_observation(sc)
+    mids = [ctx.load_mesh(m) for m in sc.meshes]
+    objs = [(mids[k], r.label, r.roi, r.poses) for k, r in enumerate(sc.requests)]
+    t0 = time.perf_counter()
+    order, pidx, lc, edges = P.perch_tree_search(ctx.ctx, sid, objs, beam)
+    t_tree = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    par = [ctx.best(ctx.score(sid, mids[k], r.label, r.roi, r.poses))[0] for k, r in enumerate(sc.requests)]
+    t_par = time.perf_counter() - t0
+
+    def err_mm(k, h):
+        pose = sc.requests[k].poses[h].reshape(3, 4).astype(np.float64)
+        return 1000.0 * float(np.linalg.norm(pose[:, 3] - np.asarray(sc.gt_poses[k], np.float64).reshape(3, 4)[:, 3]))
+
+    tree_pose = {j: h for j, h in zip(order, pidx)}
+    ctx.close()
+    return {"workload": desc + f"; tree beam {beam}, host buffers, synchronous",
+            "edges_scored": edges, "tree_s": t_tree, "tree_edges_s": edges / t_tree,
+            "parallel_s": t_par, "order": order, "path_cost": lc,
+            "translation_error_mm": {"tree": [err_mm(k, tree_pose[k]) for k in range(len(objs))],
+                                     "parallel": [err_mm(k, par[k]) for k in range(len(objs))]}}
+
+
 def served_leg(P, dev, seed=9):
     """Poisson request traces; serial plain path vs the continuous-batching
     server.  Latency = submission (arrival) to results.  Two mixes: all three
@@ -536,11 +565,12 @@ def main():
         return
 
     # ---- batched and served forms (rank 0, N = 1)
-    batched = served = refine = None
+    batched = served = refine = tree = None
     if not a.no_forms and world == 1:
         batched = batched_leg(P, torch, dev)
         served = served_leg(P, dev)
         refine = refine_leg(P, torch, dev)
+        tree = tree_leg(P, torch, dev)
 
     # ---- CPU oracle baseline and the roofline's algorithmic work
     cpu, work = (None, None)
@@ -591,6 +621,7 @@ def main():
         "batched": batched,
         "served": served,
         "refine": refine,
+        "tree": tree,
     }
     print(json.dumps(out))
     ctx.close()

@@ -79,7 +79,10 @@ def _args():
     ap.add_argument("--grid-half", type=int, default=21, help="positions per axis = 2*g+1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched, served, refine and tree legs")
+    ap.add_argument("--legs", default="batched,served,refine,tree",
+                    help="comma-separated subset of the batched, served, refine and tree legs")
+    ap.add_argument("--refine-hyp", type=int, default=4096, help="hypotheses per object of the refine leg")
     return ap.parse_args()
 
 
@@ -168,9 +171,20 @@ def cpu_baseline(sc, seconds, rng_seed=0):
         if time.perf_counter() >= deadline:
             break
     work = np.concatenate(work)
+    # the same oracle on one core: one hypothesis per object
+    t1, n1 = 0.0, 0
+    for req in sc.requests:
+        pick = rng.choice(len(req.poses), 1, replace=False)
+        osc = O.OracleScene.from_scene(sc)
+        om = O.OracleMesh.from_mesh(sc.meshes[req.mesh_index])
+        t0 = time.perf_counter()
+        O.score(osc, om, req.poses[pick], label=req.label, roi=req.roi, threads=1)
+        t1 += time.perf_counter() - t0
+        n1 += 1
     return {"value": total_h / total_t, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{total_h} random hypotheses ({rounds} rounds x {per} per object) of the same "
-                      f"workload, brute-force nearest neighbours, {total_t:.1f} s"}, work
+                      f"workload, brute-force nearest neighbours, {total_t:.1f} s",
+            "value_1core": n1 / t1, "sample_1core": f"{n1} hypotheses (one per object), {t1:.1f} s"}, work
 
 
 def reference_arm(a):
@@ -566,11 +580,12 @@ def main():
 
     # ---- batched and served forms (rank 0, N = 1)
     batched = served = refine = tree = None
-    if not a.no_forms and world == 1:
-        batched = batched_leg(P, torch, dev)
-        served = served_leg(P, dev)
-        refine = refine_leg(P, torch, dev)
-        tree = tree_leg(P, torch, dev)
+    legs = set() if a.no_forms else set(a.legs.split(","))
+    if world == 1:
+        batched = batched_leg(P, torch, dev) if "batched" in legs else None
+        served = served_leg(P, dev) if "served" in legs else None
+        refine = refine_leg(P, torch, dev, n_hyp=a.refine_hyp) if "refine" in legs else None
+        tree = tree_leg(P, torch, dev) if "tree" in legs else None
 
     # ---- CPU oracle baseline and the roofline's algorithmic work
     cpu, work = (None, None)
@@ -596,12 +611,22 @@ def main():
                        "cell_candidates": C, "in_volume": IV, "ops": per_h}
         achieved = ops_step / (score_total_ms / 1000.0)
         traffic = measured_traffic()
+        # the rasteriser's shared-memory z-buffer updates against the measured atomicMin rate
+        try:
+            a32, a64 = P.perch_measure_smem_atomics(local)
+        except P.PerchError:
+            a32 = a64 = None
+        frags = sum(mean[k]["fragments"] * len(r.poses) for k, r in enumerate(reqs)) / (score_total_ms / 1000.0)
+        raster = {"fragments_per_s": frags, "smem_atomic_min_u32_per_s": a32,
+                  "smem_atomic_min_u64_per_s": a64, "frac_u32": (frags / a32) if a32 else None,
+                  "note": "one 32-bit shared-memory atomicMin per covered sample on this workload"}
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_ops,
                 "traffic": None if traffic is None else traffic,
                 "kernel": "k_score (fused raster + resolve + 27-cell radius search + J_o)",
                 "ops_per_unit": OPS, "work_per_hypothesis_by_object": mean,
-                "peak_basis": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz (max SM clock)"}
+                "peak_basis": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz (max SM clock)",
+                "raster_atomics": raster}
     lat = sorted(obj_lat)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,

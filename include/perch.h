@@ -421,6 +421,12 @@ PERCH_API perch_status perch_tree_search(perch_ctx *ctx, int32_t scene_id, const
                                          int32_t K, int32_t beam_width, int32_t *order,
                                          int32_t *pose_index, int64_t *level_cost, int64_t *edges_scored);
 
+/* Measured shared-memory atomicMin throughput of the device (operations per
+ * second over all SMs, random addresses in a 32 KB array per block), the
+ * ceiling of the rasteriser's z-buffer updates.  A measurement helper with no
+ * counterpart in the paper; about 50 ms of GPU time. */
+PERCH_API perch_status perch_measure_smem_atomics(int32_t device, double *u32_per_s, double *u64_per_s);
+
 /* Debug view of the rasteriser used by perch_score_hypotheses: the z-buffer of
  * one pose as 64-bit keys (depth << 32) | triangle id, 0xFFFFFFFFFFFFFFFF where
  * nothing is covered.  keys is a HOST buffer of W*H uint64 of the scene; the

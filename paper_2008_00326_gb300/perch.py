@@ -29,7 +29,8 @@ EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_
            "perch_batch_graph_create", "perch_batch_graph_launch", "perch_batch_graph_destroy",
            "perch_autotune", "perch_server_start", "perch_submit", "perch_poll", "perch_wait",
            "perch_ticket_times", "perch_server_stop", "perch_pose_proposals",
-           "perch_default_gicp_params", "perch_refine_hypotheses", "perch_tree_search")
+           "perch_default_gicp_params", "perch_refine_hypotheses", "perch_tree_search",
+           "perch_measure_smem_atomics")
 
 
 class PerchError(RuntimeError):
@@ -188,6 +189,7 @@ def load(path: str | None = None):
         "perch_default_gicp_params": ([P], I32),
         "perch_refine_hypotheses": ([P, I32, I32, I32, P, P, I64, P, P, P, P], I32),
         "perch_tree_search": ([P, I32, P, I32, I32, P, P, P, P], I32),
+        "perch_measure_smem_atomics": ([I32, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -437,6 +439,15 @@ def perch_tree_search(ctx, scene_id, objects, beam_width):
     _check(ctx, load().perch_tree_search(ctx, scene_id, arr, K, beam_width, order.ctypes.data,
                                           pidx.ctypes.data, lc.ctypes.data, C.byref(edges)))
     return order.tolist(), pidx.tolist(), lc.tolist(), edges.value
+
+
+def perch_measure_smem_atomics(device=0):
+    """(u32, u64) shared-memory atomicMin operations per second."""
+    a, b = C.c_double(), C.c_double()
+    st = load().perch_measure_smem_atomics(device, C.byref(a), C.byref(b))
+    if st != PERCH_OK:
+        raise PerchError(st, "perch_measure_smem_atomics")
+    return a.value, b.value
 
 
 def perch_set_launch_config(ctx, threads, zbuf_words, mark_bits=0):

@@ -1412,13 +1412,28 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
         *zbuf_words = c->cfg.zcap_words;
         return PERCH_OK;
     }
-    // time each shape on a sample: the first min(n, 384) hypotheses of each item
-    std::vector<perch_work_item> sample(items, items + n_items);
-    for (auto& it : sample) it.n = std::min<int64_t>(it.n, 384);
+    // time each shape on a sample of whole items, largest first, holding at
+    // least an eighth of the hypotheses (and 50,000, or all): launches of
+    // the same sizes as the real run, so per-launch tails weigh the same
+    std::vector<int32_t> idx(n_items);
+    long long all = 0;
+    for (int32_t i = 0; i < n_items; ++i) {
+        idx[i] = i;
+        all += std::max<int64_t>(0, items[i].n);
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return items[x].n > items[y].n; });
+    const long long want = std::min(all, std::max(all / 8, 50000ll));
+    std::vector<perch_work_item> sample;
+    long long got = 0;
+    for (int32_t i : idx) {
+        if (got >= want) break;
+        sample.push_back(items[i]);
+        got += std::max<int64_t>(0, items[i].n);
+    }
     std::vector<perch::Job> jobs;
     int mw;
     long long total;
-    perch_status st = batch_jobs(c, sample.data(), n_items, poses, costs, &jobs, &mw, &total);
+    perch_status st = batch_jobs(c, sample.data(), (int32_t)sample.size(), poses, costs, &jobs, &mw, &total);
     if (st != PERCH_OK) return st;
     const perch::ScoreConfig saved = c->cfg;
     perch::ScoreConfig best = saved;
@@ -1435,7 +1450,7 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
             cfg.zcap_words = zw[zi];
             if (perch::score_smem_bytes(cfg, mw) > 200 * 1024) continue;
             float ms = 3.0e38f;
-            for (int rep = 0; rep < 3 && st == PERCH_OK; ++rep) {
+            for (int rep = 0; rep < 2 && st == PERCH_OK; ++rep) {
                 cudaEventRecord(e0, c->stream);
                 st = run_jobs(c, c->plain, jobs, mw, cfg, c->stream, nullptr);
                 cudaEventRecord(e1, c->stream);

@@ -364,27 +364,32 @@ def tree_leg(P, torch, dev, beam=4):
     the parallel per-object search of PERCH 2.0 on the same poses."""
     sc, desc = _workload(21)
     ctx = P.Context(dev.index or 0)
-    sid = ctx.set_observation(sc)
     mids = [ctx.load_mesh(m) for m in sc.meshes]
     objs = [(mids[k], r.label, r.roi, r.poses) for k, r in enumerate(sc.requests)]
-    t0 = time.perf_counter()
-    order, pidx, lc, edges = P.perch_tree_search(ctx.ctx, sid, objs, beam)
-    t_tree = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    par = [ctx.best(ctx.score(sid, mids[k], r.label, r.roi, r.poses))[0] for k, r in enumerate(sc.requests)]
-    t_par = time.perf_counter() - t0
 
     def err_mm(k, h):
         pose = sc.requests[k].poses[h].reshape(3, 4).astype(np.float64)
         return 1000.0 * float(np.linalg.norm(pose[:, 3] - np.asarray(sc.gt_poses[k], np.float64).reshape(3, 4)[:, 3]))
 
-    tree_pose = {j: h for j, h in zip(order, pidx)}
+    out = {"workload": desc + f"; tree beam {beam}, host buffers, synchronous"}
+    # with the observed-depth occluder marking of PERCH 2.0, and without it
+    # (the tree alone models the occlusions between the placed objects)
+    for name, over in (("occluder_marking", {}), ("no_occluder_marking", {"occ_margin_units": -1})):
+        sid = ctx.set_observation(sc, **over)
+        t0 = time.perf_counter()
+        order, pidx, lc, edges = P.perch_tree_search(ctx.ctx, sid, objs, beam)
+        t_tree = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        par = [ctx.best(ctx.score(sid, mids[k], r.label, r.roi, r.poses))[0] for k, r in enumerate(sc.requests)]
+        t_par = time.perf_counter() - t0
+        tree_pose = {j: h for j, h in zip(order, pidx)}
+        out[name] = {"edges_scored": edges, "tree_s": t_tree, "tree_edges_s": edges / t_tree,
+                     "parallel_s": t_par, "order": order, "path_cost": lc,
+                     "translation_error_mm": {"tree": [err_mm(k, tree_pose[k]) for k in range(len(objs))],
+                                              "parallel": [err_mm(k, par[k]) for k in range(len(objs))]}}
+        P.perch_release_scene(ctx.ctx, sid)
     ctx.close()
-    return {"workload": desc + f"; tree beam {beam}, host buffers, synchronous",
-            "edges_scored": edges, "tree_s": t_tree, "tree_edges_s": edges / t_tree,
-            "parallel_s": t_par, "order": order, "path_cost": lc,
-            "translation_error_mm": {"tree": [err_mm(k, tree_pose[k]) for k in range(len(objs))],
-                                     "parallel": [err_mm(k, par[k]) for k in range(len(objs))]}}
+    return out
 
 
 def served_leg(P, dev, seed=9):

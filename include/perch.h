@@ -423,6 +423,21 @@ PERCH_API perch_status perch_tree_search(perch_ctx *ctx, int32_t scene_id, const
                                          int32_t K, int32_t beam_width, int32_t *order,
                                          int32_t *pose_index, int64_t *level_cost, int64_t *edges_scored);
 
+/* ---- Pose accuracy (the measures of Sec. VI) ---------------------------------
+ * perch_add_s: for each of n pose pairs, the mean over the mesh's vertices x
+ * of || P x - T x || (symmetric 0: ADD) or of the distance from P x to the
+ * closest T y over the vertices y (symmetric 1: ADD-S), in metres; vertex
+ * transforms and distances in binary32, the mean in binary64.  poses and
+ * poses_true are n*12 row-major 3x4, add receives n doubles.  cuda_stream
+ * NULL: HOST pointers, synchronous; otherwise DEVICE pointers on that stream.
+ * ADD-S costs n * V^2 distance evaluations (V vertices).
+ * perch_add_s_auc (host only): the area under the accuracy curve
+ * acc(t) = |{i : add_i < t}| / n for t in [0, max_threshold], divided by
+ * max_threshold: the mean of max(0, 1 - add_i / max_threshold). */
+PERCH_API perch_status perch_add_s(perch_ctx *ctx, int32_t mesh_id, const float *poses, const float *poses_true,
+                                   int64_t n, int32_t symmetric, double *add, void *cuda_stream);
+PERCH_API perch_status perch_add_s_auc(const double *add, int64_t n, double max_threshold, double *auc);
+
 /* Measured shared-memory atomicMin throughput of the device (operations per
  * second over all SMs, random addresses in a 32 KB array per block), the
  * ceiling of the rasteriser's z-buffer updates.  A measurement helper with no

@@ -76,6 +76,8 @@ def lib():
         L.or_gicp_quantise.restype = C.c_int64
         L.or_gicp_solve.argtypes = [P, P]
         L.or_gicp_rotation.argtypes = [P, P]
+        L.or_add_s.argtypes = [P, C.c_int32, P, P, C.c_int32]
+        L.or_add_s.restype = C.c_double
         L.or_score_tree.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, P, P, P, P, P, C.c_int32]
         _lib = L
     return _lib
@@ -286,6 +288,31 @@ def score_tree(scene: OracleScene, mesh: OracleMesh, poses, state, label=-1, roi
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return (costs, band, (cd, cm, cv)) if child else (costs, band)
+
+
+def add_s(verts, pose_a, pose_b, symmetric=True):
+    """ADD-S (symmetric) or ADD of pose_a against pose_b over the model points, float64."""
+    v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+    a = np.ascontiguousarray(pose_a, np.float32).reshape(12)
+    b = np.ascontiguousarray(pose_b, np.float32).reshape(12)
+    return float(lib().or_add_s(_ptr(v), v.shape[0], _ptr(a), _ptr(b), int(bool(symmetric))))
+
+
+def add_auc(errors, max_threshold=0.1):
+    """Area under the accuracy curve acc(t) = |{i : e_i < t}| / n on [0, T],
+    divided by T: the step function integrated piece by piece between its
+    sorted break points."""
+    e = np.sort(np.asarray(errors, np.float64))
+    n, T = len(e), float(max_threshold)
+    area, prev, below = 0.0, 0.0, 0
+    for x in e:
+        if x >= T:
+            break
+        area += (x - prev) * below / n if x > prev else 0.0
+        prev = max(prev, x)
+        below += 1
+    area += (T - prev) * below / n
+    return area / T
 
 
 def num_threads():

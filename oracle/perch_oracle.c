@@ -1118,3 +1118,49 @@ int or_score_tree(const or_scene *sc, const or_mesh *m, int32_t label, const int
     free(Ixyz); free(Ilab); free(Ipix);
     return rc;
 }
+
+/* ---------------------------------------------------------------------- */
+/* ADD and ADD-S pose errors (the accuracy measure of Sec. VI)             */
+/* ---------------------------------------------------------------------- */
+
+/* Mean over the model points x of the distance between x under pose A and
+ * (symmetric: the closest model point, else the same point) under pose B,
+ * in binary64 (poses row-major 3x4). */
+double or_add_s(const float *verts, int32_t n_verts, const float A[12], const float B[12], int32_t symmetric)
+{
+    if (n_verts < 1)
+        return 0.0;
+    double *pb = malloc(sizeof(double) * 3 * n_verts);
+    if (!pb)
+        return -1.0;
+    for (int32_t i = 0; i < n_verts; i++) {
+        const float *x = verts + 3 * i;
+        for (int r = 0; r < 3; r++)
+            pb[3 * i + r] = (double)B[4 * r] * x[0] + (double)B[4 * r + 1] * x[1] + (double)B[4 * r + 2] * x[2]
+                            + (double)B[4 * r + 3];
+    }
+    double sum = 0.0;
+    for (int32_t i = 0; i < n_verts; i++) {
+        const float *x = verts + 3 * i;
+        double pa[3];
+        for (int r = 0; r < 3; r++)
+            pa[r] = (double)A[4 * r] * x[0] + (double)A[4 * r + 1] * x[1] + (double)A[4 * r + 2] * x[2]
+                    + (double)A[4 * r + 3];
+        double best;
+        if (symmetric) {
+            best = INFINITY;
+            for (int32_t j = 0; j < n_verts; j++) {
+                double dx = pa[0] - pb[3 * j], dy = pa[1] - pb[3 * j + 1], dz = pa[2] - pb[3 * j + 2];
+                double d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < best)
+                    best = d2;
+            }
+        } else {
+            double dx = pa[0] - pb[3 * i], dy = pa[1] - pb[3 * i + 1], dz = pa[2] - pb[3 * i + 2];
+            best = dx * dx + dy * dy + dz * dz;
+        }
+        sum += sqrt(best);
+    }
+    free(pb);
+    return sum / n_verts;
+}

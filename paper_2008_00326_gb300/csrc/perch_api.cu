@@ -1240,6 +1240,45 @@ perch_status perch_tree_search(perch_ctx* c, int32_t scene_id, const perch_tree_
     return PERCH_OK;
 }
 
+perch_status perch_add_s(perch_ctx* c, int32_t mesh_id, const float* poses, const float* poses_true, int64_t n,
+                         int32_t symmetric, double* add, void* cuda_stream)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (n < 0) return fail(c, PERCH_E_INVALID, "n < 0");
+    if (n == 0) return PERCH_OK;
+    if (!poses || !poses_true || !add) return fail(c, PERCH_E_INVALID, "null pointer");
+    auto mi = c->meshes.find(mesh_id);
+    if (mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
+    DeviceGuard g(c->device);
+    const perch::DevMesh& m = mi->second.dm;
+    if (cuda_stream) {
+        cudaError_t e = perch::launch_add_s(m.verts, m.n_verts, poses, poses_true, n, symmetric ? 1 : 0, add,
+                                            (cudaStream_t)cuda_stream);
+        return e ? cuda_fail(c, e, "perch_add_s") : PERCH_OK;
+    }
+    perch_status st = ensure_stage(c, (size_t)n * (48 + 48 + 8));
+    if (st != PERCH_OK) return st;
+    float* dp = (float*)c->stage;
+    float* dt = (float*)((char*)c->stage + (size_t)n * 48);
+    double* dout = (double*)((char*)c->stage + (size_t)n * 96);
+    cudaError_t e = cudaMemcpyAsync(dp, poses, (size_t)n * 48, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(dt, poses_true, (size_t)n * 48, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = perch::launch_add_s(m.verts, m.n_verts, dp, dt, n, symmetric ? 1 : 0, dout, c->stream);
+    if (!e) e = cudaMemcpyAsync(add, dout, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return e ? cuda_fail(c, e, "perch_add_s") : PERCH_OK;
+}
+
+perch_status perch_add_s_auc(const double* add, int64_t n, double max_threshold, double* auc)
+{
+    if (!add || !auc || n < 1 || !(max_threshold > 0.0)) return PERCH_E_INVALID;
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += std::max(0.0, 1.0 - add[i] / max_threshold);
+    *auc = s / (double)n;
+    return PERCH_OK;
+}
+
 perch_status perch_debug_render_keys(perch_ctx* c, int32_t scene_id, int32_t mesh_id,
                                      const int32_t* roi, const float* pose, uint64_t* keys)
 {

@@ -126,6 +126,10 @@ cudaError_t launch_gicp(const GicpArgs& a, int grid, cudaStream_t s);
 // Observed normal per pixel from central differences of the depth image.
 cudaError_t launch_obs_normals(const DevScene& sc, int normal_jump, float4* nrm, cudaStream_t s);
 
+// ADD (symmetric 0) / ADD-S (1) of n pose pairs over a mesh's vertices.
+cudaError_t launch_add_s(const float4* verts, int n_verts, const float* poses, const float* poses_true,
+                         long long n, int symmetric, double* out, cudaStream_t s);
+
 // Observation build (voxel hash over I).
 struct BuildBuffers {
     // scratch (freed after the build)

@@ -30,7 +30,7 @@ EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_
            "perch_autotune", "perch_server_start", "perch_submit", "perch_poll", "perch_wait",
            "perch_ticket_times", "perch_server_stop", "perch_pose_proposals",
            "perch_default_gicp_params", "perch_refine_hypotheses", "perch_tree_search",
-           "perch_measure_smem_atomics")
+           "perch_measure_smem_atomics", "perch_add_s", "perch_add_s_auc")
 
 
 class PerchError(RuntimeError):
@@ -190,6 +190,8 @@ def load(path: str | None = None):
         "perch_refine_hypotheses": ([P, I32, I32, I32, P, P, I64, P, P, P, P], I32),
         "perch_tree_search": ([P, I32, P, I32, I32, P, P, P, P], I32),
         "perch_measure_smem_atomics": ([I32, P, P], I32),
+        "perch_add_s": ([P, I32, P, P, I64, I32, P, P], I32),
+        "perch_add_s_auc": ([P, I64, C.c_double, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -439,6 +441,30 @@ def perch_tree_search(ctx, scene_id, objects, beam_width):
     _check(ctx, load().perch_tree_search(ctx, scene_id, arr, K, beam_width, order.ctypes.data,
                                           pidx.ctypes.data, lc.ctypes.data, C.byref(edges)))
     return order.tolist(), pidx.tolist(), lc.tolist(), edges.value
+
+
+def perch_add_s(ctx, mesh_id, poses, poses_true, symmetric=True, out=None, stream=None):
+    """ADD-S (symmetric) or ADD per pose pair.  Host mode: numpy in, float64 (n,) out."""
+    if stream is None:
+        p, pp = _host(poses, np.float32)
+        t, pt = _host(poses_true, np.float32)
+        n = p.size // 12
+        res = np.empty(n, np.float64)
+        _check(ctx, load().perch_add_s(ctx, mesh_id, pp, pt, n, int(bool(symmetric)), res.ctypes.data, None))
+        return res
+    n = poses.numel() // 12
+    _check(ctx, load().perch_add_s(ctx, mesh_id, _ptr_of(poses), _ptr_of(poses_true), n, int(bool(symmetric)),
+                                    _ptr_of(out), getattr(stream, "cuda_stream", stream)))
+    return out
+
+
+def perch_add_s_auc(add, max_threshold=0.1):
+    a, pa = _host(add, np.float64)
+    out = C.c_double()
+    st = load().perch_add_s_auc(pa, a.size, max_threshold, C.byref(out))
+    if st != PERCH_OK:
+        raise PerchError(st, "perch_add_s_auc")
+    return out.value
 
 
 def perch_measure_smem_atomics(device=0):

@@ -339,13 +339,16 @@ def refine_leg(P, torch, dev, n_hyp=4096, reps=3):
         with torch.cuda.stream(s):
             score(src)
         s.synchronize()
-        errs = []
+        errs, adds = [], []
         for k, r in enumerate(reqs):
-            pose = src[k][int(d_bi[k])].cpu().numpy().reshape(3, 4).astype(np.float64)
-            errs.append(1000.0 * float(np.linalg.norm(pose[:, 3] - np.asarray(sc.gt_poses[k], np.float64).reshape(3, 4)[:, 3])))
-        return errs
+            pose = src[k][int(d_bi[k])].cpu().numpy()
+            gt = np.asarray(sc.gt_poses[k], np.float32).reshape(12)
+            errs.append(1000.0 * float(np.linalg.norm(pose.reshape(3, 4)[:, 3].astype(np.float64)
+                                                      - gt.reshape(3, 4)[:, 3])))
+            adds.append(float(P.perch_add_s(ctx.ctx, mids[k], pose[None], gt[None], True)[0]))
+        return errs, adds
 
-    err_raw, err_ref = best_errors(d_in), best_errors(d_out)
+    (err_raw, add_raw), (err_ref, add_ref) = best_errors(d_in), best_errors(d_out)
     n = sum(len(r.poses) for r in reqs)
     ctx.close()
     return {"workload": f"sixdof_5obj: 640x480, 5 objects x {n_hyp} 6-DoF hypotheses (labels, ROIs); "
@@ -355,7 +358,11 @@ def refine_leg(P, torch, dev, n_hyp=4096, reps=3):
             "hypotheses": n, "refine_ms": t_refine, "refine_hyp_s": n / (t_refine / 1000.0),
             "pipeline_ms": t_pipe, "pipeline_hyp_s": n / (t_pipe / 1000.0),
             "mean_updates": float(info[:, 0].mean()), "mean_correspondences": float(info[:, 1].mean()),
-            "best_translation_error_mm": {"scored_as_proposed": err_raw, "refined": err_ref}}
+            "best_translation_error_mm": {"scored_as_proposed": err_raw, "refined": err_ref},
+            "best_add_s_mm": {"scored_as_proposed": [1000 * x for x in add_raw], "refined": [1000 * x for x in add_ref]},
+            "add_s_auc_0.1m": {"scored_as_proposed": P.perch_add_s_auc(add_raw), "refined": P.perch_add_s_auc(add_ref)},
+            "add_s_below_2cm": {"scored_as_proposed": sum(x < 0.02 for x in add_raw),
+                                "refined": sum(x < 0.02 for x in add_ref), "of": len(reqs)}}
 
 
 def tree_leg(P, torch, dev, beam=4):

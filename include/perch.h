@@ -251,9 +251,9 @@ PERCH_API perch_status perch_batch_graph_launch(perch_batch_graph *g, void *cuda
 PERCH_API perch_status perch_batch_graph_destroy(perch_batch_graph *g);
 
 /* Autotuner: time the candidate launch shapes (threads per block x z-buffer
- * words) on a sample of this batch -- its largest items, whole, holding at
- * least an eighth of the hypotheses (DEVICE poses/costs; the sampled items'
- * costs are overwritten) --, keep the
+ * words) on a sample of this batch -- every 8th item in order of size,
+ * whole; batches of fewer than 16 items whole (DEVICE poses/costs; the
+ * sampled items' costs are overwritten) --, keep the
  * fastest as the context's launch configuration and remember it for batches
  * of the same class (largest ROI area and triangle count, each rounded to a
  * power of two); a later call for a known class returns the remembered shape

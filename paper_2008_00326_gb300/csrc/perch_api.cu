@@ -1451,24 +1451,16 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
         *zbuf_words = c->cfg.zcap_words;
         return PERCH_OK;
     }
-    // time each shape on a sample of whole items, largest first, holding at
-    // least an eighth of the hypotheses (and 50,000, or all): launches of
-    // the same sizes as the real run, so per-launch tails weigh the same
+    // time each shape on a sample of whole items (launches of the real
+    // sizes, so per-launch tails weigh the same): every 8th item in order of
+    // size, which keeps the batch's mix of small and large items; batches of
+    // fewer than 16 items are timed whole
     std::vector<int32_t> idx(n_items);
-    long long all = 0;
-    for (int32_t i = 0; i < n_items; ++i) {
-        idx[i] = i;
-        all += std::max<int64_t>(0, items[i].n);
-    }
+    for (int32_t i = 0; i < n_items; ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return items[x].n > items[y].n; });
-    const long long want = std::min(all, std::max(all / 8, 50000ll));
     std::vector<perch_work_item> sample;
-    long long got = 0;
-    for (int32_t i : idx) {
-        if (got >= want) break;
-        sample.push_back(items[i]);
-        got += std::max<int64_t>(0, items[i].n);
-    }
+    const int32_t step = n_items < 16 ? 1 : 8;
+    for (int32_t k = step / 2; k < n_items; k += step) sample.push_back(items[idx[k]]);
     std::vector<perch::Job> jobs;
     int mw;
     long long total;

@@ -645,7 +645,7 @@ def main():
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "hypotheses_per_step": n_step, "l2": "flushed between steps (512 MiB write)",
-                   "launch": {"threads": 256, "zbuf_words": 16384}},
+                   "launch": {"threads": 256, "zbuf_words": 8192, "mark_bits": 65536}},
         "latency_ms": {"search_p50": lat[len(lat) // 2], "search_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "what": f"one object's {len(reqs[0].poses):,}-hypothesis search (score + argmin), device-timed"},
         "e2e": {"value": world * n_step / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -230,12 +230,13 @@ int mark_words_for(const SceneRec& s, int label, const int roi[4], int cap_bits)
 }
 
 // Fit the z-buffer into the opt-in shared memory limit of the device.
+// Shrink the z-buffer of *cfg (the caller's launch shape) until the block's
+// shared memory fits the device.
 perch_status fit_config(perch_ctx* c, int mark_words, perch::ScoreConfig* cfg)
 {
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (max_optin <= 0) max_optin = 48 * 1024;
-    *cfg = c->cfg;
     while (perch::score_smem_bytes(*cfg, mark_words) > (size_t)max_optin && cfg->zcap_words > 1024)
         cfg->zcap_words /= 2;
     if (perch::score_smem_bytes(*cfg, mark_words) > (size_t)max_optin)
@@ -1331,7 +1332,7 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
     perch_status st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
     if (st != PERCH_OK) return st;
     if (total == 0) return fail(c, PERCH_E_INVALID, "empty batch");
-    perch::ScoreConfig cfg;
+    perch::ScoreConfig cfg = c->cfg;
     if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
     const int resident = perch::score_grid(cfg, mw);
     if (resident <= 0) {

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <condition_variable>
 #include <deque>
@@ -41,6 +42,7 @@ struct SceneRec {
     void* table = nullptr;
     void* nrm = nullptr;           // observed normals (GICP targets), made on first use
     int nrm_jump = -1;             // the normal_max_jump_units they were made with
+    void* near = nullptr;          // near-cell bitmap (DevScene::near_bits)
 };
 
 // Everything one chain of scoring launches needs besides its inputs: one
@@ -387,6 +389,46 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
     return PERCH_OK;
 }
 
+// Near-cell bitmap of an observation: one bit per hash cell of the observed
+// points' cell box grown by one, set iff one of the cell's 27 neighbours holds
+// a point.  Skipped (no filter) when the box exceeds 2^27 cells.
+perch_status build_near_cells(perch_ctx* c, SceneRec& s)
+{
+    perch::DevScene& d = s.ds;
+    d.near_bits = nullptr;
+    if (d.n_pts <= 0) return PERCH_OK;
+    void* bnd = nullptr;
+    perch_status st = dalloc(c, 6 * sizeof(int), &bnd);
+    if (st != PERCH_OK) return st;
+    const int init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+    int got[6];
+    cudaError_t e = cudaMemcpyAsync(bnd, init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = perch::launch_cell_bounds(d, (int*)bnd, c->stream);
+    if (!e) e = cudaMemcpyAsync(got, bnd, sizeof(got), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    dfree(c, bnd);
+    if (e) return cuda_fail(c, e, "near-cell bounds");
+    long long cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        d.near_lo[a] = got[a] - 1;
+        d.near_n[a] = got[3 + a] - got[a] + 3;
+        cells *= d.near_n[a];
+    }
+    if (cells > (1ll << 27)) return PERCH_OK;
+    const size_t bytes = (size_t)((cells + 31) / 32) * 4;
+    void* occ = nullptr;
+    if ((st = dalloc(c, bytes, &s.near)) != PERCH_OK) return st;
+    if ((st = dalloc(c, bytes, &occ)) != PERCH_OK) return st;
+    e = cudaMemsetAsync(s.near, 0, bytes, c->stream);
+    if (!e) e = cudaMemsetAsync(occ, 0, bytes, c->stream);
+    if (!e) e = perch::launch_near_cells(d, (uint32_t*)occ, (uint32_t*)s.near, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    dfree(c, occ);
+    if (e) return cuda_fail(c, e, "near-cell bitmap");
+    d.near_bits = (const uint32_t*)s.near;
+    return PERCH_OK;
+}
+
 // Grow a scratch buffer of X (after every earlier run that used X).
 perch_status grow(perch_ctx* c, ScoreScratch& X, void** buf, size_t* have, size_t need)
 {
@@ -676,6 +718,7 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     };
     auto cleanup_scene = [&]() {
         dfree(c, s.depth); dfree(c, s.labels); dfree(c, s.lab); dfree(c, s.pts); dfree(c, s.table); dfree(c, s.nrm);
+        dfree(c, s.near);
     };
     if ((st = dalloc(c, npx * sizeof(uint16_t), &s.depth)) ||
         (labels && (st = dalloc(c, npx * sizeof(int32_t), &s.labels))) ||
@@ -757,6 +800,10 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     }
     d.table = (const uint4*)s.table;
     d.table_mask = cap_small - 1;
+    if ((st = build_near_cells(c, s)) != PERCH_OK) {
+        cleanup_scene();
+        return st;
+    }
     int32_t id = c->next_id++;
     c->scenes[id] = s;
     *scene_id = id;
@@ -772,6 +819,7 @@ perch_status perch_release_scene(perch_ctx* c, int32_t scene_id)
     cudaStreamSynchronize(c->stream);
     SceneRec& s = it->second;
     dfree(c, s.depth); dfree(c, s.labels); dfree(c, s.lab); dfree(c, s.pts); dfree(c, s.table); dfree(c, s.nrm);
+        dfree(c, s.near);
     c->scenes.erase(it);
     return PERCH_OK;
 }

@@ -26,6 +26,11 @@ struct DevScene {
     const uint4* table;       // hash slots: (key lo, key hi, start, count)
     uint32_t table_mask;
     int n_pts;
+    // bit per hash cell in the box [near_lo, near_lo + near_n): set iff one of
+    // the cell's 27 neighbours (itself included) holds an observed point;
+    // cells outside the box have none.  nullptr: no filter.
+    const uint32_t* near_bits;
+    int near_lo[3], near_n[3];
 };
 
 // Device-resident mesh.
@@ -148,6 +153,10 @@ cudaError_t launch_build(const DevScene& sc, const BuildBuffers& b, uint32_t tab
                          const uint8_t* rgb_dev, int* err, cudaStream_t s);
 cudaError_t launch_compact_table(const uint4* big, uint32_t cap_big, uint4* small, uint32_t cap_small,
                                  int* err, cudaStream_t s);
+// Bounding box of the observed points' hash cells: bounds = (min x, y, z, max x, y, z).
+cudaError_t launch_cell_bounds(const DevScene& sc, int* bounds, cudaStream_t s);
+// Fill sc.near_bits (zeroed) through the occupancy bitmap occ (zeroed, same size).
+cudaError_t launch_near_cells(const DevScene& sc, uint32_t* occ, uint32_t* near_bits, cudaStream_t s);
 
 // Argmin of J = J_o + J_r (ties to the lowest id / index).
 struct BestArgs {

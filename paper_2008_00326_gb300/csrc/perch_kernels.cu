@@ -11,6 +11,8 @@
 // so no multiply-add is contracted.  Edge functions are exact int32.
 #include "perch_internal.cuh"
 
+#include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -261,6 +263,82 @@ __global__ void k_compact_table(const uint4* big, uint32_t cap_big, uint4* small
         h = (h + 1) & mask;
     }
     atomicOr(err, kErrHashFull);
+}
+
+// ---- near-cell bitmap: lets a query whose 27 neighbour cells are all empty
+// skip the hash lookups (exact: such a query has no candidate at all)
+
+__global__ void k_cell_bounds(DevScene sc, int* bounds)
+{
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sc.n_pts; i += gridDim.x * blockDim.x) {
+        const float4 p = sc.pts[i];
+        const int c[3] = {cell_coord(p.x, sc.cell), cell_coord(p.y, sc.cell), cell_coord(p.z, sc.cell)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { lo[a] = min(lo[a], c[a]); hi[a] = max(hi[a], c[a]); }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { atomicMin(&bounds[a], lo[a]); atomicMax(&bounds[3 + a], hi[a]); }
+    }
+}
+
+__device__ __forceinline__ long long near_index(const DevScene& sc, int x, int y, int z)
+{
+    const int ix = x - sc.near_lo[0], iy = y - sc.near_lo[1], iz = z - sc.near_lo[2];
+    if (ix < 0 || iy < 0 || iz < 0 || ix >= sc.near_n[0] || iy >= sc.near_n[1] || iz >= sc.near_n[2]) return -1;
+    return ((long long)iz * sc.near_n[1] + iy) * sc.near_n[0] + ix;
+}
+
+__global__ void k_cell_occupancy(DevScene sc, uint32_t* occ)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sc.n_pts; i += gridDim.x * blockDim.x) {
+        const float4 p = sc.pts[i];
+        const long long b = near_index(sc, cell_coord(p.x, sc.cell), cell_coord(p.y, sc.cell),
+                                       cell_coord(p.z, sc.cell));
+        if (b >= 0) atomicOr(&occ[b >> 5], 1u << (b & 31));
+    }
+}
+
+__global__ void k_cell_dilate(DevScene sc, const uint32_t* occ, uint32_t* near_bits)
+{
+    const long long n = (long long)sc.near_n[0] * sc.near_n[1] * sc.near_n[2];
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < n;
+         b += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(b % sc.near_n[0]) + sc.near_lo[0];
+        const int y = (int)((b / sc.near_n[0]) % sc.near_n[1]) + sc.near_lo[1];
+        const int z = (int)(b / ((long long)sc.near_n[0] * sc.near_n[1])) + sc.near_lo[2];
+        bool any = false;
+        for (int k = 0; k < 27 && !any; ++k) {
+            const long long q = near_index(sc, x + k % 3 - 1, y + (k / 3) % 3 - 1, z + k / 9 - 1);
+            any = q >= 0 && ((occ[q >> 5] >> (q & 31)) & 1u);
+        }
+        if (any) atomicOr(&near_bits[b >> 5], 1u << (b & 31));
+    }
+}
+
+cudaError_t launch_cell_bounds(const DevScene& sc, int* bounds, cudaStream_t s)
+{
+    if (sc.n_pts <= 0) return cudaSuccess;
+    k_cell_bounds<<<min(1024, (sc.n_pts + 255) / 256), 256, 0, s>>>(sc, bounds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_cells(const DevScene& sc, uint32_t* occ, uint32_t* near_bits, cudaStream_t s)
+{
+    if (sc.n_pts <= 0) return cudaSuccess;
+    k_cell_occupancy<<<min(1024, (sc.n_pts + 255) / 256), 256, 0, s>>>(sc, occ);
+    const long long n = (long long)sc.near_n[0] * sc.near_n[1] * sc.near_n[2];
+    k_cell_dilate<<<(unsigned)std::min<long long>(4096, (n + 255) / 256), 256, 0, s>>>(sc, occ, near_bits);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_compact_table(const uint4* big, uint32_t cap_big, uint4* small, uint32_t cap_small,
@@ -582,7 +660,12 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
         cx = cell_coord(qx, sc.cell);
         cy = cell_coord(qy, sc.cell);
         cz = cell_coord(qz, sc.cell);
-        key = cell_key(cx, cy, cz);
+        if (sc.near_bits) {
+            // no observed point in the 27 cells: nothing to look up
+            const long long b = near_index(sc, cx, cy, cz);
+            valid = b >= 0 && ((__ldg(&sc.near_bits[b >> 5]) >> (b & 31)) & 1u);
+        }
+        if (valid) key = cell_key(cx, cy, cz);
     }
     W.q[lane] = make_float4(qx, qy, qz, 0.0f);
     W.best[lane] = kEmptyKey;

@@ -211,10 +211,12 @@ PERCH_API perch_status perch_set_launch_config(perch_ctx *ctx, int32_t threads, 
                                                int32_t mark_bits);
 
 /* ---- batched form ----------------------------------------------------------
- * Hypotheses of many (scene, mesh) searches scored by ONE persistent launch:
- * every block of the scoring kernel takes the next hypothesis of the whole
- * list from a device counter, so searches of very different sizes (objects,
- * ROIs, hypothesis counts) share the GPU without per-search launches.  Each
+ * Hypotheses of many (scene, mesh) searches scored by ONE call: each item gets
+ * a persistent launch of the whole resident grid with its scene and mesh in
+ * the kernel parameters, and the launches are dealt round-robin over four
+ * side streams, so the blocks of item j+1 start on the SMs that item j's
+ * blocks leave at its tail -- searches of very different sizes (objects,
+ * ROIs, hypothesis counts) share the GPU without a per-search tail.  Each
  * item is what perch_score_hypotheses takes (Sec. IV-A "Parallel Search":
  * every object of every scene is searched independently). */
 typedef struct perch_work_item {
@@ -235,10 +237,10 @@ PERCH_API perch_status perch_score_batch(perch_ctx *ctx, const perch_work_item *
                                          const float *poses, int32_t *costs, void *cuda_stream);
 
 /* A batch built once as a CUDA graph and replayed: one counter-reset node and
- * one persistent single-item scoring kernel per item, all independent, each
- * with a grid proportional to its item's share of the hypotheses, so a single
- * graph launch runs every search concurrently (items read their scene and
- * mesh from the kernel parameters, the fastest path).  The item list, the
+ * one persistent scoring kernel node per item with the whole resident grid,
+ * node j depending on node j - 4 (the side-stream round robin of
+ * perch_score_batch as a graph), so a single graph launch runs every search
+ * (items read their scene and mesh from the kernel parameters).  The item list, the
  * device pose/cost arrays and the launch shape are fixed at creation; the
  * caller refills the pose array between replays.  The graph owns its scratch,
  * so replays of one graph must be ordered (one stream), while different graphs

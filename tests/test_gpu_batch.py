@@ -1,4 +1,4 @@
-"""Batched form: one persistent launch over many scenes' searches.
+"""Batched form: many scenes' searches in one call or one replayed graph.
 
 Every item's costs must be identical whether it is scored alone
 (perch_score_hypotheses) or inside a batch with other scenes, meshes, label

@@ -70,6 +70,22 @@ def measured_traffic():
         return None
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's time (MAX all-reduce); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Weak scaling: every rank processes its own copy of the units; the job's
+    rate is all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,12 +566,8 @@ def main():
                 s1.record(stream)
                 stream.synchronize()
                 score_ms.append((k, s0.elapsed_time(s1)))
-    ms_step = total_ms / a.steps
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * n_step / (ms_step / 1000.0)
+    ms_step = max_over_ranks(total_ms / a.steps, dist, dev)
+    value = whole_job_rate(n_step, world, ms_step)
 
     # ---- e2e through the public API with host buffers (pinned)
     pinned = [torch.from_numpy(r.poses).pin_memory().numpy() for r in reqs]
@@ -576,11 +588,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         step_host()
-    e2e_ms = 1000.0 * (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0) / e2e_steps, dist, dev)
     h2d = sum(p.nbytes for p in pinned) + sum(c.nbytes for c in host_costs)
     d2h = sum(c.nbytes for c in host_costs) + len(reqs) * 12
 
@@ -648,7 +656,7 @@ def main():
                    "launch": {"threads": 256, "zbuf_words": 8192, "mark_bits": 65536}},
         "latency_ms": {"search_p50": lat[len(lat) // 2], "search_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "what": f"one object's {len(reqs[0].poses):,}-hypothesis search (score + argmin), device-timed"},
-        "e2e": {"value": world * n_step / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(n_step, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": a.steps * 2 * len(reqs),
         "clocks": clk,

@@ -232,7 +232,7 @@ typedef struct perch_work_item {
  * hypothesis; item i uses entries [pose_offset, pose_offset + n).  Items may
  * not overlap.  cuda_stream NULL: HOST pointers, synchronous; otherwise DEVICE
  * pointers enqueued on that stream.  items is a host array, copied by the call.
- * The total number of hypotheses must stay below 2^32. */
+ * Each item must hold fewer than 2^32 hypotheses. */
 PERCH_API perch_status perch_score_batch(perch_ctx *ctx, const perch_work_item *items, int32_t n_items,
                                          const float *poses, int32_t *costs, void *cuda_stream);
 

@@ -270,7 +270,9 @@ PERCH_API perch_status perch_autotune(perch_ctx *ctx, const perch_work_item *ite
  * scheduler thread packs the queued requests into launches of the batched
  * scorer whenever one of `slots` launch slots is free, so requests that
  * arrive while others are on the GPU join the next launch and launches overlap
- * on the device (each slot has its own scratch and stream).  Scenes and meshes
+ * on the device (each slot has its own scratch and stream).  Within a slot the
+ * requests run smallest first and each one completes (its costs copied back,
+ * its ticket done) as soon as its own scoring is finished.  Scenes and meshes
  * stay resident in the context; each slot's device staging for
  * max_batch_hypotheses poses and costs is allocated at start-up and charged
  * to the context's HBM budget, so admission is bounded by that budget.

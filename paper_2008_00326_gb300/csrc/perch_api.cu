@@ -13,6 +13,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -309,9 +310,14 @@ perch_status make_job(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t l
 // several jobs the launches go round-robin over X's side streams, so the
 // blocks of job j+1 start on the SMs that job j's blocks leave at its tail,
 // and every job keeps its fields in the parameter bank.
+// after_job (optional) is called right after job j's launch with the stream
+// it went to, to enqueue work that needs only that job (the server's
+// per-request read-back).
+using AfterJob = std::function<cudaError_t(size_t, cudaStream_t)>;
+
 perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Job>& jobs,
                       int mark_words, const perch::ScoreConfig& cfg_in, cudaStream_t st,
-                      unsigned long long* dump)
+                      unsigned long long* dump, const AfterJob* after_job = nullptr)
 {
     long long total = 0;
     int max_verts = 0;
@@ -378,7 +384,9 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
         a.job = jobs[j];
         a.n = jobs[j].n;
         a.next = X.next + j;
-        e = perch::launch_score(a, cfg, grid, fan ? X.side[j % kSideStreams] : st);
+        cudaStream_t js = fan ? X.side[j % kSideStreams] : st;
+        e = perch::launch_score(a, cfg, grid, js);
+        if (!e && after_job) e = (*after_job)(j, js);
     }
     for (int k = 0; k < nside && fan && !e; ++k) {
         e = cudaEventRecord(X.join[k], X.side[k]);
@@ -1592,6 +1600,7 @@ struct Slot {
     int32_t* h_costs = nullptr;     // pinned
     std::vector<std::shared_ptr<ServedRequest>> reqs;
     std::vector<int64_t> offsets;
+    std::vector<cudaEvent_t> req_done;  // per request: its costs are in h_costs
     bool busy = false;
 };
 
@@ -1643,12 +1652,28 @@ void serve_schedule(perch_server* S)
             auto r = S->pending.front();
             S->pending.pop_front();
             S->pending_hyps -= r->n;
-            slot.offsets.push_back(total);
             slot.reqs.push_back(r);
             total += r->n;
         }
+        // smallest requests first: each completes as soon as its own launch
+        // and read-back are done, so short ones do not wait for long ones
+        std::stable_sort(slot.reqs.begin(), slot.reqs.end(),
+                         [](const std::shared_ptr<ServedRequest>& x, const std::shared_ptr<ServedRequest>& y) {
+                             return x->n < y->n;
+                         });
+        for (size_t k = 0, off = 0; k < slot.reqs.size(); off += slot.reqs[k]->n, ++k) slot.offsets.push_back(off);
         slot.busy = true;
         lk.unlock();
+        perch_status st = PERCH_OK;
+        while (slot.req_done.size() < slot.reqs.size()) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                st = PERCH_E_CUDA;
+                break;
+            }
+            slot.req_done.push_back(ev);
+        }
 
         std::vector<perch::Job> jobs;
         int mw = 0;
@@ -1662,16 +1687,19 @@ void serve_schedule(perch_server* S)
             jobs.push_back(J);
             mw = std::max(mw, r->mark_words);
         }
-        perch_status st = PERCH_OK;
-        cudaError_t e = cudaMemcpyAsync(slot.d_poses, slot.h_poses, total * 48, cudaMemcpyHostToDevice, slot.stream);
+        cudaError_t e = cudaSuccess;
+        if (st == PERCH_OK) e = cudaMemcpyAsync(slot.d_poses, slot.h_poses, total * 48, cudaMemcpyHostToDevice, slot.stream);
         if (e) st = PERCH_E_CUDA;
         if (st == PERCH_OK) {
+            const AfterJob readback = [&](size_t j, cudaStream_t js) {
+                const int64_t off = slot.offsets[j], n = slot.reqs[j]->n;
+                cudaError_t r = cudaMemcpyAsync(slot.h_costs + 2 * off, slot.d_costs + 2 * off, n * 8,
+                                                cudaMemcpyDeviceToHost, js);
+                return r ? r : cudaEventRecord(slot.req_done[j], js);
+            };
             std::lock_guard<std::mutex> g(S->ctx_mu);
-            st = run_jobs(S->c, slot.X, jobs, mw, S->c->cfg, slot.stream, nullptr);
+            st = run_jobs(S->c, slot.X, jobs, mw, S->c->cfg, slot.stream, nullptr, &readback);
         }
-        if (st == PERCH_OK)
-            e = cudaMemcpyAsync(slot.h_costs, slot.d_costs, total * 8, cudaMemcpyDeviceToHost, slot.stream);
-        if (st == PERCH_OK && e) st = PERCH_E_CUDA;
         cudaEventRecord(slot.done, slot.stream);
         if (st != PERCH_OK)
             for (auto& r : slot.reqs) r->status = st;
@@ -1695,21 +1723,22 @@ void serve_complete(perch_server* S)
         const int si = S->in_flight.front();
         lk.unlock();
         Slot& slot = S->slots[si];
-        cudaError_t e = cudaEventSynchronize(slot.done);
-        const int64_t t = now_ns();
+        // requests in launch order, each as soon as its own read-back is done
         for (size_t k = 0; k < slot.reqs.size(); ++k) {
             auto& r = slot.reqs[k];
+            cudaError_t e = r->status == PERCH_OK ? cudaEventSynchronize(slot.req_done[k]) : cudaSuccess;
             if (e != cudaSuccess && r->status == PERCH_OK) r->status = PERCH_E_CUDA;
             if (r->status == PERCH_OK)
                 std::memcpy(r->user_costs, slot.h_costs + 2 * slot.offsets[k], r->n * 2 * sizeof(int32_t));
-            r->t_done = t;
-        }
-        lk.lock();
-        for (auto& r : slot.reqs) {
+            r->t_done = now_ns();
+            std::lock_guard<std::mutex> g(S->mu);
             r->done = true;
             r->poses.clear();
             r->poses.shrink_to_fit();
+            S->cv_wait.notify_all();
         }
+        cudaEventSynchronize(slot.done);
+        lk.lock();
         slot.reqs.clear();
         slot.busy = false;
         S->in_flight.pop_front();
@@ -1760,6 +1789,7 @@ perch_status perch_server_start(perch_ctx* c, const perch_server_config* cfg, pe
             if (slot.h_costs) cudaFreeHost(slot.h_costs);
             if (slot.stream) cudaStreamDestroy(slot.stream);
             if (slot.done) cudaEventDestroy(slot.done);
+            for (auto ev : slot.req_done) cudaEventDestroy(ev);
         }
         delete S;
         return st;
@@ -1856,6 +1886,7 @@ perch_status perch_server_stop(perch_server* S)
         if (slot.h_costs) cudaFreeHost(slot.h_costs);
         if (slot.stream) cudaStreamDestroy(slot.stream);
         if (slot.done) cudaEventDestroy(slot.done);
+        for (auto ev : slot.req_done) cudaEventDestroy(ev);
     }
     delete S;
     return PERCH_OK;

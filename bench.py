@@ -420,7 +420,8 @@ def served_leg(P, dev, seed=9):
     server.  Latency = submission (arrival) to results.  Two mixes: all three
     workloads (large searches), and the two small ones only."""
     from paper_2008_00326_gb300 import scenes
-    ctx = P.Context(dev.index or 0)
+    budget = 40 << 30          # admission: every device allocation is charged to a 40 GiB budget
+    ctx = P.Context(dev.index or 0, hbm_budget_bytes=budget)
     kinds = []
     for sc in (scenes.tabletop_small(), scenes.tabletop_3obj(), scenes.sixdof_5obj()):
         sid = ctx.set_observation(sc)
@@ -428,8 +429,10 @@ def served_leg(P, dev, seed=9):
         kinds.append([(sid, mids[r.mesh_index], r.label, r.roi, r.poses) for r in sc.requests])
     mixed = _served_rates(P, ctx, kinds, (5, 20, 50, 100, 200), 120, seed)
     small = _served_rates(P, ctx, [kinds[0], kinds[2]], (50, 200, 500, 1000), 300, seed + 1)
+    resident = ctx.hbm_used
     ctx.close()
-    return {"server": {"slots": 2, "max_batch_hypotheses": 1 << 16},
+    return {"server": {"slots": 2, "max_batch_hypotheses": 1 << 16, "hbm_budget_bytes": budget,
+                       "hbm_resident_bytes": resident},
             "mixed": {"mix": "uniform over tabletop_small (968 hyp), one tabletop_3obj object "
                              "(29,584 hyp), one sixdof_5obj object (4,096 hyp); scenes resident",
                       "rates": mixed},

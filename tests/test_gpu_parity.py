@@ -100,6 +100,20 @@ def test_small_colour_on_band(ctx, oracle):
     assert ctx.best(got) == oracle.best(want)
 
 
+@pytest.mark.parametrize("delta", [0.0005, 0.03])
+def test_cell_bitmap_on_and_off(ctx, oracle, delta):
+    """delta 0.5 mm: the observed cloud spans more than 2^27 hash cells, so the
+    near-cell filter is off; 3 cm: few, large cells.  Both bit-exact."""
+    sc = scenes.tabletop_small(seed=21)
+    sc.params.delta_m = delta
+    sid, mids = _load(ctx, sc)
+    req = sc.requests[0]
+    poses = req.poses[::24]
+    got = ctx.score(sid, mids[0], req.label, req.roi, poses)
+    want, _ = oracle.score(*_oracle(oracle, sc, req), poses, label=req.label, roi=req.roi)
+    assert np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("threads,zbuf_words,mark_bits",
                          [(256, 8192, 0), (128, 1024, 1024), (512, 2048, 2048), (256, 16384, 0)])
 def test_three_objects_reduced(ctx, oracle, threads, zbuf_words, mark_bits):

@@ -530,6 +530,7 @@ struct __align__(16) WarpProbe {
     float4 q[32];                 // query of each lane
     unsigned long long best[32];  // nearest-neighbour key of each lane's query
     uint4 cache[kCellCache];      // recent cell lookups: (key lo, key hi, start, count)
+    float4 stage[64];             // a chunk of the group's candidates, shared by its queries
 };
 
 // Per-warp scratch: the radius search and the rasteriser's triangle stage
@@ -606,10 +607,12 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
 // Radius search for up to 32 queued points (one per lane; `valid` marks the
 // lanes holding one).  Lanes whose points fall in the same hash cell form a
 // group (__match_any_sync); each group's 27-cell neighbourhood is looked up
-// once, cooperatively.  The group's candidates are then tested by all 32
-// lanes: floor(32 / G) lanes per query (G = the group's queries) split the
-// candidate list, each keeps its minimum (d2 bits, pixel) in a register and
-// folds it into the query's result with one shared-memory atomicMin.  Returns the
+// once, cooperatively.  The group's candidates are then staged in shared
+// memory 64 at a time (two coalesced loads per lane, each candidate loaded
+// once however many of the group's queries test it) and tested by all 32
+// lanes: floor(32 / G) lanes per query (G = the group's queries) split each
+// chunk, each keeps its minimum (d2 bits, pixel) in a register and folds it
+// into the query's result with one shared-memory atomicMin.  Returns the
 // lane's own result: the nearest observed point within delta (smallest FP32
 // squared distance, ties to the lowest pixel index) or kEmptyKey.  All 32
 // lanes must call it.
@@ -620,19 +623,17 @@ struct MarkBand {
     int u0, u1, v0, v1, vw;
 };
 
-// Candidates j, j + k, ... of a group's runs against query q: the minimum
-// (d2 bits << 32 | pixel) within delta, or kEmptyKey.  MARK (jo_mode 1) also
-// marks every observed point within delta that lies in the admissible band.
+// Candidates j, j + k, ... of a staged chunk of n against query q, folded
+// into local: the minimum (d2 bits << 32 | pixel) within delta, or kEmptyKey.
+// MARK (jo_mode 1) also marks every observed point within delta that lies in
+// the admissible band.
 template <bool MARK>
-__device__ __forceinline__ unsigned long long scan_candidates(const DevScene& sc, const float4 q,
-                                                              const int2* runs, int T, int j, int k,
-                                                              const MarkBand& mb)
+__device__ __forceinline__ unsigned long long scan_staged(const DevScene& sc, const float4 q, const float4* stage,
+                                                          int n, int j, int k, const MarkBand& mb,
+                                                          unsigned long long local)
 {
-    unsigned long long local = kEmptyKey;
-    int r = 0;
-    for (int ci = j; ci < T; ci += k) {
-        while (runs[r].y <= ci) ++r;
-        const float4 c = __ldg(&sc.pts[runs[r].x + ci]);
+    for (int i = j; i < n; i += k) {
+        const float4 c = stage[i];
         float ex = __fsub_rn(q.x, c.x), ey = __fsub_rn(q.y, c.y), ez = __fsub_rn(q.z, c.z);
         float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
         if (d2 <= sc.delta2) {
@@ -699,16 +700,33 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
             const int T = W.total[g];
             if (T == 0) continue;
             // k = floor(32 / G) lanes per query; lane j of a query takes
-            // candidates j, j + k, ... and keeps its minimum in a register
+            // candidates j, j + k, ... of each staged chunk and keeps its
+            // minimum in a register
             const int G = __popc(W.mask[g]);
             const int k = 32 / G;
-            if (lane < G * k) {
-                const int ql = W.qlist[g][lane / k];
-                const unsigned long long local =
-                    sc.jo_mode == 1 ? scan_candidates<true>(sc, W.q[ql], W.runs[g], T, lane % k, k, mb)
-                                    : scan_candidates<false>(sc, W.q[ql], W.runs[g], T, lane % k, k, mb);
-                if (local != kEmptyKey) atomicMin(&W.best[ql], local);
+            const bool active = lane < G * k;
+            const int ql = active ? W.qlist[g][lane / k] : 0;
+            const float4 q = W.q[ql];
+            unsigned long long local = kEmptyKey;
+            int r = 0;
+            for (int c0 = 0; c0 < T; c0 += 64) {
+                const int ci = c0 + lane, cj = ci + 32;
+                if (ci < T) {
+                    while (W.runs[g][r].y <= ci) ++r;
+                    W.stage[lane] = __ldg(&sc.pts[W.runs[g][r].x + ci]);
+                }
+                if (cj < T) {
+                    while (W.runs[g][r].y <= cj) ++r;
+                    W.stage[lane + 32] = __ldg(&sc.pts[W.runs[g][r].x + cj]);
+                }
+                __syncwarp();
+                const int n = min(64, T - c0);
+                if (active)
+                    local = sc.jo_mode == 1 ? scan_staged<true>(sc, q, W.stage, n, lane % k, k, mb, local)
+                                            : scan_staged<false>(sc, q, W.stage, n, lane % k, k, mb, local);
+                __syncwarp();
             }
+            if (active && local != kEmptyKey) atomicMin(&W.best[ql], local);
         }
         __syncwarp();
     }

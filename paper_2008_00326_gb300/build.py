@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libperch.so")
 BUILD_DIR = os.path.join(PKG, "_build")
-SOURCES = ["perch_api.cu", "perch_kernels.cu", "perch_noalloc.cu", "perch_microbench.cu", "perch_metrics.cu"]
+SOURCES = ["perch_api.cu", "perch_batch.cu", "perch_serve.cu", "perch_refine.cu", "perch_tree.cu", "perch_kernels.cu",
+           "perch_noalloc.cu", "perch_microbench.cu", "perch_metrics.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
               "-Xcompiler", "-fPIC,-fvisibility=hidden", "--expt-relaxed-constexpr"]

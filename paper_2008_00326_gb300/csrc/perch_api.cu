@@ -1,120 +1,23 @@
-// libperch host side: the C ABI declared in include/perch.h.
+// libperch host side: contexts, resident meshes and observations, scoring,
+// argmin, proposals, pose errors and the debug views of the C ABI declared in
+// include/perch.h (batched form: perch_batch.cu; served form: perch_serve.cu;
+// refinement: perch_refine.cu; tree search: perch_tree.cu).
 //
 // A context owns every device allocation it makes and charges each to its HBM
 // budget.  Meshes and observations are copied once and stay resident; scoring
 // calls launch the fused kernel (perch_kernels.cu) on the caller's stream or,
 // in synchronous mode, on the context's own stream with staging copies.
-#include "perch.h"
-#include "perch_internal.cuh"
+#include "perch_host.cuh"
 
 #include <algorithm>
-#include <chrono>
 #include <climits>
 #include <cmath>
-#include <condition_variable>
-#include <deque>
-#include <functional>
-#include <memory>
-#include <mutex>
-#include <thread>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <map>
-#include <string>
-#include <unordered_map>
-#include <vector>
 
-namespace {
+namespace perch_host {
 
-struct MeshRec {
-    perch::DevMesh dm{};
-    void* verts = nullptr;
-    void* tris = nullptr;
-};
-
-struct SceneRec {
-    perch::DevScene ds{};
-    perch_params params{};
-    void* depth = nullptr;
-    void* labels = nullptr;
-    void* lab = nullptr;
-    void* pts = nullptr;
-    void* table = nullptr;
-    void* nrm = nullptr;           // observed normals (GICP targets), made on first use
-    int nrm_jump = -1;             // the normal_max_jump_units they were made with
-    void* near = nullptr;          // near-cell bitmap (DevScene::near_bits)
-};
-
-// Everything one chain of scoring launches needs besides its inputs: one
-// hypothesis counter per job followed by the vertex-cache slot mask (zeroed
-// together before each run), the vertex-cache pool, and the side streams a
-// multi-job run spreads its launches over.  Runs that share a ScoreScratch
-// are ordered on the GPU through `last`.
-constexpr int kSideStreams = 4;
-
-struct ScoreScratch {
-    unsigned* next = nullptr;      // device: counters, then slot mask
-    size_t next_words = 0;
-    void* vcache = nullptr;
-    size_t vcache_bytes = 0;
-    void* src = nullptr;           // GICP source clouds, one slot per resident block
-    size_t src_bytes = 0;
-    cudaStream_t side[kSideStreams] = {};
-    cudaEvent_t fork = nullptr;
-    cudaEvent_t join[kSideStreams] = {};
-    cudaEvent_t last = nullptr;
-};
-
-class DeviceGuard {
-public:
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
-        if (prev_ != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        if (prev_ >= 0) cudaSetDevice(prev_);
-    }
-
-private:
-    int prev_ = -1;
-};
-
-}  // namespace
-
-struct perch_ctx {
-    int device = 0;
-    uint64_t budget = 0;
-    uint64_t used = 0;
-    std::unordered_map<void*, size_t> allocs;
-    std::map<int32_t, MeshRec> meshes;
-    std::map<int32_t, SceneRec> scenes;
-    int32_t next_id = 1;
-    std::string err;
-    cudaStream_t stream = nullptr;
-    void* stage = nullptr;
-    size_t stage_bytes = 0;
-    int* d_err = nullptr;
-    unsigned long long* d_best_partial = nullptr;   // 3 words per block, 1024 blocks
-    unsigned* d_best_ticket = nullptr;
-    long long* d_best_index = nullptr;
-    int32_t* d_best_cost = nullptr;
-    ScoreScratch plain;                    // scratch of the context's own scoring launches
-    std::map<uint64_t, perch::ScoreConfig> tuned;   // autotuner results by batch class
-    perch::ScoreConfig cfg{256, 8192, 1 << 16};
-};
-
-struct perch_batch_graph {
-    perch_ctx* ctx = nullptr;
-    unsigned* next = nullptr;              // the graph's own counters and slot mask
-    void* vcache = nullptr;                // and vertex-cache pool
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-
-namespace {
 
 perch_status fail(perch_ctx* c, perch_status st, const char* fmt, ...)
 {
@@ -176,7 +79,6 @@ perch_status ensure_stage(perch_ctx* c, size_t bytes)
     return st;
 }
 
-// Read and clear the device error word (synchronous).
 perch_status check_device_error(perch_ctx* c)
 {
     int h = 0;
@@ -217,12 +119,6 @@ perch_status clip_roi(perch_ctx* c, const SceneRec& s, const int32_t* roi, int o
     return PERCH_OK;
 }
 
-// Capacity of the shared-memory bitset that marks nearest neighbours inside
-// the admissible box.  Boxes larger than this are processed in row bands (each
-// band repeats the render and search), so the capacity only trades shared
-// memory against that rare repetition.  At least one image row always fits.
-constexpr int kMarkBitsDefault = 1 << 16;
-
 int mark_words_for(const SceneRec& s, int label, const int roi[4], int cap_bits)
 {
     long long bits = label >= 0 ? (long long)(roi[2] - roi[0]) * (roi[3] - roi[1])
@@ -232,9 +128,8 @@ int mark_words_for(const SceneRec& s, int label, const int roi[4], int cap_bits)
     return (int)(((bits + 31) / 32 + 2) & ~1ll);   // even: keeps the later 8-byte arrays aligned
 }
 
-// Fit the z-buffer into the opt-in shared memory limit of the device.
 // Shrink the z-buffer of *cfg (the caller's launch shape) until the block's
-// shared memory fits the device.
+// shared memory fits the device's opt-in limit.
 perch_status fit_config(perch_ctx* c, int mark_words, perch::ScoreConfig* cfg)
 {
     int max_optin = 0;
@@ -276,7 +171,6 @@ void scratch_free(perch_ctx* c, ScoreScratch& X)
     X = ScoreScratch{};
 }
 
-// Build the device description of one work item.
 perch_status make_job(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t label,
                       const int32_t* roi, const float* poses, int32_t* costs, long long n,
                       perch::Job* J, int* mark_words, const SceneRec** scene, const MeshRec** mesh)
@@ -313,11 +207,9 @@ perch_status make_job(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t l
 // after_job (optional) is called right after job j's launch with the stream
 // it went to, to enqueue work that needs only that job (the server's
 // per-request read-back).
-using AfterJob = std::function<cudaError_t(size_t, cudaStream_t)>;
-
 perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Job>& jobs,
                       int mark_words, const perch::ScoreConfig& cfg_in, cudaStream_t st,
-                      unsigned long long* dump, const AfterJob* after_job = nullptr)
+                      unsigned long long* dump, const AfterJob* after_job)
 {
     long long total = 0;
     int max_verts = 0;
@@ -397,6 +289,12 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
     return PERCH_OK;
 }
 
+}  // namespace perch_host
+
+using namespace perch_host;
+
+namespace {
+
 // Near-cell bitmap of an observation: one bit per hash cell of the observed
 // points' cell box grown by one, set iff one of the cell's 27 neighbours holds
 // a point.  Skipped (no filter) when the box exceeds 2^27 cells.
@@ -434,85 +332,6 @@ perch_status build_near_cells(perch_ctx* c, SceneRec& s)
     dfree(c, occ);
     if (e) return cuda_fail(c, e, "near-cell bitmap");
     d.near_bits = (const uint32_t*)s.near;
-    return PERCH_OK;
-}
-
-// Grow a scratch buffer of X (after every earlier run that used X).
-perch_status grow(perch_ctx* c, ScoreScratch& X, void** buf, size_t* have, size_t need)
-{
-    if (need <= *have) return PERCH_OK;
-    cudaEventSynchronize(X.last);
-    dfree(c, *buf);
-    *buf = nullptr;
-    *have = 0;
-    perch_status st = dalloc(c, need, buf);
-    if (st == PERCH_OK) *have = need;
-    return st;
-}
-
-// Launch the GICP refinement of one job on stream st, after every earlier run
-// that used X (they share the counter, the slot pool and the caches).
-perch_status run_gicp(perch_ctx* c, ScoreScratch& X, const perch::Job& J, const perch_gicp_params& gp,
-                      const float4* nrm, float* poses_out, int32_t* info, cudaStream_t st)
-{
-    if (J.n == 0) return PERCH_OK;
-    if (J.n > 0xFFFFFFF0ll) return fail(c, PERCH_E_INVALID, "more than 2^32 hypotheses in one call");
-    int dev = 0, max_optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int zcap = c->cfg.zcap_words;
-    while (perch::gicp_smem_bytes(zcap) > (size_t)max_optin && zcap > 1024) zcap /= 2;
-    const int grid = perch::gicp_grid(zcap);
-    if (grid <= 0) {
-        cudaGetLastError();
-        return fail(c, PERCH_E_CUDA, "refinement kernel does not fit on the device");
-    }
-    const long long s = J.sc.stride;
-    const long long lattice = ((J.roi[2] - J.roi[0] + s - 1) / s) * ((J.roi[3] - J.roi[1] + s - 1) / s);
-    long long cap = gp.max_source_points > 0 ? gp.max_source_points : 65536;
-    cap = std::max(1ll, std::min(cap, lattice));
-    perch_status stt = grow(c, X, &X.src, &X.src_bytes, (size_t)grid * (size_t)cap * 2 * sizeof(float4));
-    if (stt != PERCH_OK) return stt;
-    long long vstride = 0;
-    if (J.sc.W <= 1023 && J.sc.H <= 1023) {
-        vstride = ((long long)J.m.n_verts + 31) / 32 * 32;
-        stt = grow(c, X, &X.vcache, &X.vcache_bytes, (size_t)grid * vstride * sizeof(unsigned long long));
-        if (stt != PERCH_OK) return stt;
-    }
-    const size_t words = 1 + ((size_t)grid + 31) / 32;
-    if (words > X.next_words) {
-        size_t have = X.next_words * sizeof(unsigned);
-        void* p = X.next;
-        stt = grow(c, X, &p, &have, std::max<size_t>(words, 64) * sizeof(unsigned));
-        X.next = (unsigned*)p;
-        X.next_words = have / sizeof(unsigned);
-        if (stt != PERCH_OK) return stt;
-    }
-    perch::GicpArgs a{};
-    a.job = J;
-    a.n = J.n;
-    a.zcap_words = zcap;
-    a.err = c->d_err;
-    a.next = X.next;
-    a.smask = X.next + 1;
-    a.slots = grid;
-    a.src = (float4*)X.src;
-    a.src_cap = (int)cap;
-    a.vcache = vstride ? (unsigned long long*)X.vcache : nullptr;
-    a.vstride = vstride;
-    a.nrm = nrm;
-    a.max_iters = gp.max_iterations;
-    a.min_corr = gp.min_correspondences;
-    a.epsilon = gp.epsilon;
-    a.stop_rot = gp.stop_rotation_rad;
-    a.stop_trans = gp.stop_translation_m;
-    a.poses_out = poses_out;
-    a.info = info;
-    cudaError_t e = cudaStreamWaitEvent(st, X.last, 0);
-    if (!e) e = cudaMemsetAsync(X.next, 0, words * sizeof(unsigned), st);
-    if (!e) e = perch::launch_gicp(a, grid, st);
-    if (!e) e = cudaEventRecord(X.last, st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "refinement launch");
     return PERCH_OK;
 }
 
@@ -870,72 +689,6 @@ perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh
     return check_device_error(c);
 }
 
-// Validate a batch and turn it into jobs; `base_poses` / `base_costs` are the
-// arrays the item offsets index.
-static perch_status batch_jobs(perch_ctx* c, const perch_work_item* items, int32_t n_items,
-                               const float* base_poses, int32_t* base_costs,
-                               std::vector<perch::Job>* jobs, int* mark_words, long long* total)
-{
-    if (!items || n_items < 0) return fail(c, PERCH_E_INVALID, "bad item list");
-    jobs->clear();
-    *mark_words = 0;
-    *total = 0;
-    std::vector<std::pair<long long, long long>> spans;
-    for (int32_t i = 0; i < n_items; ++i) {
-        const perch_work_item& it = items[i];
-        if (it.n < 0 || it.pose_offset < 0) return fail(c, PERCH_E_INVALID, "item %d: negative n or offset", i);
-        if (it.n == 0) continue;
-        const int32_t* roi = (it.roi[2] > it.roi[0] && it.roi[3] > it.roi[1]) ? it.roi : nullptr;
-        perch::Job J;
-        int mw;
-        perch_status st = make_job(c, it.scene_id, it.mesh_id, it.label, roi, base_poses + 12 * it.pose_offset,
-                                   base_costs + 2 * it.pose_offset, it.n, &J, &mw, nullptr, nullptr);
-        if (st != PERCH_OK) return st;
-        jobs->push_back(J);
-        *mark_words = std::max(*mark_words, mw);
-        *total += it.n;
-        spans.push_back({it.pose_offset, it.pose_offset + it.n});
-    }
-    std::sort(spans.begin(), spans.end());
-    for (size_t i = 1; i < spans.size(); ++i)
-        if (spans[i].first < spans[i - 1].second) return fail(c, PERCH_E_INVALID, "batch items overlap");
-    return PERCH_OK;
-}
-
-perch_status perch_score_batch(perch_ctx* c, const perch_work_item* items, int32_t n_items,
-                               const float* poses, int32_t* costs, void* cuda_stream)
-{
-    if (!c) return PERCH_E_INVALID;
-    c->err.clear();
-    if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
-    DeviceGuard g(c->device);
-    std::vector<perch::Job> jobs;
-    int mw;
-    long long total;
-    long long extent = 0;
-    for (int32_t i = 0; items && i < n_items; ++i) extent = std::max<long long>(extent, items[i].pose_offset + items[i].n);
-    if (cuda_stream) {
-        perch_status st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
-        if (st != PERCH_OK) return st;
-        return run_jobs(c, c->plain, jobs, mw, c->cfg, (cudaStream_t)cuda_stream, nullptr);
-    }
-    perch_status st = ensure_stage(c, (size_t)std::max<long long>(1, extent) * (48 + 8));
-    if (st != PERCH_OK) return st;
-    float* d_poses = (float*)c->stage;
-    int32_t* d_costs = (int32_t*)((char*)c->stage + (size_t)extent * 48);
-    if ((st = batch_jobs(c, items, n_items, d_poses, d_costs, &jobs, &mw, &total)) != PERCH_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(d_poses, poses, extent * 48, cudaMemcpyHostToDevice, c->stream);
-    if (e) return cuda_fail(c, e, "perch_score_batch upload");
-    if ((st = run_jobs(c, c->plain, jobs, mw, c->cfg, c->stream, nullptr)) != PERCH_OK) return st;
-    for (int32_t i = 0; i < n_items && !e; ++i)
-        if (items[i].n > 0)
-            e = cudaMemcpyAsync(costs + 2 * items[i].pose_offset, d_costs + 2 * items[i].pose_offset,
-                                items[i].n * 8, cudaMemcpyDeviceToHost, c->stream);
-    if (!e) e = cudaStreamSynchronize(c->stream);
-    if (e) return cuda_fail(c, e, "perch_score_batch");
-    return check_device_error(c);
-}
-
 perch_status perch_best(perch_ctx* c, const int32_t* costs, const uint64_t* ids, int64_t n,
                         int64_t* best_index, int32_t* best_cost, void* cuda_stream)
 {
@@ -1037,266 +790,6 @@ perch_status perch_pose_proposals(perch_ctx* c, int32_t scene_id, int32_t mesh_i
     return e ? cuda_fail(c, e, "perch_pose_proposals") : PERCH_OK;
 }
 
-perch_status perch_default_gicp_params(perch_gicp_params* p)
-{
-    if (!p) return PERCH_E_INVALID;
-    p->max_iterations = 10;
-    p->epsilon = 1e-3f;
-    p->normal_max_jump_units = 200;
-    p->min_correspondences = 6;
-    p->stop_rotation_rad = 1e-5f;
-    p->stop_translation_m = 1e-5f;
-    p->max_source_points = 0;
-    return PERCH_OK;
-}
-
-perch_status perch_refine_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t label,
-                                     const int32_t* roi, const float* poses, int64_t n,
-                                     const perch_gicp_params* params, float* poses_out, int32_t* info,
-                                     void* cuda_stream)
-{
-    if (!c) return PERCH_E_INVALID;
-    c->err.clear();
-    if (n < 0) return fail(c, PERCH_E_INVALID, "n < 0");
-    if (n == 0) return PERCH_OK;
-    if (!poses || !poses_out || !params) return fail(c, PERCH_E_INVALID, "null poses, poses_out or params");
-    const perch_gicp_params gp = *params;
-    if (gp.max_iterations < 0 || gp.max_iterations > 1000)
-        return fail(c, PERCH_E_INVALID, "max_iterations must be in [0, 1000]");
-    if (!finite(gp.epsilon) || !(gp.epsilon > 0.0f) || !(gp.epsilon < 1.0f))
-        return fail(c, PERCH_E_INVALID, "epsilon must be in (0, 1)");
-    if (gp.normal_max_jump_units < 0 || gp.min_correspondences < 1 || gp.max_source_points < 0)
-        return fail(c, PERCH_E_INVALID, "normal_max_jump_units, min_correspondences or max_source_points out of range");
-    if (!finite(gp.stop_rotation_rad) || !finite(gp.stop_translation_m) || gp.stop_rotation_rad < 0.0f ||
-        gp.stop_translation_m < 0.0f)
-        return fail(c, PERCH_E_INVALID, "stop thresholds must be finite and >= 0");
-    DeviceGuard g(c->device);
-    perch::Job J;
-    int mw;
-    perch_status st = make_job(c, scene_id, mesh_id, label, roi, poses, nullptr, n, &J, &mw, nullptr, nullptr);
-    if (st != PERCH_OK) return st;
-    J.sc.jo_mode = 0;
-    // observed normals of the scene for this jump threshold (made once, synchronously)
-    SceneRec& S = c->scenes[scene_id];
-    if (!S.nrm || S.nrm_jump != gp.normal_max_jump_units) {
-        cudaEventSynchronize(c->plain.last);
-        if (!S.nrm && (st = dalloc(c, (size_t)S.ds.W * S.ds.H * sizeof(float4), &S.nrm)) != PERCH_OK) return st;
-        cudaError_t e = perch::launch_obs_normals(S.ds, gp.normal_max_jump_units, (float4*)S.nrm, c->stream);
-        if (!e) e = cudaStreamSynchronize(c->stream);
-        if (e) return cuda_fail(c, e, "observed normals");
-        S.nrm_jump = gp.normal_max_jump_units;
-    }
-    const float4* nrm = (const float4*)S.nrm;
-    if (cuda_stream) return run_gicp(c, c->plain, J, gp, nrm, poses_out, info, (cudaStream_t)cuda_stream);
-    const long long chunk = 1 << 18;
-    const long long k0 = std::min<long long>(n, chunk);
-    if ((st = ensure_stage(c, (size_t)k0 * (48 + 48 + 8))) != PERCH_OK) return st;
-    float* d_in = (float*)c->stage;
-    float* d_out = (float*)((char*)c->stage + (size_t)k0 * 48);
-    int32_t* d_info = (int32_t*)((char*)c->stage + (size_t)k0 * 96);
-    for (long long off = 0; off < n; off += chunk) {
-        const long long k = std::min(chunk, n - off);
-        cudaError_t e = cudaMemcpyAsync(d_in, poses + 12 * off, k * 48, cudaMemcpyHostToDevice, c->stream);
-        if (e) return cuda_fail(c, e, "perch_refine_hypotheses upload");
-        perch::Job Jk = J;
-        Jk.poses = d_in;
-        Jk.n = k;
-        if ((st = run_gicp(c, c->plain, Jk, gp, nrm, d_out, d_info, c->stream)) != PERCH_OK) return st;
-        e = cudaMemcpyAsync(poses_out + 12 * off, d_out, k * 48, cudaMemcpyDeviceToHost, c->stream);
-        if (!e && info) e = cudaMemcpyAsync(info + 2 * off, d_info, k * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (!e) e = cudaStreamSynchronize(c->stream);
-        if (e) return cuda_fail(c, e, "perch_refine_hypotheses");
-    }
-    return check_device_error(c);
-}
-
-perch_status perch_tree_search(perch_ctx* c, int32_t scene_id, const perch_tree_object* objects, int32_t K,
-                               int32_t beam_width, int32_t* order, int32_t* pose_index, int64_t* level_cost,
-                               int64_t* edges_scored)
-{
-    if (!c) return PERCH_E_INVALID;
-    c->err.clear();
-    if (!objects || !order || !pose_index || !level_cost) return fail(c, PERCH_E_INVALID, "null argument");
-    if (K < 1 || K > 64) return fail(c, PERCH_E_INVALID, "K must be in [1, 64]");
-    if (beam_width < 1 || beam_width > 4096) return fail(c, PERCH_E_INVALID, "beam_width must be in [1, 4096]");
-    auto si = c->scenes.find(scene_id);
-    if (si == c->scenes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown scene %d", scene_id);
-    if (si->second.ds.jo_mode != 0) return fail(c, PERCH_E_INVALID, "the tree search needs jo_mode 0");
-    DeviceGuard g(c->device);
-    const perch::DevScene& ds = si->second.ds;
-    const size_t npx = (size_t)ds.W * ds.H, words = (npx + 31) / 32;
-    // validate the objects and lay their poses out in one device buffer
-    std::vector<long long> off(K + 1, 0);
-    for (int32_t j = 0; j < K; ++j) {
-        if (!objects[j].poses || objects[j].n < 1) return fail(c, PERCH_E_INVALID, "object %d: no poses", j);
-        off[j + 1] = off[j] + objects[j].n;
-    }
-    const long long total = off[K];
-    // scratch: poses, per-level edge costs, 2 x beam state images
-    const size_t state_bytes = npx * sizeof(uint32_t) + 2 * words * sizeof(uint32_t);
-    const size_t cost_cap = (size_t)beam_width * (size_t)total;
-    void *d_poses = nullptr, *d_costs = nullptr, *d_states = nullptr;
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(c->stream);
-        dfree(c, d_poses);
-        dfree(c, d_costs);
-        dfree(c, d_states);
-    };
-    perch_status st = dalloc(c, (size_t)total * 48, &d_poses);
-    if (st == PERCH_OK) st = dalloc(c, (cost_cap + 2) * 8, &d_costs);
-    if (st == PERCH_OK) st = dalloc(c, 2 * (size_t)beam_width * state_bytes, &d_states);
-    if (st != PERCH_OK) {
-        cleanup();
-        return st;
-    }
-    auto slot = [&](int half, int k) { return (char*)d_states + ((size_t)half * beam_width + k) * state_bytes; };
-    cudaError_t e = cudaSuccess;
-    for (int32_t j = 0; j < K && !e; ++j)
-        e = cudaMemcpyAsync((float*)d_poses + 12 * off[j], objects[j].poses, (size_t)objects[j].n * 48,
-                            cudaMemcpyHostToDevice, c->stream);
-    if (!e) e = cudaMemsetAsync(slot(0, 0), 0, state_bytes, c->stream);
-    if (e) {
-        cleanup();
-        return cuda_fail(c, e, "perch_tree_search setup");
-    }
-    struct State {
-        long long g;
-        uint64_t placed;
-        std::vector<int32_t> order, pose;
-        std::vector<int64_t> cost;
-    };
-    std::vector<State> cur(1, State{0, 0, {}, {}, {}});
-    int half = 0;
-    long long edges = 0;
-    std::vector<int32_t> h_costs;
-    auto tree_of = [&](int half_, int k, bool out, int child_k) {
-        perch::TreeState T{};
-        char* base = slot(half_, k);
-        T.depth = (const uint32_t*)base;
-        T.mark = (const uint32_t*)(base + npx * 4);
-        T.vol = (const uint32_t*)(base + npx * 4 + words * 4);
-        if (out) {
-            char* cb = slot(1 - half_, child_k);
-            T.out_depth = (uint32_t*)cb;
-            T.out_mark = (uint32_t*)(cb + npx * 4);
-            T.out_vol = (uint32_t*)(cb + npx * 4 + words * 4);
-        }
-        T.margin = std::max(0, ds.occ_margin);
-        return T;
-    };
-    for (int32_t level = 0; level < K; ++level) {
-        // every remaining object at every pose, from every state of the level
-        std::vector<perch::Job> jobs;
-        std::vector<std::pair<int, int>> who;       // (state rank, object) per job
-        std::vector<long long> coff;
-        long long acc = 0;
-        int mw = 0;
-        for (size_t b = 0; b < cur.size(); ++b)
-            for (int32_t j = 0; j < K; ++j) {
-                if (cur[b].placed >> j & 1) continue;
-                const perch_tree_object& o = objects[j];
-                const int32_t* roi = (o.roi[2] > o.roi[0] && o.roi[3] > o.roi[1]) ? o.roi : nullptr;
-                perch::Job J;
-                int w;
-                st = make_job(c, scene_id, o.mesh_id, o.label, roi, (const float*)d_poses + 12 * off[j],
-                              (int32_t*)d_costs + 2 * acc, o.n, &J, &w, nullptr, nullptr);
-                if (st != PERCH_OK) {
-                    cleanup();
-                    return st;
-                }
-                J.tree = tree_of(half, (int)b, false, 0);
-                jobs.push_back(J);
-                who.push_back({(int)b, j});
-                coff.push_back(acc);
-                mw = std::max(mw, w);
-                acc += o.n;
-            }
-        if ((st = run_jobs(c, c->plain, jobs, mw, c->cfg, c->stream, nullptr)) != PERCH_OK) {
-            cleanup();
-            return st;
-        }
-        h_costs.resize(2 * (size_t)acc);
-        e = cudaMemcpyAsync(h_costs.data(), d_costs, (size_t)acc * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (!e) e = cudaStreamSynchronize(c->stream);
-        if (e) {
-            cleanup();
-            return cuda_fail(c, e, "perch_tree_search costs");
-        }
-        edges += acc;
-        // (path cost, parent rank, object, pose) of every edge not refused
-        struct Cand {
-            long long g;
-            int b, j, h;
-        };
-        std::vector<Cand> cands;
-        for (size_t q = 0; q < jobs.size(); ++q) {
-            const int b = who[q].first, j = who[q].second;
-            for (int32_t h = 0; h < objects[j].n; ++h) {
-                const int32_t jo = h_costs[2 * (coff[q] + h)], jr = h_costs[2 * (coff[q] + h) + 1];
-                if (jo < 0) continue;
-                cands.push_back({cur[b].g + jo + jr, b, j, h});
-            }
-        }
-        if (cands.empty()) {
-            cleanup();
-            return fail(c, PERCH_E_NOTFOUND, "every placement at level %d is refused", level);
-        }
-        const size_t keep = std::min<size_t>(cands.size(), (size_t)beam_width);
-        std::partial_sort(cands.begin(), cands.begin() + keep, cands.end(), [](const Cand& x, const Cand& y) {
-            if (x.g != y.g) return x.g < y.g;
-            if (x.b != y.b) return x.b < y.b;
-            if (x.j != y.j) return x.j < y.j;
-            return x.h < y.h;
-        });
-        // materialise the kept children's state images
-        std::vector<State> nxt;
-        for (size_t k = 0; k < keep && !e; ++k) {
-            const Cand& cd = cands[k];
-            e = cudaMemcpyAsync(slot(1 - half, (int)k), slot(half, cd.b), state_bytes, cudaMemcpyDeviceToDevice,
-                                c->stream);
-            if (e) break;
-            const perch_tree_object& o = objects[cd.j];
-            const int32_t* roi = (o.roi[2] > o.roi[0] && o.roi[3] > o.roi[1]) ? o.roi : nullptr;
-            perch::Job J;
-            int w;
-            st = make_job(c, scene_id, o.mesh_id, o.label, roi, (const float*)d_poses + 12 * (off[cd.j] + cd.h),
-                          (int32_t*)d_costs + 2 * cost_cap, 1, &J, &w, nullptr, nullptr);
-            if (st == PERCH_OK) {
-                J.tree = tree_of(half, cd.b, true, (int)k);
-                std::vector<perch::Job> one(1, J);
-                st = run_jobs(c, c->plain, one, w, c->cfg, c->stream, nullptr);
-            }
-            if (st != PERCH_OK) {
-                cleanup();
-                return st;
-            }
-            State s = cur[cd.b];
-            s.g = cd.g;
-            s.placed |= 1ull << cd.j;
-            s.order.push_back(cd.j);
-            s.pose.push_back(cd.h);
-            s.cost.push_back(cd.g);
-            nxt.push_back(std::move(s));
-        }
-        if (e) {
-            cleanup();
-            return cuda_fail(c, e, "perch_tree_search state");
-        }
-        cur.swap(nxt);
-        half = 1 - half;
-    }
-    st = check_device_error(c);
-    cleanup();
-    if (st != PERCH_OK) return st;
-    for (int32_t l = 0; l < K; ++l) {
-        order[l] = cur[0].order[l];
-        pose_index[l] = cur[0].pose[l];
-        level_cost[l] = cur[0].cost[l];
-    }
-    if (edges_scored) *edges_scored = edges;
-    return PERCH_OK;
-}
-
 perch_status perch_add_s(perch_ctx* c, int32_t mesh_id, const float* poses, const float* poses_true, int64_t n,
                          int32_t symmetric, double* add, void* cuda_stream)
 {
@@ -1372,524 +865,6 @@ perch_status perch_debug_render_keys(perch_ctx* c, int32_t scene_id, int32_t mes
     dfree(c, dump);
     if (st != PERCH_OK) return st;
     return check_device_error(c);
-}
-
-perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items, int32_t n_items,
-                                      const float* poses, int32_t* costs, perch_batch_graph** out)
-{
-    if (!c || !out) return PERCH_E_INVALID;
-    c->err.clear();
-    *out = nullptr;
-    if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
-    DeviceGuard g(c->device);
-    std::vector<perch::Job> jobs;
-    int mw;
-    long long total;
-    perch_status st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
-    if (st != PERCH_OK) return st;
-    if (total == 0) return fail(c, PERCH_E_INVALID, "empty batch");
-    perch::ScoreConfig cfg = c->cfg;
-    if ((st = fit_config(c, mw, &cfg)) != PERCH_OK) return st;
-    const int resident = perch::score_grid(cfg, mw);
-    if (resident <= 0) {
-        cudaGetLastError();
-        return fail(c, PERCH_E_CUDA, "scoring kernel does not fit on the device");
-    }
-    perch_batch_graph* G = new (std::nothrow) perch_batch_graph();
-    if (!G) return fail(c, PERCH_E_NOMEM, "graph handle");
-    G->ctx = c;
-    // One kernel node per item, each with the whole resident grid, its own
-    // counter and the shared vertex-cache pool; node j follows node j - 4,
-    // mirroring the side-stream round robin of the direct launch.
-    const size_t nj = jobs.size();
-    int max_verts = 0;
-    bool small_images = true;
-    for (const auto& j : jobs) {
-        max_verts = std::max(max_verts, j.m.n_verts);
-        small_images = small_images && j.sc.W <= 1023 && j.sc.H <= 1023;
-    }
-    const long long vstride = small_images ? ((long long)max_verts + 31) / 32 * 32 : 0;
-    const size_t words = nj + ((size_t)resident + 31) / 32;
-    void* p = nullptr;
-    if ((st = dalloc(c, words * sizeof(unsigned), &p)) == PERCH_OK) G->next = (unsigned*)p;
-    if (st == PERCH_OK && vstride > 0)
-        st = dalloc(c, (size_t)resident * vstride * sizeof(unsigned long long), &G->vcache);
-    cudaError_t e = cudaSuccess;
-    if (st == PERCH_OK) e = cudaGraphCreate(&G->graph, 0);
-    cudaGraphNode_t reset = nullptr;
-    if (st == PERCH_OK && !e) {
-        cudaMemsetParams mp{};
-        mp.dst = G->next;
-        mp.value = 0;
-        mp.elementSize = 4;
-        mp.width = words;
-        mp.height = 1;
-        mp.pitch = 0;
-        e = cudaGraphAddMemsetNode(&reset, G->graph, nullptr, 0, &mp);
-    }
-    std::vector<cudaGraphNode_t> nodes(nj, nullptr);
-    for (size_t j = 0; j < nj && st == PERCH_OK && !e; ++j) {
-        if (jobs[j].n == 0) {
-            if (j >= 4) nodes[j] = nodes[j - 4];
-            continue;
-        }
-        perch::ScoreArgs a{};
-        a.job = jobs[j];
-        a.n = jobs[j].n;
-        a.zcap_words = cfg.zcap_words;
-        a.mark_words = mw;
-        a.err = c->d_err;
-        a.next = G->next + j;
-        a.vcache = vstride ? (unsigned long long*)G->vcache : nullptr;
-        a.vstride = vstride;
-        a.vmask = G->next + nj;
-        a.vslots = resident;
-        cudaGraphNode_t dep = (j >= 4 && nodes[j - 4]) ? nodes[j - 4] : reset;
-        e = perch::add_score_node(G->graph, &dep, 1, a, cfg, resident, &nodes[j]);
-    }
-    if (st == PERCH_OK && !e) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
-    if (st == PERCH_OK && e) st = cuda_fail(c, e, "perch_batch_graph_create");
-    if (st != PERCH_OK) {
-        perch_batch_graph_destroy(G);
-        return st;
-    }
-    *out = G;
-    return PERCH_OK;
-}
-
-perch_status perch_batch_graph_launch(perch_batch_graph* G, void* cuda_stream)
-{
-    if (!G || !G->exec) return PERCH_E_INVALID;
-    DeviceGuard g(G->ctx->device);
-    cudaError_t e = cudaGraphLaunch(G->exec, (cudaStream_t)cuda_stream);
-    if (e) return cuda_fail(G->ctx, e, "perch_batch_graph_launch");
-    return PERCH_OK;
-}
-
-perch_status perch_batch_graph_destroy(perch_batch_graph* G)
-{
-    if (!G) return PERCH_OK;
-    perch_ctx* c = G->ctx;
-    DeviceGuard g(c->device);
-    cudaDeviceSynchronize();
-    if (G->exec) cudaGraphExecDestroy(G->exec);
-    if (G->graph) cudaGraphDestroy(G->graph);
-    dfree(c, G->next);
-    dfree(c, G->vcache);
-    delete G;
-    return PERCH_OK;
-}
-
-perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t n_items,
-                            const float* poses, int32_t* costs, int32_t* threads, int32_t* zbuf_words)
-{
-    if (!c || !threads || !zbuf_words) return PERCH_E_INVALID;
-    c->err.clear();
-    if (!items || n_items < 1 || !poses || !costs) return fail(c, PERCH_E_INVALID, "empty batch");
-    DeviceGuard g(c->device);
-    // class of the batch: largest ROI area and triangle count, as powers of two
-    long long max_area = 0, max_tris = 0;
-    for (int32_t i = 0; i < n_items; ++i) {
-        auto si = c->scenes.find(items[i].scene_id);
-        auto mi = c->meshes.find(items[i].mesh_id);
-        if (si == c->scenes.end() || mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "item %d", i);
-        long long area = (items[i].roi[2] > items[i].roi[0] && items[i].roi[3] > items[i].roi[1])
-                             ? (long long)(items[i].roi[2] - items[i].roi[0]) * (items[i].roi[3] - items[i].roi[1])
-                             : (long long)si->second.ds.W * si->second.ds.H;
-        max_area = std::max(max_area, area);
-        max_tris = std::max<long long>(max_tris, mi->second.dm.n_tris);
-    }
-    const uint64_t key = ((uint64_t)next_pow2(max_area) << 32) | next_pow2(max_tris);
-    auto hit = c->tuned.find(key);
-    if (hit != c->tuned.end()) {
-        c->cfg.threads = hit->second.threads;
-        c->cfg.zcap_words = hit->second.zcap_words;
-        *threads = c->cfg.threads;
-        *zbuf_words = c->cfg.zcap_words;
-        return PERCH_OK;
-    }
-    // time each shape on a sample of whole items (launches of the real
-    // sizes, so per-launch tails weigh the same): every 8th item in order of
-    // size, which keeps the batch's mix of small and large items; batches of
-    // fewer than 16 items are timed whole
-    std::vector<int32_t> idx(n_items);
-    for (int32_t i = 0; i < n_items; ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return items[x].n > items[y].n; });
-    std::vector<perch_work_item> sample;
-    const int32_t step = n_items < 16 ? 1 : 8;
-    for (int32_t k = step / 2; k < n_items; k += step) sample.push_back(items[idx[k]]);
-    std::vector<perch::Job> jobs;
-    int mw;
-    long long total;
-    perch_status st = batch_jobs(c, sample.data(), (int32_t)sample.size(), poses, costs, &jobs, &mw, &total);
-    if (st != PERCH_OK) return st;
-    const perch::ScoreConfig saved = c->cfg;
-    perch::ScoreConfig best = saved;
-    float best_ms = 3.0e38f;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    const int th[3] = {128, 256, 512};
-    const int zw[4] = {2048, 4096, 8192, 16384};
-    for (int ti = 0; ti < 3 && st == PERCH_OK; ++ti) {
-        for (int zi = 0; zi < 4 && st == PERCH_OK; ++zi) {
-            perch::ScoreConfig cfg = saved;
-            cfg.threads = th[ti];
-            cfg.zcap_words = zw[zi];
-            if (perch::score_smem_bytes(cfg, mw) > 200 * 1024) continue;
-            float ms = 3.0e38f;
-            for (int rep = 0; rep < 2 && st == PERCH_OK; ++rep) {
-                cudaEventRecord(e0, c->stream);
-                st = run_jobs(c, c->plain, jobs, mw, cfg, c->stream, nullptr);
-                cudaEventRecord(e1, c->stream);
-                cudaEventSynchronize(e1);
-                float t = 0.0f;
-                cudaEventElapsedTime(&t, e0, e1);
-                if (rep > 0) ms = std::min(ms, t);
-            }
-            if (st == PERCH_OK && ms < best_ms) {
-                best_ms = ms;
-                best = cfg;
-            }
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st != PERCH_OK) return st;
-    c->cfg.threads = best.threads;
-    c->cfg.zcap_words = best.zcap_words;
-    c->tuned[key] = c->cfg;
-    *threads = c->cfg.threads;
-    *zbuf_words = c->cfg.zcap_words;
-    return check_device_error(c);
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
-// served form: continuous batching over launch slots
-// ---------------------------------------------------------------------------
-
-namespace {
-
-int64_t now_ns()
-{
-    return std::chrono::duration_cast<std::chrono::nanoseconds>(
-               std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-
-struct ServedRequest {
-    uint64_t ticket = 0;
-    perch::Job tmpl{};              // scene, mesh, label, ROI (pointers filled per launch)
-    int mark_words = 0;
-    std::vector<float> poses;       // copy of the caller's poses
-    int32_t* user_costs = nullptr;
-    int64_t n = 0;
-    int64_t t_submit = 0, t_done = 0;
-    perch_status status = PERCH_OK;
-    bool done = false;
-};
-
-struct Slot {
-    ScoreScratch X;
-    cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    float* d_poses = nullptr;
-    int32_t* d_costs = nullptr;
-    float* h_poses = nullptr;       // pinned
-    int32_t* h_costs = nullptr;     // pinned
-    std::vector<std::shared_ptr<ServedRequest>> reqs;
-    std::vector<int64_t> offsets;
-    std::vector<cudaEvent_t> req_done;  // per request: its costs are in h_costs
-    bool busy = false;
-};
-
-}  // namespace
-
-struct perch_server {
-    perch_ctx* c = nullptr;
-    perch_server_config cfg{};
-    std::vector<Slot> slots;
-    std::mutex mu;                  // queue, slots, tickets
-    std::mutex ctx_mu;              // context state used by submit and the scheduler
-    std::condition_variable cv_sched, cv_done, cv_wait;
-    std::deque<std::shared_ptr<ServedRequest>> pending;
-    int64_t pending_hyps = 0;
-    std::deque<int> in_flight;      // slots in launch order
-    std::unordered_map<uint64_t, std::shared_ptr<ServedRequest>> tickets;
-    uint64_t next_ticket = 1;
-    bool stopping = false;
-    bool sched_done = false;
-    std::thread sched, completer;
-};
-
-namespace {
-
-void serve_schedule(perch_server* S)
-{
-    cudaSetDevice(S->c->device);
-    for (;;) {
-        std::unique_lock<std::mutex> lk(S->mu);
-        auto free_slot = [&]() {
-            for (size_t i = 0; i < S->slots.size(); ++i)
-                if (!S->slots[i].busy) return (int)i;
-            return -1;
-        };
-        S->cv_sched.wait(lk, [&] {
-            return (S->stopping && S->pending.empty()) || (!S->pending.empty() && free_slot() >= 0);
-        });
-        if (S->pending.empty()) break;
-        if (S->cfg.max_wait_us > 0 && !S->stopping && S->pending_hyps < S->cfg.max_batch_hypotheses)
-            S->cv_sched.wait_for(lk, std::chrono::microseconds(S->cfg.max_wait_us), [&] {
-                return S->stopping || S->pending_hyps >= S->cfg.max_batch_hypotheses;
-            });
-        const int si = free_slot();
-        Slot& slot = S->slots[si];
-        slot.reqs.clear();
-        slot.offsets.clear();
-        int64_t total = 0;
-        while (!S->pending.empty() && total + S->pending.front()->n <= S->cfg.max_batch_hypotheses) {
-            auto r = S->pending.front();
-            S->pending.pop_front();
-            S->pending_hyps -= r->n;
-            slot.reqs.push_back(r);
-            total += r->n;
-        }
-        // smallest requests first: each completes as soon as its own launch
-        // and read-back are done, so short ones do not wait for long ones
-        std::stable_sort(slot.reqs.begin(), slot.reqs.end(),
-                         [](const std::shared_ptr<ServedRequest>& x, const std::shared_ptr<ServedRequest>& y) {
-                             return x->n < y->n;
-                         });
-        for (size_t k = 0, off = 0; k < slot.reqs.size(); off += slot.reqs[k]->n, ++k) slot.offsets.push_back(off);
-        slot.busy = true;
-        lk.unlock();
-        perch_status st = PERCH_OK;
-        while (slot.req_done.size() < slot.reqs.size()) {
-            cudaEvent_t ev = nullptr;
-            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                st = PERCH_E_CUDA;
-                break;
-            }
-            slot.req_done.push_back(ev);
-        }
-
-        std::vector<perch::Job> jobs;
-        int mw = 0;
-        for (size_t k = 0; k < slot.reqs.size(); ++k) {
-            const auto& r = slot.reqs[k];
-            std::memcpy(slot.h_poses + 12 * slot.offsets[k], r->poses.data(), r->poses.size() * sizeof(float));
-            perch::Job J = r->tmpl;
-            J.poses = slot.d_poses + 12 * slot.offsets[k];
-            J.costs = slot.d_costs + 2 * slot.offsets[k];
-            J.n = r->n;
-            jobs.push_back(J);
-            mw = std::max(mw, r->mark_words);
-        }
-        cudaError_t e = cudaSuccess;
-        if (st == PERCH_OK) e = cudaMemcpyAsync(slot.d_poses, slot.h_poses, total * 48, cudaMemcpyHostToDevice, slot.stream);
-        if (e) st = PERCH_E_CUDA;
-        if (st == PERCH_OK) {
-            const AfterJob readback = [&](size_t j, cudaStream_t js) {
-                const int64_t off = slot.offsets[j], n = slot.reqs[j]->n;
-                cudaError_t r = cudaMemcpyAsync(slot.h_costs + 2 * off, slot.d_costs + 2 * off, n * 8,
-                                                cudaMemcpyDeviceToHost, js);
-                return r ? r : cudaEventRecord(slot.req_done[j], js);
-            };
-            std::lock_guard<std::mutex> g(S->ctx_mu);
-            st = run_jobs(S->c, slot.X, jobs, mw, S->c->cfg, slot.stream, nullptr, &readback);
-        }
-        cudaEventRecord(slot.done, slot.stream);
-        if (st != PERCH_OK)
-            for (auto& r : slot.reqs) r->status = st;
-        lk.lock();
-        // hand the slot to the completion thread only once its event is recorded
-        S->in_flight.push_back(si);
-        S->cv_done.notify_all();
-    }
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->sched_done = true;
-    S->cv_done.notify_all();
-}
-
-void serve_complete(perch_server* S)
-{
-    cudaSetDevice(S->c->device);
-    for (;;) {
-        std::unique_lock<std::mutex> lk(S->mu);
-        S->cv_done.wait(lk, [&] { return !S->in_flight.empty() || S->sched_done; });
-        if (S->in_flight.empty()) break;
-        const int si = S->in_flight.front();
-        lk.unlock();
-        Slot& slot = S->slots[si];
-        // requests in launch order, each as soon as its own read-back is done
-        for (size_t k = 0; k < slot.reqs.size(); ++k) {
-            auto& r = slot.reqs[k];
-            cudaError_t e = r->status == PERCH_OK ? cudaEventSynchronize(slot.req_done[k]) : cudaSuccess;
-            if (e != cudaSuccess && r->status == PERCH_OK) r->status = PERCH_E_CUDA;
-            if (r->status == PERCH_OK)
-                std::memcpy(r->user_costs, slot.h_costs + 2 * slot.offsets[k], r->n * 2 * sizeof(int32_t));
-            r->t_done = now_ns();
-            std::lock_guard<std::mutex> g(S->mu);
-            r->done = true;
-            r->poses.clear();
-            r->poses.shrink_to_fit();
-            S->cv_wait.notify_all();
-        }
-        cudaEventSynchronize(slot.done);
-        lk.lock();
-        slot.reqs.clear();
-        slot.busy = false;
-        S->in_flight.pop_front();
-        S->cv_sched.notify_all();
-        S->cv_wait.notify_all();
-    }
-}
-
-}  // namespace
-
-extern "C" {
-
-perch_status perch_server_start(perch_ctx* c, const perch_server_config* cfg, perch_server** out)
-{
-    if (!c || !cfg || !out) return PERCH_E_INVALID;
-    c->err.clear();
-    *out = nullptr;
-    if (cfg->slots < 1 || cfg->slots > 16 || cfg->max_batch_hypotheses < 1 || cfg->max_batch_hypotheses > (1ll << 30) ||
-        cfg->max_wait_us < 0)
-        return fail(c, PERCH_E_INVALID, "server configuration out of range");
-    DeviceGuard g(c->device);
-    perch_server* S = new (std::nothrow) perch_server();
-    if (!S) return fail(c, PERCH_E_NOMEM, "server");
-    S->c = c;
-    S->cfg = *cfg;
-    S->slots.resize(cfg->slots);
-    perch_status st = PERCH_OK;
-    const size_t nb = (size_t)cfg->max_batch_hypotheses;
-    for (auto& slot : S->slots) {
-        void* p = nullptr;
-        if (st == PERCH_OK) st = scratch_init(c, slot.X);
-        if (st == PERCH_OK && (st = dalloc(c, nb * 48, &p)) == PERCH_OK) slot.d_poses = (float*)p;
-        if (st == PERCH_OK && (st = dalloc(c, nb * 8, &p)) == PERCH_OK) slot.d_costs = (int32_t*)p;
-        if (st == PERCH_OK && (cudaMallocHost(&p, nb * 48) != cudaSuccess || !(slot.h_poses = (float*)p)))
-            st = fail(c, PERCH_E_NOMEM, "pinned staging");
-        if (st == PERCH_OK && (cudaMallocHost(&p, nb * 8) != cudaSuccess || !(slot.h_costs = (int32_t*)p)))
-            st = fail(c, PERCH_E_NOMEM, "pinned staging");
-        if (st == PERCH_OK && (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
-                               cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess))
-            st = cuda_fail(c, cudaGetLastError(), "server stream");
-    }
-    if (st != PERCH_OK) {
-        for (auto& slot : S->slots) {
-            scratch_free(c, slot.X);
-            dfree(c, slot.d_poses);
-            dfree(c, slot.d_costs);
-            if (slot.h_poses) cudaFreeHost(slot.h_poses);
-            if (slot.h_costs) cudaFreeHost(slot.h_costs);
-            if (slot.stream) cudaStreamDestroy(slot.stream);
-            if (slot.done) cudaEventDestroy(slot.done);
-            for (auto ev : slot.req_done) cudaEventDestroy(ev);
-        }
-        delete S;
-        return st;
-    }
-    S->sched = std::thread(serve_schedule, S);
-    S->completer = std::thread(serve_complete, S);
-    *out = S;
-    return PERCH_OK;
-}
-
-perch_status perch_submit(perch_server* S, const perch_request* req, uint64_t* ticket)
-{
-    if (!S || !req || !ticket) return PERCH_E_INVALID;
-    if (!req->poses || !req->costs || req->n < 1) return PERCH_E_INVALID;
-    if (req->n > S->cfg.max_batch_hypotheses) return PERCH_E_BUDGET;
-    auto r = std::make_shared<ServedRequest>();
-    {
-        std::lock_guard<std::mutex> g(S->ctx_mu);
-        const int32_t* roi = (req->roi[2] > req->roi[0] && req->roi[3] > req->roi[1]) ? req->roi : nullptr;
-        perch_status st = make_job(S->c, req->scene_id, req->mesh_id, req->label, roi, nullptr, nullptr,
-                                   req->n, &r->tmpl, &r->mark_words, nullptr, nullptr);
-        if (st != PERCH_OK) return st;
-    }
-    r->poses.assign(req->poses, req->poses + 12 * req->n);
-    r->user_costs = req->costs;
-    r->n = req->n;
-    r->t_submit = now_ns();
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (S->stopping) return PERCH_E_BUSY;
-    r->ticket = S->next_ticket++;
-    S->tickets[r->ticket] = r;
-    S->pending.push_back(r);
-    S->pending_hyps += r->n;
-    *ticket = r->ticket;
-    S->cv_sched.notify_all();
-    return PERCH_OK;
-}
-
-perch_status perch_poll(perch_server* S, uint64_t ticket)
-{
-    if (!S) return PERCH_E_INVALID;
-    std::lock_guard<std::mutex> lk(S->mu);
-    auto it = S->tickets.find(ticket);
-    if (it == S->tickets.end()) return PERCH_E_NOTFOUND;
-    if (!it->second->done) return PERCH_E_BUSY;
-    return it->second->status;
-}
-
-perch_status perch_wait(perch_server* S, uint64_t ticket, int64_t timeout_us)
-{
-    if (!S) return PERCH_E_INVALID;
-    std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->tickets.find(ticket);
-    if (it == S->tickets.end()) return PERCH_E_NOTFOUND;
-    auto r = it->second;
-    if (timeout_us < 0) {
-        S->cv_wait.wait(lk, [&] { return r->done; });
-    } else if (!S->cv_wait.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; })) {
-        return PERCH_E_TIMEOUT;
-    }
-    return r->status;
-}
-
-perch_status perch_ticket_times(perch_server* S, uint64_t ticket, int64_t* submit_ns, int64_t* done_ns)
-{
-    if (!S || !submit_ns || !done_ns) return PERCH_E_INVALID;
-    std::lock_guard<std::mutex> lk(S->mu);
-    auto it = S->tickets.find(ticket);
-    if (it == S->tickets.end()) return PERCH_E_NOTFOUND;
-    if (!it->second->done) return PERCH_E_BUSY;
-    *submit_ns = it->second->t_submit;
-    *done_ns = it->second->t_done;
-    return PERCH_OK;
-}
-
-perch_status perch_server_stop(perch_server* S)
-{
-    if (!S) return PERCH_OK;
-    {
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->stopping = true;
-        S->cv_sched.notify_all();
-    }
-    if (S->sched.joinable()) S->sched.join();
-    if (S->completer.joinable()) S->completer.join();
-    perch_ctx* c = S->c;
-    DeviceGuard g(c->device);
-    for (auto& slot : S->slots) {
-        if (slot.stream) cudaStreamSynchronize(slot.stream);
-        scratch_free(c, slot.X);
-        dfree(c, slot.d_poses);
-        dfree(c, slot.d_costs);
-        if (slot.h_poses) cudaFreeHost(slot.h_poses);
-        if (slot.h_costs) cudaFreeHost(slot.h_costs);
-        if (slot.stream) cudaStreamDestroy(slot.stream);
-        if (slot.done) cudaEventDestroy(slot.done);
-        for (auto ev : slot.req_done) cudaEventDestroy(ev);
-    }
-    delete S;
-    return PERCH_OK;
 }
 
 }  // extern "C"

@@ -1,4 +1,4 @@
-// Internal types shared by the host API (perch_api.cu) and the kernels
+// Internal types shared by the host API (perch_api.cu and its siblings) and the kernels
 // (perch_kernels.cu) of libperch.  Not part of the public ABI.
 #pragma once
 

@@ -96,8 +96,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched, served, refine and tree legs")
-    ap.add_argument("--legs", default="batched,served,refine,tree",
-                    help="comma-separated subset of the batched, served, refine and tree legs")
+    ap.add_argument("--legs", default="batched,served,refine,tree,configs",
+                    help="comma-separated subset of the batched, served, refine, tree and configs legs")
     ap.add_argument("--refine-hyp", type=int, default=4096, help="hypotheses per object of the refine leg")
     return ap.parse_args()
 
@@ -201,6 +201,61 @@ def cpu_baseline(sc, seconds, rng_seed=0):
             "sample": f"{total_h} random hypotheses ({rounds} rounds x {per} per object) of the same "
                       f"workload, brute-force nearest neighbours, {total_t:.1f} s",
             "value_1core": n1 / t1, "sample_1core": f"{n1} hypotheses (one per object), {t1:.1f} s"}, work
+
+
+def configs_leg(P, torch, dev, oracle_seconds=4.0, reps=3):
+    """The other synthetic configurations: device-timed GPU rate (poses
+    resident) beside the oracle's rate on a bounded sample, host cores."""
+    from paper_2008_00326_gb300 import scenes
+    from oracle import oracle as O
+    s = torch.cuda.Stream(dev)
+    out = {}
+    cases = (("tabletop_small: 160x120, one 516-triangle box, 968 3-DoF hypotheses", scenes.tabletop_small()),
+             ("sixdof_5obj: 640x480, 5 x 30k-triangle meshes, labels and ROIs, 5 x 4,096 6-DoF hypotheses",
+              scenes.sixdof_5obj()))
+    with P.Context(dev.index or 0) as ctx:
+        for desc, sc in cases:
+            sid = ctx.set_observation(sc)
+            mids = [ctx.load_mesh(m) for m in sc.meshes]
+            dp = [torch.from_numpy(r.poses).to(dev) for r in sc.requests]
+            dc = [torch.empty((len(r.poses), 2), dtype=torch.int32, device=dev) for r in sc.requests]
+            n = sum(len(r.poses) for r in sc.requests)
+
+            def run():
+                for k, r in enumerate(sc.requests):
+                    P.perch_score_hypotheses(ctx.ctx, sid, mids[r.mesh_index], r.label, r.roi, dp[k], dc[k], s)
+
+            best = float("inf")
+            with torch.cuda.stream(s):
+                run()
+                s.synchronize()
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    run()
+                    e1.record(s)
+                    s.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+            # the oracle on random hypotheses of the same configuration
+            rng = np.random.default_rng(3)
+            per = max(1, O.num_threads())
+            osc = O.OracleScene.from_scene(sc)
+            t_cpu, n_cpu = 0.0, 0
+            while t_cpu < oracle_seconds:
+                r = sc.requests[int(rng.integers(0, len(sc.requests)))]
+                pick = rng.choice(len(r.poses), min(per, len(r.poses)), replace=False)
+                om = O.OracleMesh.from_mesh(sc.meshes[r.mesh_index])
+                t0 = time.perf_counter()
+                O.score(osc, om, r.poses[pick], label=r.label, roi=r.roi)
+                t_cpu += time.perf_counter() - t0
+                n_cpu += len(pick)
+            out[sc.name] = {"workload": desc, "hypotheses": n, "gpu_ms": best,
+                            "gpu_hyp_s": n / (best / 1000.0),
+                            "oracle_hyp_s": n_cpu / t_cpu, "oracle_cores": per,
+                            "oracle_sample": f"{n_cpu} random hypotheses, {t_cpu:.1f} s"}
+            P.perch_release_scene(ctx.ctx, sid)
+    return out
 
 
 def reference_arm(a):
@@ -602,13 +657,14 @@ def main():
         return
 
     # ---- batched and served forms (rank 0, N = 1)
-    batched = served = refine = tree = None
+    batched = served = refine = tree = others = None
     legs = set() if a.no_forms else set(a.legs.split(","))
     if world == 1:
         batched = batched_leg(P, torch, dev) if "batched" in legs else None
         served = served_leg(P, dev) if "served" in legs else None
         refine = refine_leg(P, torch, dev, n_hyp=a.refine_hyp) if "refine" in legs else None
         tree = tree_leg(P, torch, dev) if "tree" in legs else None
+        others = configs_leg(P, torch, dev) if ("configs" in legs and not a.no_cpu_baseline) else None
 
     # ---- CPU oracle baseline and the roofline's algorithmic work
     cpu, work = (None, None)
@@ -670,6 +726,7 @@ def main():
         "served": served,
         "refine": refine,
         "tree": tree,
+        "other_configs": others,
     }
     print(json.dumps(out))
     ctx.close()

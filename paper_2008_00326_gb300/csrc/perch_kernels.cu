@@ -1396,7 +1396,7 @@ cudaError_t launch_score(const ScoreArgs& a, const ScoreConfig& cfg, int grid, c
 // fixed-point sums make the result independent of the summation order.
 
 constexpr int kGicpTerms = 28;
-constexpr int kGicpThreads = 256;
+constexpr int kGicpThreads = 128;   // four blocks per SM: source clouds are small
 constexpr float kGicpScale = 16777216.0f;    // 2^24
 constexpr float kGicpLimit = 1048576.0f;     // a correspondence with a larger |term| is skipped
 
@@ -1683,7 +1683,7 @@ __host__ __device__ inline size_t gicp_probe_offset(int zcap_words)
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, 2) k_gicp(GicpArgs a)
+__global__ void __launch_bounds__(NT, 512 / NT) k_gicp(GicpArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12], s_Rf[9], s_tf[3];

@@ -203,18 +203,19 @@ def cpu_baseline(sc, seconds, rng_seed=0):
             "value_1core": n1 / t1, "sample_1core": f"{n1} hypotheses (one per object), {t1:.1f} s"}, work
 
 
-def configs_leg(P, torch, dev, oracle_seconds=4.0, reps=3):
-    """The other synthetic configurations: device-timed GPU rate (poses
-    resident) beside the oracle's rate on a bounded sample, host cores."""
+def _other_config_scenes():
     from paper_2008_00326_gb300 import scenes
-    from oracle import oracle as O
+    return (("tabletop_small: 160x120, one 516-triangle box, 968 3-DoF hypotheses", scenes.tabletop_small()),
+            ("sixdof_5obj: 640x480, 5 x 30k-triangle meshes, labels and ROIs, 5 x 4,096 6-DoF hypotheses",
+             scenes.sixdof_5obj()))
+
+
+def configs_leg(P, torch, dev, reps=3):
+    """The other synthetic configurations, device-timed with poses resident."""
     s = torch.cuda.Stream(dev)
     out = {}
-    cases = (("tabletop_small: 160x120, one 516-triangle box, 968 3-DoF hypotheses", scenes.tabletop_small()),
-             ("sixdof_5obj: 640x480, 5 x 30k-triangle meshes, labels and ROIs, 5 x 4,096 6-DoF hypotheses",
-              scenes.sixdof_5obj()))
     with P.Context(dev.index or 0) as ctx:
-        for desc, sc in cases:
+        for desc, sc in _other_config_scenes():
             sid = ctx.set_observation(sc)
             mids = [ctx.load_mesh(m) for m in sc.meshes]
             dp = [torch.from_numpy(r.poses).to(dev) for r in sc.requests]
@@ -237,24 +238,31 @@ def configs_leg(P, torch, dev, oracle_seconds=4.0, reps=3):
                     e1.record(s)
                     s.synchronize()
                     best = min(best, e0.elapsed_time(e1))
-            # the oracle on random hypotheses of the same configuration
-            rng = np.random.default_rng(3)
-            per = max(1, O.num_threads())
-            osc = O.OracleScene.from_scene(sc)
-            t_cpu, n_cpu = 0.0, 0
-            while t_cpu < oracle_seconds:
-                r = sc.requests[int(rng.integers(0, len(sc.requests)))]
-                pick = rng.choice(len(r.poses), min(per, len(r.poses)), replace=False)
-                om = O.OracleMesh.from_mesh(sc.meshes[r.mesh_index])
-                t0 = time.perf_counter()
-                O.score(osc, om, r.poses[pick], label=r.label, roi=r.roi)
-                t_cpu += time.perf_counter() - t0
-                n_cpu += len(pick)
-            out[sc.name] = {"workload": desc, "hypotheses": n, "gpu_ms": best,
-                            "gpu_hyp_s": n / (best / 1000.0),
-                            "oracle_hyp_s": n_cpu / t_cpu, "oracle_cores": per,
-                            "oracle_sample": f"{n_cpu} random hypotheses, {t_cpu:.1f} s"}
+            out[sc.name] = {"workload": desc, "hypotheses": n, "gpu_ms": best, "gpu_hyp_s": n / (best / 1000.0)}
             P.perch_release_scene(ctx.ctx, sid)
+    return out
+
+
+def cpu_baseline_other_configs(seconds=4.0):
+    """The oracle, as it stands, on random hypotheses of the other
+    configurations (host cores)."""
+    from oracle import oracle as O
+    out = {}
+    for desc, sc in _other_config_scenes():
+        rng = np.random.default_rng(3)
+        per = max(1, O.num_threads())
+        osc = O.OracleScene.from_scene(sc)
+        t_cpu, n_cpu = 0.0, 0
+        while t_cpu < seconds:
+            r = sc.requests[int(rng.integers(0, len(sc.requests)))]
+            pick = rng.choice(len(r.poses), min(per, len(r.poses)), replace=False)
+            om = O.OracleMesh.from_mesh(sc.meshes[r.mesh_index])
+            t0 = time.perf_counter()
+            O.score(osc, om, r.poses[pick], label=r.label, roi=r.roi)
+            t_cpu += time.perf_counter() - t0
+            n_cpu += len(pick)
+        out[sc.name] = {"value": n_cpu / t_cpu, "unit": UNIT, "cores": per,
+                        "sample": f"{n_cpu} random hypotheses, {t_cpu:.1f} s"}
     return out
 
 
@@ -664,12 +672,14 @@ def main():
         served = served_leg(P, dev) if "served" in legs else None
         refine = refine_leg(P, torch, dev, n_hyp=a.refine_hyp) if "refine" in legs else None
         tree = tree_leg(P, torch, dev) if "tree" in legs else None
-        others = configs_leg(P, torch, dev) if ("configs" in legs and not a.no_cpu_baseline) else None
+        others = configs_leg(P, torch, dev) if "configs" in legs else None
 
     # ---- CPU oracle baseline and the roofline's algorithmic work
     cpu, work = (None, None)
     if not a.no_cpu_baseline and world == 1:
         cpu, work = cpu_baseline(sc, a.cpu_seconds)
+        if others is not None:
+            cpu["other_configs"] = cpu_baseline_other_configs()
     roof = None
     per_obj_ms = {}
     for k, ms in score_ms:

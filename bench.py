@@ -243,14 +243,14 @@ def configs_leg(P, torch, dev, reps=3):
     return out
 
 
-def cpu_baseline_other_configs(seconds=4.0):
+def cpu_baseline_other_configs(cores, seconds=4.0):
     """The oracle, as it stands, on random hypotheses of the other
-    configurations (host cores)."""
+    configurations, on `cores` host threads."""
     from oracle import oracle as O
     out = {}
     for desc, sc in _other_config_scenes():
         rng = np.random.default_rng(3)
-        per = max(1, O.num_threads())
+        per = max(1, cores)
         osc = O.OracleScene.from_scene(sc)
         t_cpu, n_cpu = 0.0, 0
         while t_cpu < seconds:
@@ -258,7 +258,7 @@ def cpu_baseline_other_configs(seconds=4.0):
             pick = rng.choice(len(r.poses), min(per, len(r.poses)), replace=False)
             om = O.OracleMesh.from_mesh(sc.meshes[r.mesh_index])
             t0 = time.perf_counter()
-            O.score(osc, om, r.poses[pick], label=r.label, roi=r.roi)
+            O.score(osc, om, r.poses[pick], label=r.label, roi=r.roi, threads=per)
             t_cpu += time.perf_counter() - t0
             n_cpu += len(pick)
         out[sc.name] = {"value": n_cpu / t_cpu, "unit": UNIT, "cores": per,
@@ -679,7 +679,7 @@ def main():
     if not a.no_cpu_baseline and world == 1:
         cpu, work = cpu_baseline(sc, a.cpu_seconds)
         if others is not None:
-            cpu["other_configs"] = cpu_baseline_other_configs()
+            cpu["other_configs"] = cpu_baseline_other_configs(cpu["cores"])
     roof = None
     per_obj_ms = {}
     for k, ms in score_ms:

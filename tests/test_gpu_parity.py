@@ -295,6 +295,32 @@ def test_edge_cases(ctx, oracle, P):
     assert np.array_equal(got, want) and np.all(got[:, 0] == 0)
 
 
+def test_wide_image_and_64bit_keys(ctx, oracle):
+    """W > 1023 (no vertex cache: triangles set up from the pose directly) at
+    the largest image the int32 edge functions allow, and poses beyond 6.5 m
+    (64-bit depth keys)."""
+    sc = scenes.tabletop_small(seed=33, W=1200, H=388)
+    sc.params.stride = 4                      # keeps the brute-force oracle quick
+    assert sc.W * sc.H <= 466033
+    sid, mids = _load(ctx, sc)
+    req = sc.requests[0]
+    osc, om = _oracle(oracle, sc, req)
+    poses = req.poses[::61]
+    got = ctx.score(sid, mids[0], req.label, req.roi, poses)
+    want, _ = oracle.score(osc, om, poses, label=req.label, roi=req.roi)
+    assert np.array_equal(got, want)
+    far = poses.copy().reshape(-1, 3, 4)
+    far[:, 2, 3] = 7.0                        # 7 m ahead: depths above 65,535 units
+    far = far.reshape(-1, 12)
+    sid_all = ctx.set_observation(sc, occ_margin_units=-1)   # keep the far points (no occluders)
+    got = ctx.score(sid_all, mids[0], req.label, req.roi, far)
+    want, _ = oracle.score(oracle.OracleScene.from_scene(sc, occ_margin=-1), om, far, label=req.label, roi=req.roi)
+    assert np.array_equal(got, want) and np.all(want[:, 1] > 0)
+    keys = ctx.render_keys(sid, mids[0], req.roi, far[0], sc.W, sc.H)
+    wkeys, _ = oracle.render_keys(osc, om, far[0], req.roi)
+    assert np.array_equal(keys, wkeys) and np.any((wkeys != EMPTY) & ((wkeys >> np.uint64(32)) > 65535))
+
+
 def test_errors_and_budget(P):
     sc = scenes.tabletop_small()
     with P.Context(0, hbm_budget_bytes=1 << 16) as small:

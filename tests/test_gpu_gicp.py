@@ -127,6 +127,21 @@ def test_full_size_stride2_sample(P, ctx, oracle):
         assert np.array_equal(got[pick].view(np.uint32), want.view(np.uint32)), k
 
 
+def test_wide_image_without_vertex_cache(P, ctx, oracle):
+    """W > 1023: the refinement renders without the vertex cache."""
+    sc = scenes.tabletop_small(seed=34, W=1200, H=388)
+    sc.params.stride = 4
+    sid = ctx.set_observation(sc)
+    mid = ctx.load_mesh(sc.meshes[0])
+    req = sc.requests[0]
+    poses = req.poses[::97]
+    got, info = ctx.refine(sid, mid, req.label, req.roi, poses)
+    want, winfo = oracle.gicp(oracle.OracleScene.from_scene(sc), oracle.OracleMesh.from_mesh(sc.meshes[0]),
+                              poses, label=req.label, roi=req.roi)
+    assert np.array_equal(info, winfo)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
 def test_labels_and_roi_6dof(P, ctx, oracle):
     sc = scenes.sixdof_5obj(n_hyp=48, W=320, H=240, tri_scale=0.1)
     sid = ctx.set_observation(sc)

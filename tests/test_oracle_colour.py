@@ -107,3 +107,26 @@ def test_hue_wrap_mean_angle(oracle):
     # a pair 180 deg apart reports a zero wrap gap (band case)
     _, gap = oracle.ciede2000(np.array([50, 20, 0], np.float32), np.array([50, -20, 0], np.float32))
     assert gap < 1e-3
+
+
+def _lch(L, C, h_deg):
+    h = math.radians(h_deg)
+    return (L, C * math.cos(h), C * math.sin(h))
+
+
+@pytest.mark.parametrize("centre,expect_rotation", [(270.0, True), (90.0, False), (180.0, False)])
+def test_rotation_term_by_swapped_chromas(oracle, centre, expect_rotation):
+    """The rotation term R_T (dC'/S_C)(dH'/S_H) is the only part of CIEDE2000
+    that changes sign when two colours at hues centre -+ phi swap chromas:
+    with hues mirrored about the a* or b* axis (centres 90, 180 and 270 deg),
+    C', h'-bar, S_C, S_H and |dC' dH'| are the same for both pairs.  So the
+    two distances differ only where the rotation acts -- in the blue region
+    around 275 deg -- and there the pair with dC' dH' > 0 is the closer one
+    (R_T < 0)."""
+    phi, C1, C2, L = 10.0, 20.0, 40.0, 50.0
+    pair1 = _de(oracle, _lch(L, C1, centre - phi), _lch(L, C2, centre + phi))   # dC' > 0, dh' > 0
+    pair2 = _de(oracle, _lch(L, C2, centre - phi), _lch(L, C1, centre + phi))   # dC' < 0, dh' > 0
+    if expect_rotation:
+        assert pair1 < pair2 - 0.05, (pair1, pair2)
+    else:
+        assert abs(pair1 - pair2) < 1e-4, (pair1, pair2)

@@ -10,9 +10,18 @@ value : device-timed throughput with poses resident in HBM (CUDA events on the
         launching stream, L2 flushed between steps by a 512 MiB write).
 e2e   : the same metric through the public API with HOST buffers: pinned poses
         copied in and costs + argmin read back inside the timed region.
-roofline : the scoring kernel, bound by FP32 ALU issue (distance tests);
-        algorithmic work = oracle-counted 27-cell candidates x 8 FP32 ops.
-cpu_baseline : the plain C oracle on a bounded sample of the same workload.
+roofline : the scoring kernel against the 32-bit ALU issue peak; algorithmic
+        work = the oracle's per-hypothesis counts (vertices, triangle set-ups,
+        covered samples, kept points, 27-cell candidates, points of V) times
+        the operations each takes (OPS); DRAM traffic from the committed ncu
+        capture while the kernel source matches it; the rasteriser's shared-
+        memory atomics against their measured rate.
+cpu_baseline : the plain C oracle on a bounded sample of the same workload
+        (all host threads and one), and of the other configurations.
+batched / served / refine / tree / other_configs : the batched form (64
+        uneven scenes, autotuned), the served form (Poisson traces, serial
+        path vs server), GICP refinement then scoring (6-DoF), the tree search
+        of variant 2.0-B, and the other synthetic configurations.
 
 N > 1 (torchrun): every rank scores its own copy of the batch (independent
 problems, weak scaling, no data-path collective); value = all ranks' hypotheses

@@ -196,20 +196,21 @@ def cpu_baseline(sc, seconds, rng_seed=0):
         if time.perf_counter() >= deadline:
             break
     work = np.concatenate(work)
-    # the same oracle on one core: one hypothesis per object
+    # the same oracle on one core: at least 16 hypotheses in all
     t1, n1 = 0.0, 0
+    per1 = -(-16 // len(sc.requests))
     for req in sc.requests:
-        pick = rng.choice(len(req.poses), 1, replace=False)
+        pick = rng.choice(len(req.poses), per1, replace=False)
         osc = O.OracleScene.from_scene(sc)
         om = O.OracleMesh.from_mesh(sc.meshes[req.mesh_index])
         t0 = time.perf_counter()
         O.score(osc, om, req.poses[pick], label=req.label, roi=req.roi, threads=1)
         t1 += time.perf_counter() - t0
-        n1 += 1
+        n1 += len(pick)
     return {"value": total_h / total_t, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{total_h} random hypotheses ({rounds} rounds x {per} per object) of the same "
                       f"workload, brute-force nearest neighbours, {total_t:.1f} s",
-            "value_1core": n1 / t1, "sample_1core": f"{n1} hypotheses (one per object), {t1:.1f} s"}, work
+            "value_1core": n1 / t1, "sample_1core": f"{n1} hypotheses ({per1} per object), {t1:.1f} s"}, work
 
 
 def _other_config_scenes():
@@ -664,6 +665,8 @@ def main():
     for _ in range(e2e_steps):
         step_host()
     e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0) / e2e_steps, dist, dev)
+    # bytes the calls copy: the poses in; the costs and (index, cost) of the argmin out
+    # (perch_best in host mode copies the costs back in, so they count both ways)
     h2d = sum(p.nbytes for p in pinned) + sum(c.nbytes for c in host_costs)
     d2h = sum(c.nbytes for c in host_costs) + len(reqs) * 12
 

@@ -184,8 +184,10 @@ PERCH_API perch_status perch_best(perch_ctx *ctx, const int32_t *costs, const ui
  *   best_cost (int32) are DEVICE pointers on the current CUDA device; the work
  *   is enqueued on cuda_stream (NULL: the default stream) and the result is
  *   written when the stream reaches it.
- *   1 <= n <= 2^31-1, otherwise PERCH_E_INVALID; PERCH_E_CUDA if a CUDA call
- *   fails.
+ *   1 <= n <= 2^31-1, otherwise PERCH_E_INVALID.  PERCH_E_INVALID too when a
+ *   pointer is not device memory of the current device (host, pinned, managed
+ *   or another GPU's memory: checked with cudaPointerGetAttributes before any
+ *   launch); PERCH_E_CUDA if a CUDA call fails.
  * It allocates nothing.  Its scratch (the kernel's per-block partial results
  * and completion ticket, 24.8 KB for at most 1024 blocks) is a static device
  * array that every GPU loading the library holds until the process exits.

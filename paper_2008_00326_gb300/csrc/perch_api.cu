@@ -372,7 +372,7 @@ perch_status perch_create(perch_ctx** out, int32_t device, uint64_t hbm_budget_b
     if (e != cudaSuccess) st = cuda_fail(c, e, "cudaStreamCreate");
     void* p = nullptr;
     if (st == PERCH_OK && (st = dalloc(c, sizeof(int), &p)) == PERCH_OK) c->d_err = (int*)p;
-    if (st == PERCH_OK && (st = dalloc(c, sizeof(unsigned long long) * 3 * 1024, &p)) == PERCH_OK)
+    if (st == PERCH_OK && (st = dalloc(c, sizeof(unsigned long long) * 3 * perch::kBestMaxBlocks, &p)) == PERCH_OK)
         c->d_best_partial = (unsigned long long*)p;
     if (st == PERCH_OK && (st = dalloc(c, 64, &p)) == PERCH_OK) {
         c->d_best_ticket = (unsigned*)p;

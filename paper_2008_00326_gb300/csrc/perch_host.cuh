@@ -93,7 +93,7 @@ struct perch_ctx {
     void* stage = nullptr;
     size_t stage_bytes = 0;
     int* d_err = nullptr;
-    unsigned long long* d_best_partial = nullptr;   // 3 words per block, 1024 blocks
+    unsigned long long* d_best_partial = nullptr;   // 3 words per block, kBestMaxBlocks blocks
     unsigned* d_best_ticket = nullptr;
     long long* d_best_index = nullptr;
     int32_t* d_best_cost = nullptr;

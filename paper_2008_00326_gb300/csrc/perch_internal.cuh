@@ -158,14 +158,17 @@ cudaError_t launch_cell_bounds(const DevScene& sc, int* bounds, cudaStream_t s);
 // Fill sc.near_bits (zeroed) through the occupancy bitmap occ (zeroed, same size).
 cudaError_t launch_near_cells(const DevScene& sc, uint32_t* occ, uint32_t* near_bits, cudaStream_t s);
 
-// Argmin of J = J_o + J_r (ties to the lowest id / index).
+// Argmin of J = J_o + J_r (ties to the lowest id / index).  The kernel
+// launches at most kBestMaxBlocks blocks; each leaves three 64-bit words
+// (packed cost, id, index) in `partial`.
+constexpr int kBestMaxBlocks = 1024;
 struct BestArgs {
     const int32_t* costs;
     const unsigned long long* ids;  // or nullptr
     long long n;
     long long* best_index;
     int32_t* best_cost;
-    unsigned long long* partial;    // scratch: 2 words per block
+    unsigned long long* partial;    // scratch: 3 words per block, 3 * kBestMaxBlocks words
     unsigned int* ticket;           // scratch: 1 word, zero on entry, zero on exit
 };
 int best_blocks(long long n);

@@ -2043,7 +2043,7 @@ __global__ void __launch_bounds__(kBestThreads) k_best(BestArgs a)
 int best_blocks(long long n)
 {
     long long b = (n + kBestThreads - 1) / kBestThreads;
-    return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+    return (int)(b < 1 ? 1 : (b > kBestMaxBlocks ? kBestMaxBlocks : b));
 }
 
 cudaError_t launch_best(const BestArgs& a, cudaStream_t s)

@@ -18,10 +18,10 @@
 
 namespace {
 
-// The argmin launches at most this many blocks (see perch::best_blocks); each
-// block leaves three 64-bit words, and one more word holds the ticket.
-constexpr int kMaxBlocks = 1024;
-constexpr int kScratchWords = 3 * kMaxBlocks + 32;   // 24.8 KB
+// The argmin launches at most perch::kBestMaxBlocks blocks; each block leaves
+// three 64-bit words, and one more word holds the ticket.
+constexpr int kScratchWords = 3 * perch::kBestMaxBlocks + 32;   // 24.8 KB
+static_assert(kScratchWords >= 3 * perch::kBestMaxBlocks + 1, "partials plus the ticket");
 
 static __device__ __align__(256) unsigned long long g_best_scratch[kScratchWords];
 
@@ -49,6 +49,19 @@ cudaError_t scratch_on_current_device(unsigned long long** out)
     return cudaSuccess;
 }
 
+// True iff p is device memory of the current device (not host, pinned host
+// or managed memory, and not another GPU's): the kernel would fault, or
+// silently read host memory, on anything else.
+bool on_current_device(const void* p, int dev)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 }  // namespace
 
 extern "C" perch_status perch_best_noalloc(const int32_t* costs, const uint64_t* ids, int64_t n,
@@ -57,7 +70,14 @@ extern "C" perch_status perch_best_noalloc(const int32_t* costs, const uint64_t*
 {
     if (!costs || !best_index || !best_cost) return PERCH_E_INVALID;
     if (n < 1 || n > 0x7FFFFFFFll) return PERCH_E_INVALID;
-    if (perch::best_blocks(n) > kMaxBlocks) return PERCH_E_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PERCH_E_CUDA;
+    }
+    if (!on_current_device(costs, dev) || !on_current_device(best_index, dev) ||
+        !on_current_device(best_cost, dev) || (ids && !on_current_device(ids, dev)))
+        return PERCH_E_INVALID;
     unsigned long long* scratch = nullptr;
     cudaError_t e = scratch_on_current_device(&scratch);
     if (e != cudaSuccess) {
@@ -72,7 +92,7 @@ extern "C" perch_status perch_best_noalloc(const int32_t* costs, const uint64_t*
     a.best_index = reinterpret_cast<long long*>(best_index);
     a.best_cost = best_cost;
     a.partial = scratch;
-    a.ticket = reinterpret_cast<unsigned*>(scratch + 3 * kMaxBlocks);
+    a.ticket = reinterpret_cast<unsigned*>(scratch + 3 * perch::kBestMaxBlocks);
     // the ticket must start at zero; the partials are written before they are read
     e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = perch::launch_best(a, s);

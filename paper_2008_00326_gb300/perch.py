@@ -322,9 +322,36 @@ def perch_best(ctx, costs, ids=None, stream=None, out_index=None, out_cost=None)
                                    _ptr_of(out_index), _ptr_of(out_cost), handle))
 
 
+def _require_cuda(name, t, dtypes, min_numel=1):
+    """t must be a contiguous torch CUDA tensor on the current device with one
+    of `dtypes` and at least min_numel elements (the kernel would otherwise be
+    handed a host pointer or read past the end)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a torch CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, not the current device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} has dtype {t.dtype}; expected one of {dtypes}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name} needs at least {min_numel} elements")
+
+
 def perch_best_noalloc(costs, ids, out_index, out_cost, stream=None):
-    """Argmin without a context or any allocation: torch CUDA tensors in and out."""
-    n = costs.numel() // 2
+    """Argmin without a context or any allocation: contiguous torch CUDA tensors
+    on the current device -- costs int32 (n, 2), ids int64 (n,) or None,
+    out_index int64 and out_cost int32 with at least one element each."""
+    import torch
+    _require_cuda("costs", costs, (torch.int32,))
+    if costs.dim() != 2 or costs.shape[1] != 2:
+        raise ValueError("costs must have shape (n, 2)")
+    n = costs.shape[0]
+    if ids is not None:
+        _require_cuda("ids", ids, (torch.int64,), n)
+    _require_cuda("out_index", out_index, (torch.int64,))
+    _require_cuda("out_cost", out_cost, (torch.int32,))
     handle = getattr(stream, "cuda_stream", stream)
     st = load().perch_best_noalloc(_ptr_of(costs), None if ids is None else _ptr_of(ids), n,
                                    _ptr_of(out_index), _ptr_of(out_cost), handle)

@@ -130,3 +130,55 @@ def test_rotation_term_by_swapped_chromas(oracle, centre, expect_rotation):
         assert pair1 < pair2 - 0.05, (pair1, pair2)
     else:
         assert abs(pair1 - pair2) < 1e-4, (pair1, pair2)
+
+
+def _lab_from_primed(L, Cp1, hp1, Cp2, hp2):
+    """Two Lab colours whose primed chromas and hues (after CIEDE2000's a*
+    rescaling by 1 + G, G from the mean unprimed chroma) are (Cp1, hp1) and
+    (Cp2, hp2) degrees: the fixed point a = a' / (1 + G(C-bar)), float64."""
+    r = math.radians
+    ap1, b1 = Cp1 * math.cos(r(hp1)), Cp1 * math.sin(r(hp1))
+    ap2, b2 = Cp2 * math.cos(r(hp2)), Cp2 * math.sin(r(hp2))
+    g = 0.0
+    for _ in range(60):
+        a1, a2 = ap1 / (1 + g), ap2 / (1 + g)
+        g = _G((math.hypot(a1, b1) + math.hypot(a2, b2)) / 2)
+    return (L, ap1 / (1 + g), b1), (L, ap2 / (1 + g), b2)
+
+
+def _primed(lab):
+    """Primed chroma and hue (degrees) of a float32-rounded pair, float64."""
+    l1, l2 = (np.asarray(x, np.float32).astype(np.float64) for x in lab)
+    g = _G((math.hypot(l1[1], l1[2]) + math.hypot(l2[1], l2[2])) / 2)
+    out = []
+    for l in (l1, l2):
+        ap = (1 + g) * l[1]
+        out.append((math.hypot(ap, l[2]), math.degrees(math.atan2(l[2], ap)) % 360.0))
+    return out
+
+
+@pytest.mark.parametrize("hm", [275.0, 250.0, 300.0, 262.0])
+def test_rotation_term_magnitude_in_closed_form(oracle, hm):
+    """R_T = -sin(2 dtheta) R_C with dtheta = 30 deg exp(-((h'-bar - 275 deg) / 25 deg)^2)
+    and R_C = 2 sqrt(C'-bar^7 / (C'-bar^7 + 25^7)).  With equal lightness,
+    dE00^2 = x^2 + y^2 + R_T x y for x = dC'/S_C and y = dH'/S_H (S_C, S_H, G
+    and T are pinned by the tests above), so one pair isolates R_T.  The
+    primed chromas are chosen with mean 25, where R_C = sqrt(2): at the centre
+    hue 275 deg R_T = -sqrt(6)/2 exactly; at 250 and 300 deg (one Gaussian
+    width either side) dtheta = 30 deg / e, equal on both sides; 262 deg
+    pins the width again off the inflection."""
+    phi, Cp1, Cp2 = 9.0, 15.0, 35.0
+    lab1, lab2 = _lab_from_primed(50.0, Cp1, hm - phi, Cp2, hm + phi)
+    (c1, h1), (c2, h2) = _primed((lab1, lab2))
+    cbar, hbar = (c1 + c2) / 2, (h1 + h2) / 2
+    x = (c2 - c1) / (1 + 0.045 * cbar)
+    y = 2 * math.sqrt(c1 * c2) * math.sin(math.radians(h2 - h1) / 2) / (1 + 0.015 * cbar * _T(hbar))
+    de = _de(oracle, lab1, lab2)
+    rt_measured = (de * de - x * x - y * y) / (x * y)
+    dtheta = 30.0 * math.exp(-((hm - 275.0) / 25.0) ** 2)
+    rc = 2 * math.sqrt(25.0 ** 7 / (25.0 ** 7 + 25.0 ** 7))          # = sqrt(2) at C'-bar = 25
+    want = -math.sin(math.radians(2 * dtheta)) * rc
+    if hm == 275.0:
+        assert abs(want + math.sqrt(6) / 2) < 1e-12
+    assert abs(cbar - 25.0) < 1e-4 and abs(hbar - hm) < 1e-4
+    assert abs(rt_measured - want) < 2e-3, (hm, rt_measured, want)

@@ -66,7 +66,7 @@ typedef struct {
     int32_t stride;           /* image-space downsampling factor s >= 1     */
     int32_t occ_margin;       /* occluder margin m, 0.1 mm; < 0: no occluder marking (2.0-A) */
     float z_near;             /* metres                                     */
-    int32_t jo_mode;          /* 0: NN marks (Sec. IV-A kernel); 1: Eq. 3 with Eq. 2 */
+    int32_t jo_mode;          /* 0: NN marks (Sec. IV-A kernel); 1: Eq. 3 as written (Eq. 2 / Eq. 4 from p) */
 } or_scene;
 
 typedef struct {
@@ -431,7 +431,9 @@ static int in_volume(const or_scene *sc, const or_mesh *m, const float *P, int32
 /* ---------------------------------------------------------------------- */
 
 /* Score n hypotheses.  costs[2h] = J_o, costs[2h+1] = J_r.  band[h] (may be
- * NULL) = rendered points whose colour decision lies in the tolerance band.
+ * NULL) = points whose colour decision lies in the tolerance band: rendered
+ * points, and under jo_mode 1 also the observed points of V whose decision
+ * against their nearest rendered point does.
  * work[8h..8h+7] (may be NULL) = triangle set-ups, culled triangles,
  * fragments, visible pixels, kept rendered points L, delta-cell candidates
  * (observed points in the 27 cells of edge delta around q's cell), |I cap V|,
@@ -528,16 +530,32 @@ int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t 
                         continue;
                     wk[6]++;
                     if (sc->jo_mode == 1) {
-                        /* Eq. 3 as written, with OUTLIER of Eq. 2: is any rendered
-                         * point of R \ C within delta of p? */
+                        /* Eq. 3 as written: OUTLIER(p | R \ C), with Eq. 2 / Eq. 4
+                         * applied from the observed side ("or vice-versa",
+                         * Sec. IV-B): p's nearest rendered point q'' (smallest
+                         * d2, ties to the lowest pixel index -- R is listed in
+                         * pixel order) must lie within delta and, with the colour
+                         * check on, differ from p by at most tau_c. */
                         const float *p = Ixyz + 3 * j;
-                        int near = 0;
-                        for (int64_t k = 0; k < L && !near; k++) {
+                        float best = INFINITY;
+                        int64_t bk = -1;
+                        for (int64_t k = 0; k < L; k++) {
                             const float *q = Rxyz + 3 * k;
                             float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
-                            near = ((dx * dx + dy * dy) + dz * dz) <= delta2;
+                            float d2 = (dx * dx + dy * dy) + dz * dz;
+                            if (d2 < best) { best = d2; bk = k; }
                         }
-                        if (!near)
+                        int inlier = bk >= 0 && best <= delta2;
+                        if (inlier && sc->color_check) {
+                            float lq[3], gap;
+                            or_srgb_to_lab(Rrgb + 3 * bk, lq);
+                            float dE = or_ciede2000(lq, Ilab + 3 * j, &gap);
+                            if (fabsf(dE - sc->tau_c) <= 1e-3f || gap <= 1e-3f)
+                                nband++;
+                            if (dE > sc->tau_c)
+                                inlier = 0;
+                        }
+                        if (!inlier)
                             Jo++;
                     } else if (!mark[j]) {
                         Jo++;

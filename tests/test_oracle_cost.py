@@ -124,6 +124,58 @@ def test_eq3_jo_matches_kdtree(oracle, small):
         assert costs[n, 0] == int(np.sum(d > sc.params.delta_m)), h
 
 
+def test_eq3_jo_with_colour_matches_kdtree(oracle, small):
+    """jo_mode 1 with the colour check (Eq. 3 with Eq. 4 applied from the
+    observed side): p in I cap V is an inlier iff its nearest rendered point
+    (scipy's k-d tree, ties to the lower index) lies within delta and their
+    CIEDE2000 difference is at most tau_c.  Hypotheses near the ground truth,
+    where many observed points pass the distance test and the colour decides."""
+    from scipy.spatial import cKDTree
+    sc = small
+    tau = 12.5
+    osc = oracle.OracleScene.from_scene(sc, jo_mode=1, color_check=1, tau_c=tau)
+    mesh = sc.meshes[0]
+    om = oracle.OracleMesh.from_mesh(mesh)
+    req = sc.requests[0]
+    g = req.gt_index
+    pick = np.unique(np.clip(np.array([g, g - 1, g + 1, g - 8, g + 8, g - 88, g + 88, g + 3]), 0, len(req.poses) - 1))
+    costs, band = oracle.score(osc, om, req.poses[pick])
+    I, Ilab, _ = oracle.observed_points(osc)
+    colour_decided = 0
+    for n, h in enumerate(pick):
+        pose = req.poses[h]
+        keys, _ = oracle.render_keys(osc, om, pose)
+        q, qrgb, _ = oracle.rendered_points(osc, om, pose, keys)
+        R = pose.reshape(3, 4)[:, :3].astype(np.float64)
+        t = pose.reshape(3, 4)[:, 3].astype(np.float64)
+        pl = (I.astype(np.float64) - t) @ R
+        inside = np.nonzero(((pl[:, 0] ** 2 + pl[:, 1] ** 2) <= mesh.vol_radius ** 2) & (pl[:, 2] >= 0) &
+                            (pl[:, 2] <= mesh.vol_height))[0]
+        jo, amb = 0, 0
+        tree = cKDTree(q.astype(np.float64)) if len(q) else None
+        for j in inside:
+            if tree is None:
+                jo += 1
+                continue
+            d, k = tree.query(I[j].astype(np.float64), k=2)
+            kk = int(k[0])
+            if abs(d[1] - d[0]) < 1e-9:
+                kk = int(min(k[0], k[1]))
+                amb += 1
+            if abs(d[0] - sc.params.delta_m) < 1e-6:
+                amb += 1
+            ok = d[0] <= sc.params.delta_m
+            if ok:
+                dE, gap = oracle.ciede2000(oracle.srgb_to_lab(qrgb[kk]), Ilab[j])
+                if abs(dE - tau) < 1e-3 or gap < 1e-3:
+                    amb += 1
+                colour_decided += dE > tau
+                ok = dE <= tau
+            jo += not ok
+        assert abs(int(costs[n, 0]) - jo) <= amb, (h, costs[n, 0], jo, amb)
+    assert colour_decided > 0          # the colour term changed some decisions
+
+
 def _observation_from_render(oracle, sc, pose):
     """Noise-free observation made by the oracle's own renderer at `pose`."""
     blank = oracle.OracleScene(np.zeros((sc.H, sc.W), np.uint16), np.zeros((sc.H, sc.W, 3), np.uint8),

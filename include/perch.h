@@ -78,9 +78,15 @@ typedef int32_t perch_status;
  *   jo_mode          0: J_o as the J_o kernel of Sec. IV-A computes it -- an observed
  *                    point of V(O) is an inlier iff it is the nearest neighbour of a
  *                    rendered point it explains;
- *                    1: J_o as Eq. 3 writes it with the distance test of Eq. 2 -- an
- *                    observed point of V(O) is an inlier iff some rendered point of
- *                    R \ C lies within delta (colour is not used for J_o). */
+ *                    1: J_o as Eq. 3 writes it, OUTLIER(p | R \ C) with the test
+ *                    applied from the observed side ("or vice-versa", Sec. IV-B):
+ *                    an observed point p of V(O) is an inlier iff its nearest
+ *                    rendered point q of R \ C (smallest squared distance, ties to
+ *                    the lowest pixel index) lies within delta (Eq. 2) and, with
+ *                    color_check on, the CIEDE2000 difference of q's and p's
+ *                    colours is at most tau_c (Eq. 4).  Keeps a 64-bit key per
+ *                    pixel of the admissible box in shared memory (row bands of
+ *                    4 x mark_bits / 64 pixels); slower than mode 0. */
 typedef struct perch_params {
     float delta_m;
     float tau_c;

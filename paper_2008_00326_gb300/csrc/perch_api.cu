@@ -121,10 +121,14 @@ perch_status clip_roi(perch_ctx* c, const SceneRec& s, const int32_t* roi, int o
 
 int mark_words_for(const SceneRec& s, int label, const int roi[4], int cap_bits)
 {
-    long long bits = label >= 0 ? (long long)(roi[2] - roi[0]) * (roi[3] - roi[1])
-                                : (long long)s.ds.W * s.ds.H;
-    bits = std::min<long long>(bits, cap_bits);
-    bits = std::max<long long>(bits, s.ds.W);
+    // jo_mode 1 keeps a 64-bit key per pixel (its nearest rendered point)
+    // instead of a mark bit: four times the capacity, at least one image row
+    const int per_px = s.ds.jo_mode == 1 ? 64 : 1;
+    const long long cap = s.ds.jo_mode == 1 ? 4ll * cap_bits : cap_bits;
+    long long bits = per_px * (label >= 0 ? (long long)(roi[2] - roi[0]) * (roi[3] - roi[1])
+                                          : (long long)s.ds.W * s.ds.H);
+    bits = std::min<long long>(bits, cap);
+    bits = std::max<long long>(bits, (long long)per_px * s.ds.W);
     return (int)(((bits + 31) / 32 + 2) & ~1ll);   // even: keeps the later 8-byte arrays aligned
 }
 

@@ -57,7 +57,7 @@ __device__ __forceinline__ float3 srgb8_to_lab(uint32_t r8, uint32_t g8, uint32_
 }
 
 // CIEDE2000 with kL = kC = kH = 1, angles in degrees.
-__device__ float ciede2000(float3 p, float3 q)
+__device__ __forceinline__ float ciede2000(float3 p, float3 q)
 {
     const float kRad = 0.017453292519943295f;
     const float k25p7 = 6103515625.0f;
@@ -616,8 +616,9 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
 // lane's own result: the nearest observed point within delta (smallest FP32
 // squared distance, ties to the lowest pixel index) or kEmptyKey.  All 32
 // lanes must call it.
-// Admissible band of the marks bitset (used by jo_mode 1, where every
-// observed point within delta of a rendered point is marked).
+// Admissible band of the observed-side keys (jo_mode 1: for every observed
+// point of the band, the key (d2 bits << 32 | rendered pixel) of its nearest
+// rendered point within delta, kEmptyKey if none).
 struct MarkBand {
     uint32_t* marks;
     int u0, u1, v0, v1, vw;
@@ -625,8 +626,9 @@ struct MarkBand {
 
 // Candidates j, j + k, ... of a staged chunk of n against query q, folded
 // into local: the minimum (d2 bits << 32 | pixel) within delta, or kEmptyKey.
-// MARK (jo_mode 1) also marks every observed point within delta that lies in
-// the admissible band.
+// MARK (jo_mode 1) also folds the pair into the key of every observed point
+// within delta that lies in the admissible band: its nearest rendered point
+// is the smallest (d2, rendered pixel), the rendered pixel carried in q.w.
 template <bool MARK>
 __device__ __forceinline__ unsigned long long scan_staged(const DevScene& sc, const float4 q, const float4* stage,
                                                           int n, int j, int k, const MarkBand& mb,
@@ -643,8 +645,9 @@ __device__ __forceinline__ unsigned long long scan_staged(const DevScene& sc, co
                 const uint32_t pw = __float_as_uint(c.w);
                 const int pu = (int)(pw & 0xFFFFu), pv = (int)(pw >> 16);
                 if (pu >= mb.u0 && pu < mb.u1 && pv >= mb.v0 && pv < mb.v1) {
-                    const int bit = (pv - mb.v0) * mb.vw + (pu - mb.u0);
-                    atomicOr(&mb.marks[bit >> 5], 1u << (bit & 31));
+                    const int i = (pv - mb.v0) * mb.vw + (pu - mb.u0);
+                    atomicMin(reinterpret_cast<unsigned long long*>(mb.marks) + i,
+                              ((unsigned long long)__float_as_uint(d2) << 32) | __float_as_uint(q.w));
                 }
             }
         }
@@ -652,8 +655,9 @@ __device__ __forceinline__ unsigned long long scan_staged(const DevScene& sc, co
     return local;
 }
 
+template <bool MARK>
 __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float qx, float qy,
-                                          float qz, WarpProbe& W, int lane, const MarkBand& mb)
+                                          float qz, uint32_t qpix, WarpProbe& W, int lane, const MarkBand& mb)
 {
     int cx = 0, cy = 0, cz = 0;
     unsigned long long key = kEmptyKey;
@@ -668,7 +672,7 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
         }
         if (valid) key = cell_key(cx, cy, cz);
     }
-    W.q[lane] = make_float4(qx, qy, qz, 0.0f);
+    W.q[lane] = make_float4(qx, qy, qz, __uint_as_float(qpix));
     W.best[lane] = kEmptyKey;
     const unsigned grp = __match_any_sync(0xffffffffu, key);
     const int leader = __ffs(grp) - 1;
@@ -722,8 +726,7 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
                 __syncwarp();
                 const int n = min(64, T - c0);
                 if (active)
-                    local = sc.jo_mode == 1 ? scan_staged<true>(sc, q, W.stage, n, lane % k, k, mb, local)
-                                            : scan_staged<false>(sc, q, W.stage, n, lane % k, k, mb, local);
+                    local = scan_staged<MARK>(sc, q, W.stage, n, lane % k, k, mb, local);
                 __syncwarp();
             }
             if (active && local != kEmptyKey) atomicMin(&W.best[ql], local);
@@ -925,14 +928,92 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
     }
 }
 
+// Affine integer colour at pixel (u, v) of the set-up triangle o: per channel
+// (w0 c0 + w1 c1 + w2 c2 + floor(A / 2)) / A with the edge values w of the
+// pixel's sample (screen-space interpolation of the per-vertex colour, rounded
+// half up), packed r | g << 8 | b << 16.
+__device__ __forceinline__ uint32_t interp_colour(const DevMesh& m, const TriSetup& o, int u, int v)
+{
+    const int sx = 16 * u, sy = 16 * v;
+    const long long w0 = edge_fn(o.x[1], o.y[1], o.x[2], o.y[2], sx, sy);
+    const long long w1 = edge_fn(o.x[2], o.y[2], o.x[0], o.y[0], sx, sy);
+    const long long w2 = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], sx, sy);
+    const uint32_t c0 = __float_as_uint(__ldg(&m.verts[o.vid[0]].w));
+    const uint32_t c1 = __float_as_uint(__ldg(&m.verts[o.vid[1]].w));
+    const uint32_t c2 = __float_as_uint(__ldg(&m.verts[o.vid[2]].w));
+    const long long half = o.A / 2;
+    uint32_t crgb = 0;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const long long num = w0 * ((c0 >> (8 * ch)) & 255) + w1 * ((c1 >> (8 * ch)) & 255) +
+                              w2 * ((c2 >> (8 * ch)) & 255) + half;
+        crgb |= (uint32_t)(num / o.A) << (8 * ch);
+    }
+    return crgb;
+}
+
+// The pixel (v << 16 | u) of a rendered point recovered from its
+// back-projection x = ((u - cx) z) / fx, y = ((v - cy) z) / fy: x fx / z + cx
+// equals u up to a relative error of a few 2^-24 on |u - cx| plus the rounding
+// of the sum, together below 0.2 pixel for any image of at most 466033 pixels
+// a side, so rounding to the nearest integer gives u exactly (and v alike).
+__device__ __forceinline__ uint32_t recover_pixel(const DevScene& sc, float x, float y, float z)
+{
+    const int u = __float2int_rn(__fadd_rn(__fdiv_rn(__fmul_rn(x, sc.fx), z), sc.cx));
+    const int v = __float2int_rn(__fadd_rn(__fdiv_rn(__fmul_rn(y, sc.fy), z), sc.cy));
+    return ((uint32_t)v << 16) | (uint32_t)u;
+}
+
+// jo_mode 1 with the colour check (Eq. 3 with Eq. 4 applied from the observed
+// side): every observed point p of rows [mv0, mv1) of the admissible box
+// holds the key of its nearest rendered point q; p stays an inlier iff the
+// CIEDE2000 difference between q's rendered colour and p's colour is at most
+// tau_c, else its key is cleared.  This handles the p whose q lies in the
+// z-buffer tile [tu0, tu1) x [tv0, tv1) now in shared memory (q's winning
+// triangle gives its colour).
+template <int NT, bool K32, bool VC>
+__device__ __forceinline__ void jo_colour_pass(const Job& J, const float* P, const unsigned long long* vc, const ScoreSmem& S,
+                               int tu0, int tv0, int tu1, int tv1, int tw, const int* vbox, int mv0, int mv1)
+{
+    const DevScene& sc = J.sc;
+    const int vw = vbox[2] - vbox[0];
+    const int n = vw * (mv1 - mv0);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(S.marks);
+    for (int i = threadIdx.x; i < n; i += NT) {
+        const unsigned long long k = keys[i];
+        if (k == kEmptyKey) continue;
+        const uint32_t qp = (uint32_t)k;
+        const int qu = (int)(qp & 0xFFFFu), qv = (int)(qp >> 16);
+        if (qu < tu0 || qu >= tu1 || qv < tv0 || qv >= tv1) continue;
+        const int zi = (qv - tv0) * tw + (qu - tu0);
+        // q is a kept rendered point: its z-buffer word holds its triangle
+        const int tri = K32 ? (int)(S.zbuf[zi] & 0xFFFFu)
+                            : (int)(uint32_t)reinterpret_cast<const unsigned long long*>(S.zbuf)[zi];
+        TriSetup o;
+        get_triangle<VC>(sc, J.m, P, vc, tri, o);
+        const uint32_t crgb = interp_colour(J.m, o, qu, qv);
+        const int pu = vbox[0] + i % vw, pv = mv0 + i / vw;
+        const float4 lp = __ldg(&sc.lab[pv * sc.W + pu]);
+        const float3 lq = srgb8_to_lab(crgb & 255, (crgb >> 8) & 255, (crgb >> 16) & 255);
+        if (ciede2000(lq, make_float3(lp.x, lp.y, lp.z)) > sc.tau_c) keys[i] = kEmptyKey;
+    }
+}
+
+// Specialisations of the scoring kernel: plain scoring (jo_mode 0), edges of
+// the Monotone Scene Generation tree, and jo_mode 1 (Eq. 3 as written, with
+// per-pixel nearest-rendered-point keys).  Each is compiled separately so the
+// plain path carries none of the other two's code.
+enum : int { kModePlain = 0, kModeTree = 1, kModeEq3 = 2 };
+
 // Rasterise, resolve and radius-search the pixel box rbox in z-buffer tiles.
 // J_r is accumulated when count_jr; marks are set for nearest neighbours that
 // fall in rows [mv0, mv1) of the admissible box vbox.
-template <int NT, bool K32, bool VC, bool TREE>
+template <int NT, bool K32, bool VC, int MODE>
 __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, const unsigned long long* vc,
                             const int* rbox, const ScoreSmem& S, const int* vbox, int mv0, int mv1,
                             bool count_jr, int& jr_local)
 {
+    constexpr bool TREE = MODE == kModeTree, EQ3 = MODE == kModeEq3;
     const DevScene& sc = J.sc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpProbe& WP = *reinterpret_cast<WarpProbe*>(reinterpret_cast<char*>(S.probe) + warp * kWarpScratch);
@@ -1027,23 +1108,8 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                             if (!occluded) {
                                 TriSetup o;
                                 get_triangle<VC>(sc, J.m, P, vc, tri, o);
-                                int sx = 16 * u, sy = 16 * v;
-                                long long w0 = edge_fn(o.x[1], o.y[1], o.x[2], o.y[2], sx, sy);
-                                long long w1 = edge_fn(o.x[2], o.y[2], o.x[0], o.y[0], sx, sy);
-                                long long w2 = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], sx, sy);
-                                uint32_t c0 = __float_as_uint(__ldg(&J.m.verts[o.vid[0]].w));
-                                uint32_t c1 = __float_as_uint(__ldg(&J.m.verts[o.vid[1]].w));
-                                uint32_t c2 = __float_as_uint(__ldg(&J.m.verts[o.vid[2]].w));
-                                long long half = o.A / 2;
-                                uint32_t crgb = 0;
-#pragma unroll
-                                for (int ch = 0; ch < 3; ++ch) {
-                                    long long num = w0 * ((c0 >> (8 * ch)) & 255) + w1 * ((c1 >> (8 * ch)) & 255) +
-                                                    w2 * ((c2 >> (8 * ch)) & 255) + half;
-                                    crgb |= (uint32_t)(num / o.A) << (8 * ch);
-                                }
                                 float3 q = back_project(sc, u, v, d);
-                                kp.x = q.x; kp.y = q.y; kp.z = q.z; kp.rgb = crgb;
+                                kp.x = q.x; kp.y = q.y; kp.z = q.z; kp.rgb = interp_colour(J.m, o, u, v);
                                 kept = true;
                             }
                         }
@@ -1061,7 +1127,8 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                     if (valid) kq = wq[(wq_head + lane) % kWarpQueue];
                     wq_head = (wq_head + nb) % kWarpQueue;
                     wq_count -= nb;
-                    const unsigned long long nn = probe_batch(sc, valid, kq.x, kq.y, kq.z, WP, lane, mband);
+                    const uint32_t qpix = (EQ3 && valid) ? recover_pixel(sc, kq.x, kq.y, kq.z) : 0u;
+                    const unsigned long long nn = probe_batch<EQ3>(sc, valid, kq.x, kq.y, kq.z, qpix, WP, lane, mband);
                     if (valid) {
                         bool explained = nn != kEmptyKey;
                         const int pnn = (int)(uint32_t)nn;
@@ -1077,7 +1144,7 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                         }
                         if (!explained) {
                             if (count_jr) ++jr_local;
-                        } else if (sc.jo_mode == 0) {
+                        } else if (!EQ3) {
                             if (pu >= vbox[0] && pu < vbox[2] && pv >= mv0 && pv < mv1) {
                                 int bit = (pv - mv0) * vw + (pu - vbox[0]);
                                 atomicOr(&S.marks[bit >> 5], 1u << (bit & 31));
@@ -1094,12 +1161,48 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
     }
 }
 
+// jo_mode 1 with the colour check, after score_tiles has made every key of
+// the band final: the colour pass over the same z-buffer tiles.  With one
+// tile its z-buffer is still in shared memory; otherwise each tile is
+// rendered again.
+template <int NT, bool K32, bool VC>
+__device__ __noinline__ void jo_colour_band(const ScoreArgs& a, const Job& J, const float* P,
+                                            const unsigned long long* vc, const int* rbox, const ScoreSmem& S,
+                                            const int* vbox, int mv0, int mv1)
+{
+    const int warp = threadIdx.x >> 5;
+    TriStage* TS = reinterpret_cast<TriStage*>(reinterpret_cast<char*>(S.stage) + warp * kWarpScratch);
+    const int rw = rbox[2] - rbox[0], rh = rbox[3] - rbox[1];
+    if (rw <= 0 || rh <= 0) return;
+    const int cap_px = K32 ? a.zcap_words : a.zcap_words / 2;
+    const int tw = min(rw, cap_px);
+    const int th = max(1, cap_px / tw);
+    if (th >= rh) {
+        jo_colour_pass<NT, K32, VC>(J, P, vc, S, rbox[0], rbox[1], rbox[2], rbox[3], tw, vbox, mv0, mv1);
+        __syncthreads();
+        return;
+    }
+    for (int tv0 = rbox[1]; tv0 < rbox[3]; tv0 += th) {
+        for (int tu0 = rbox[0]; tu0 < rbox[2]; tu0 += tw) {
+            const int tu1 = min(tu0 + tw, rbox[2]), tv1 = min(tv0 + th, rbox[3]);
+            const int words = K32 ? tw * (tv1 - tv0) : 2 * tw * (tv1 - tv0);
+            for (int i = threadIdx.x; i < words; i += NT) S.zbuf[i] = 0xFFFFFFFFu;
+            __syncthreads();
+            raster_tile<NT, K32, VC>(J.sc, J.m, P, vc, TS, S.zbuf, tu0, tv0, tu1, tv1, tw, a.err);
+            __syncthreads();
+            jo_colour_pass<NT, K32, VC>(J, P, vc, S, tu0, tv0, tu1, tv1, tw, vbox, mv0, mv1);
+            __syncthreads();
+        }
+    }
+}
+
 // Score hypothesis h (one block).  Writes costs[2h] = J_o, costs[2h+1] = J_r.
-template <int NT, bool TREE>
+template <int NT, int MODE>
 __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const ScoreSmem& S, float* s_pose,
                           int* s_rbox, int* s_vbox, int* s_k32, int (*s_red)[NT / 32],
                           unsigned long long* vc)
 {
+    constexpr bool TREE = MODE == kModeTree;
     const DevScene& sc = J.sc;
     if (threadIdx.x < 12) s_pose[threadIdx.x] = J.poses[h * 12 + threadIdx.x];
     if (TREE && threadIdx.x == 0) *S.refused = 0;
@@ -1121,9 +1224,11 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
     __syncthreads();
 
     // The admissible box is handled in bands of rows that fit the marks
-    // bitset; each band repeats the render + search (J_r counted once).
+    // bitset (jo_mode 1: one 64-bit key per pixel); each band repeats the
+    // render + search (J_r counted once).
+    constexpr bool jo1 = MODE == kModeEq3;
     const int vw = s_vbox[2] - s_vbox[0], vh = s_vbox[3] - s_vbox[1];
-    const int band_rows = vw > 0 ? max(1, (32 * a.mark_words) / vw) : 1;
+    const int band_rows = vw > 0 ? max(1, (jo1 ? a.mark_words / 2 : 32 * a.mark_words) / vw) : 1;
     const int n_bands = vh > 0 ? (vh + band_rows - 1) / band_rows : 1;
     int jr = 0, n_in = 0, n_marked = 0;
     const int s = sc.stride;
@@ -1132,17 +1237,28 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
     for (int band = 0; band < n_bands; ++band) {
         const int mv0 = s_vbox[1] + band * band_rows;
         const int mv1 = min(mv0 + band_rows, s_vbox[3]);
-        const int mwords = (vw * max(0, mv1 - mv0) + 31) / 32;
-        for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = 0u;
+        const int mwords = jo1 ? 2 * vw * max(0, mv1 - mv0) : (vw * max(0, mv1 - mv0) + 31) / 32;
+        const uint32_t mfill = jo1 ? 0xFFFFFFFFu : 0u;     // empty keys / clear bits
+        for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = mfill;
         __syncthreads();
         if (*s_k32) {
-            if (use_vc) score_tiles<NT, true, true, TREE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, true, false, TREE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, true, true, MODE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, true, false, MODE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
         } else {
-            if (use_vc) score_tiles<NT, false, true, TREE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, false, false, TREE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, false, true, MODE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, false, false, MODE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
         }
         __syncthreads();
+        if (jo1 && sc.color_check) {
+            // Eq. 4 from the observed side, once the band's keys are final
+            if (*s_k32) {
+                if (use_vc) jo_colour_band<NT, true, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
+                else jo_colour_band<NT, true, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
+            } else {
+                if (use_vc) jo_colour_band<NT, false, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
+                else jo_colour_band<NT, false, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
+            }
+        }
         // ---- J_o over the admissible set V(h), rows [mv0, mv1)
         const int us0 = ((s_vbox[0] + s - 1) / s) * s, vs0 = ((mv0 + s - 1) / s) * s;
         const int nu = us0 < s_vbox[2] ? (s_vbox[2] - 1 - us0) / s + 1 : 0;
@@ -1170,7 +1286,8 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
                 }
                 ++n_in;
                 int bit = (v - mv0) * vw + (u - s_vbox[0]);
-                unsigned mk = (S.marks[bit >> 5] >> (bit & 31)) & 1u;
+                unsigned mk = jo1 ? (reinterpret_cast<const unsigned long long*>(S.marks)[bit] != kEmptyKey)
+                                  : (S.marks[bit >> 5] >> (bit & 31)) & 1u;
                 if (TREE && !mk) mk = (__ldg(&J.tree.mark[pix >> 5]) >> (pix & 31)) & 1u;
                 n_marked += mk;
             }
@@ -1254,9 +1371,9 @@ __device__ int claim_vslot(unsigned* mask, int nslots)
 // Persistent scoring kernel over one job: each block repeatedly takes the
 // next hypothesis index from a device counter (zero at launch) and scores
 // it.  The job is read from the kernel parameters, so its fields are
-// constant-bank operands.  TREE: the job's hypotheses are edges of the
+// constant-bank operands.  MODE kModeTree: the job's hypotheses are edges of the
 // Monotone Scene Generation tree from the state in job.tree.
-template <int NT, bool TREE>
+template <int NT, int MODE>
 __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1282,7 +1399,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
         __syncthreads();
         const long long h = s_h;
         if (h >= a.n) break;
-        score_one<NT, TREE>(a, a.job, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+        score_one<NT, MODE>(a, a.job, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
     }
     // every thread has passed the barrier after its last use of the slot
     if (threadIdx.x == 0 && s_slot >= 0) {
@@ -1296,29 +1413,45 @@ size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
     return smem_layout(cfg.zcap_words, mark_words, cfg.threads).total;
 }
 
-template <int NT, bool TREE>
+template <int NT, int MODE>
 static int score_grid_nt(size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_score<NT, TREE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(k_score<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT, TREE>, NT, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT, MODE>, NT, smem) != cudaSuccess)
         return -1;
     return max(1, per) * max(1, sms);
+}
+
+template <int NT>
+static int score_grid_all(size_t smem)
+{
+    // the three specialisations share the vertex-cache pool: size for the smallest
+    return min(score_grid_nt<NT, kModePlain>(smem),
+               min(score_grid_nt<NT, kModeTree>(smem), score_grid_nt<NT, kModeEq3>(smem)));
 }
 
 int score_grid(const ScoreConfig& cfg, int mark_words)
 {
     size_t smem = score_smem_bytes(cfg, mark_words);
-    // the plain and the tree kernels share the vertex-cache pool: size for the smaller
     switch (cfg.threads) {
-    case 128: return min(score_grid_nt<128, false>(smem), score_grid_nt<128, true>(smem));
-    case 512: return min(score_grid_nt<512, false>(smem), score_grid_nt<512, true>(smem));
-    default: return min(score_grid_nt<256, false>(smem), score_grid_nt<256, true>(smem));
+    case 128: return score_grid_all<128>(smem);
+    case 512: return score_grid_all<512>(smem);
+    default: return score_grid_all<256>(smem);
     }
+}
+
+// The kernel specialisation a job runs on.
+template <int NT>
+static const void* score_kernel(const Job& j)
+{
+    if (j.tree.depth) return (const void*)k_score<NT, kModeTree>;
+    if (j.sc.jo_mode == 1) return (const void*)k_score<NT, kModeEq3>;
+    return (const void*)k_score<NT, kModePlain>;
 }
 
 template <int NT>
@@ -1326,16 +1459,12 @@ static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, i
 {
     const size_t smem = score_smem_bytes(cfg, a.mark_words);
     const unsigned g = (unsigned)(a.n < grid ? a.n : grid);
-    if (a.job.tree.depth) {
-        cudaError_t e = cudaFuncSetAttribute(k_score<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_score<NT, true><<<g, NT, smem, s>>>(a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_score<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_score<NT, false><<<g, NT, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    const void* fn = score_kernel<NT>(a.job);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ScoreArgs copy = a;
+    void* args[] = {&copy};
+    return cudaLaunchKernel(fn, dim3(g), dim3(NT), args, smem, s);
 }
 
 template <int NT>
@@ -1344,12 +1473,13 @@ static cudaError_t add_score_node_nt(cudaGraph_t g, const cudaGraphNode_t* deps,
                                      cudaGraphNode_t* out)
 {
     const size_t smem = score_smem_bytes(cfg, a.mark_words);
-    cudaError_t e = cudaFuncSetAttribute(k_score<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void* fn = score_kernel<NT>(a.job);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ScoreArgs copy = a;
     void* args[] = {&copy};
     cudaKernelNodeParams kp{};
-    kp.func = (void*)k_score<NT, false>;
+    kp.func = const_cast<void*>(fn);
     kp.gridDim = dim3((unsigned)(a.n < grid ? a.n : grid));
     kp.blockDim = dim3(NT);
     kp.sharedMemBytes = (unsigned)smem;
@@ -1763,7 +1893,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_gicp(GicpArgs a)
                 const float3 r0 = rotate_rn(s_Rf, 3, A.x, A.y, A.z);
                 const float3 p = make_float3(__fadd_rn(r0.x, s_tf[0]), __fadd_rn(r0.y, s_tf[1]),
                                              __fadd_rn(r0.z, s_tf[2]));
-                const unsigned long long nn = probe_batch(sc, valid, p.x, p.y, p.z, WP, lane, nomark);
+                const unsigned long long nn = probe_batch<false>(sc, valid, p.x, p.y, p.z, 0u, WP, lane, nomark);
                 bool ok = valid && nn != kEmptyKey;
                 float terms[kGicpTerms];
                 if (ok) {

@@ -163,24 +163,38 @@ def test_variant_without_occluder_marking(ctx, oracle):
 
 
 @pytest.mark.parametrize("colour", [0, 1])
-def test_eq3_exact_jo(ctx, oracle, colour):
-    """jo_mode 1: J_o as Eq. 3 writes it, with the distance test of Eq. 2."""
-    sc = scenes.tabletop_3obj(W=320, H=240, grid_half=3, n_yaw=4, tri_scale=0.25)
-    sc.params.jo_mode = 1
-    sc.params.color_check = colour
-    sid, mids = _load(ctx, sc)
-    for req in sc.requests:
-        got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
-        want, band = oracle.score(*_oracle(oracle, sc, req), req.poses, label=req.label, roi=req.roi)
-        assert np.array_equal(got[:, 0], want[:, 0])
-        assert_within_band(got, want, band, f"jo_mode 1 mesh {req.mesh_index}")
-    sc6 = scenes.sixdof_5obj(n_hyp=16, W=320, H=240, tri_scale=0.1)
-    sc6.params.jo_mode = 1
-    sid, mids = _load(ctx, sc6)
-    for req in sc6.requests:
-        got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
-        want, band = oracle.score(*_oracle(oracle, sc6, req), req.poses, label=req.label, roi=req.roi)
-        assert np.array_equal(got[:, 0], want[:, 0])
+@pytest.mark.parametrize("shape", [(256, 8192, 0), (128, 2048, 4096)])
+def test_eq3_exact_jo(ctx, oracle, colour, shape):
+    """jo_mode 1: J_o as Eq. 3 writes it -- each observed point of V against
+    its own nearest rendered point, with the distance test of Eq. 2 and, with
+    the colour check on, Eq. 4 applied from the observed side.  Colour off:
+    bit-exact; colour on: within the band.  The second launch shape forces
+    several z-buffer tiles (the colour pass renders them again) and several
+    bands of the admissible box."""
+    ctx.set_launch_config(*shape)
+    try:
+        sc = scenes.tabletop_3obj(W=320, H=240, grid_half=3, n_yaw=4, tri_scale=0.25)
+        sc.params.jo_mode = 1
+        sc.params.color_check = colour
+        sid, mids = _load(ctx, sc)
+        for req in sc.requests:
+            got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
+            want, band = oracle.score(*_oracle(oracle, sc, req), req.poses, label=req.label, roi=req.roi)
+            if colour == 0:
+                assert np.array_equal(got, want)
+            assert_within_band(got, want, band, f"jo_mode 1 mesh {req.mesh_index}")
+        sc6 = scenes.sixdof_5obj(n_hyp=16, W=320, H=240, tri_scale=0.1)
+        sc6.params.jo_mode = 1
+        sc6.params.color_check = colour
+        sid, mids = _load(ctx, sc6)
+        for req in sc6.requests:
+            got = ctx.score(sid, mids[req.mesh_index], req.label, req.roi, req.poses)
+            want, band = oracle.score(*_oracle(oracle, sc6, req), req.poses, label=req.label, roi=req.roi)
+            if colour == 0:
+                assert np.array_equal(got, want)
+            assert_within_band(got, want, band, f"jo_mode 1 6-DoF mesh {req.mesh_index}")
+    finally:
+        ctx.set_launch_config(256, 8192)
 
 
 @pytest.mark.parametrize("stride", [2, 3])

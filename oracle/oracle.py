@@ -63,6 +63,7 @@ def lib():
         L.or_rendered_points.argtypes = [P, P, P, C.c_int32, P, P, P, P]
         L.or_rendered_points.restype = C.c_int64
         L.or_score.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, C.c_int32]
+        L.or_score_nn.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, C.c_int32, C.c_int32]
         L.or_best.argtypes = [P, P, C.c_int64, P, P]
         L.or_srgb_to_lab.argtypes = [P, P]
         L.or_ciede2000.argtypes = [P, P, P]
@@ -155,16 +156,21 @@ def rendered_points(scene: OracleScene, mesh: OracleMesh, pose, keys, label=-1):
 
 
 def score(scene: OracleScene, mesh: OracleMesh, poses, label=-1, roi=None, threads=0,
-          with_work=False):
-    """(costs (n,2) int32 [J_o, J_r], band (n,) int32[, work (n,8) int64])."""
+          with_work=False, nn="brute"):
+    """(costs (n,2) int32 [J_o, J_r], band (n,) int32[, work (n,8) int64]).
+    nn: "brute" scans all of the other cloud for each nearest neighbour (Eq. 2
+    as written); "grid" scans the 5x5x5 cells of edge delta around the query
+    (the same neighbour within delta, far faster; pinned equal to "brute")."""
+    if nn not in ("brute", "grid"):
+        raise ValueError(nn)
     poses = np.ascontiguousarray(poses, np.float32).reshape(-1, 12)
     n = poses.shape[0]
     roi = np.asarray(roi if roi is not None else (0, 0, scene.W, scene.H), np.int32)
     costs = np.zeros((n, 2), np.int32)
     band = np.zeros(n, np.int32)
     work = np.zeros((n, NWORK), np.int64) if with_work else None
-    rc = lib().or_score(C.byref(scene.s), C.byref(mesh.m), label, _ptr(roi), _ptr(poses), n,
-                        _ptr(costs), _ptr(band), _ptr(work), threads)
+    rc = lib().or_score_nn(C.byref(scene.s), C.byref(mesh.m), label, _ptr(roi), _ptr(poses), n,
+                           _ptr(costs), _ptr(band), _ptr(work), threads, 1 if nn == "grid" else 0)
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return (costs, band, work) if with_work else (costs, band)

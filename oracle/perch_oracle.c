@@ -427,6 +427,143 @@ static int in_volume(const or_scene *sc, const or_mesh *m, const float *P, int32
 }
 
 /* ---------------------------------------------------------------------- */
+/* nearest neighbours: brute force (Eq. 2 as written) or a uniform grid     */
+/* ---------------------------------------------------------------------- */
+/*
+ * The grid mode finds the same nearest neighbour as the brute-force scan in
+ * far less time, so that whole configurations can be checked:
+ *   cells of edge delta, cell coordinate floorf(x / delta) per axis; the
+ *   points sorted by (cell z, cell y, cell x, index); a query looks at the
+ *   5 x 5 x 5 cells around its own.
+ * Why that is exact: a point p with fl(d2) <= fl(delta^2) lies within
+ * delta (1 + 2^-20) of q on every axis, and fl(x / delta) is within
+ * |x / delta| 2^-24 < 2^-4 of x / delta for the coordinates accepted here
+ * (|x / delta| < 2^20), so the cell coordinates of q and p differ by at most
+ * 2.  Hence the nearest point within delta, if there is one, is among the
+ * candidates and is their minimum (same d2 expression, same tie rule: the
+ * lowest index); if there is none, no candidate passes the delta test
+ * either.  Clouds with a larger coordinate fall back to the brute force.
+ */
+#define OR_GRID_BIAS (1 << 20)
+
+typedef struct {
+    int64_t key, idx;
+} or_cell_entry;
+
+typedef struct {
+    or_cell_entry *e;          /* n entries sorted by (key, idx)            */
+    int64_t n;
+    int usable;                /* 0: some |x / delta| too large, brute force */
+} or_grid;
+
+static int64_t or_cell_key(int64_t cx, int64_t cy, int64_t cz)
+{
+    return ((cz + OR_GRID_BIAS) << 42) | ((cy + OR_GRID_BIAS) << 21) | (cx + OR_GRID_BIAS);
+}
+
+static int or_cmp_entry(const void *a, const void *b)
+{
+    const or_cell_entry *x = a, *y = b;
+    if (x->key != y->key)
+        return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static int or_cell_of(float x, float delta, int32_t *c)
+{
+    float t = x / delta;
+    if (!(fabsf(t) < (float)(OR_GRID_BIAS - 8)))
+        return 0;
+    *c = (int32_t)floorf(t);
+    return 1;
+}
+
+/* Build the grid of n points (xyz) into g->e (capacity n). */
+static void or_grid_build(or_grid *g, const float *xyz, int64_t n, float delta)
+{
+    g->n = n;
+    g->usable = 1;
+    for (int64_t j = 0; j < n && g->usable; j++) {
+        int32_t c[3];
+        for (int a = 0; a < 3 && g->usable; a++)
+            g->usable = or_cell_of(xyz[3 * j + a], delta, &c[a]);
+        if (g->usable) {
+            g->e[j].key = or_cell_key(c[0], c[1], c[2]);
+            g->e[j].idx = j;
+        }
+    }
+    if (g->usable)
+        qsort(g->e, (size_t)n, sizeof(or_cell_entry), or_cmp_entry);
+}
+
+/* First entry with key >= k. */
+static int64_t or_lower_bound(const or_grid *g, int64_t k)
+{
+    int64_t lo = 0, hi = g->n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (g->e[mid].key < k)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+/* Nearest point of the cloud xyz (n points) to q: smallest
+ * d2 = (dx dx + dy dy) + dz dz, ties to the lowest index; returns its index
+ * (-1 for an empty cloud) and its d2 in *best_d2.  With a usable grid only
+ * the 5 x 5 x 5 cells around q are scanned (exact for every point within
+ * delta, see above); otherwise every point.  cand27 (may be NULL) counts the
+ * points in the 27 cells of edge delta around q's cell. */
+static int64_t or_nearest(const float *xyz, int64_t n, const or_grid *g, const int32_t *cells,
+                          const float q[3], float delta, float *best_d2, int64_t *cand27)
+{
+    float best = INFINITY;
+    int64_t bj = -1;
+    int32_t qc[3];
+    int use_grid = g && g->usable && or_cell_of(q[0], delta, &qc[0]) && or_cell_of(q[1], delta, &qc[1]) &&
+                   or_cell_of(q[2], delta, &qc[2]);
+    if (!use_grid) {
+        /* cells (may be NULL): the points' floorf(x / delta), for the count */
+        int32_t c0 = (int32_t)floorf(q[0] / delta), c1 = (int32_t)floorf(q[1] / delta),
+                c2 = (int32_t)floorf(q[2] / delta);
+        for (int64_t j = 0; j < n; j++) {
+            const float *p = xyz + 3 * j;
+            float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
+            float d2 = (dx * dx + dy * dy) + dz * dz;
+            if (d2 < best) { best = d2; bj = j; }
+            if (cand27 && cells) {
+                const int32_t *pc = cells + 3 * j;
+                if (abs(pc[0] - c0) <= 1 && abs(pc[1] - c1) <= 1 && abs(pc[2] - c2) <= 1)
+                    (*cand27)++;
+            }
+        }
+        *best_d2 = best;
+        return bj;
+    }
+    for (int dz = -2; dz <= 2; dz++)
+        for (int dy = -2; dy <= 2; dy++) {
+            int64_t k0 = or_cell_key(qc[0] - 2, qc[1] + dy, qc[2] + dz);
+            int64_t k1 = or_cell_key(qc[0] + 2, qc[1] + dy, qc[2] + dz);
+            for (int64_t i = or_lower_bound(g, k0); i < g->n && g->e[i].key <= k1; i++) {
+                int64_t j = g->e[i].idx;
+                const float *p = xyz + 3 * j;
+                float dx = q[0] - p[0], dy2 = q[1] - p[1], dz2 = q[2] - p[2];
+                float d2 = (dx * dx + dy2 * dy2) + dz2 * dz2;
+                if (d2 < best || (d2 == best && j < bj)) { best = d2; bj = j; }
+                if (cand27 && dz >= -1 && dz <= 1 && dy >= -1 && dy <= 1) {
+                    int64_t cx = (g->e[i].key & ((1 << 21) - 1)) - OR_GRID_BIAS;
+                    if (cx >= qc[0] - 1 && cx <= qc[0] + 1)
+                        (*cand27)++;
+                }
+            }
+        }
+    *best_d2 = best;
+    return bj;
+}
+
+/* ---------------------------------------------------------------------- */
 /* scoring                                                                 */
 /* ---------------------------------------------------------------------- */
 
@@ -438,22 +575,31 @@ static int in_volume(const or_scene *sc, const or_mesh *m, const float *P, int32
  * fragments, visible pixels, kept rendered points L, delta-cell candidates
  * (observed points in the 27 cells of edge delta around q's cell), |I cap V|,
  * explained points.  n_threads <= 0 uses the OpenMP default. */
-int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t roi[4],
-             const float *poses, int64_t n, int32_t *costs, int32_t *band, int64_t *work,
-             int32_t n_threads)
+int or_score_nn(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t roi[4],
+                const float *poses, int64_t n, int32_t *costs, int32_t *band, int64_t *work,
+                int32_t n_threads, int32_t grid)
 {
     int64_t WH = (int64_t)sc->W * sc->H;
     float *Ixyz = malloc(sizeof(float) * 3 * (WH + 1));
     float *Ilab = malloc(sizeof(float) * 3 * (WH + 1));
     int32_t *Ipix = malloc(sizeof(int32_t) * (WH + 1));
-    int32_t *Icell = malloc(sizeof(int32_t) * 3 * (WH + 1));
-    if (!Ixyz || !Ilab || !Ipix || !Icell) {
-        free(Ixyz); free(Ilab); free(Ipix); free(Icell);
+    or_grid Ig = {NULL, 0, 0};
+    if (grid)
+        Ig.e = malloc(sizeof(or_cell_entry) * (WH + 1));
+    if (!Ixyz || !Ilab || !Ipix || (grid && !Ig.e)) {
+        free(Ixyz); free(Ilab); free(Ipix); free(Ig.e);
         return -2;
     }
     int64_t nI = or_observed_points(sc, Ixyz, Ilab, Ipix);
+    int32_t *Icell = malloc(sizeof(int32_t) * 3 * (nI + 1));
+    if (!Icell) {
+        free(Ixyz); free(Ilab); free(Ipix); free(Ig.e);
+        return -2;
+    }
     for (int64_t j = 0; j < 3 * nI; j++)
         Icell[j] = (int32_t)floorf(Ixyz[j] / sc->delta);
+    if (grid)
+        or_grid_build(&Ig, Ixyz, nI, sc->delta);
     float delta2 = sc->delta * sc->delta;
     int rc = 0;
 #ifdef _OPENMP
@@ -469,7 +615,10 @@ int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t 
         uint8_t *Rrgb = malloc(3 * WH);
         int32_t *Rpix = malloc(sizeof(int32_t) * WH);
         uint8_t *mark = malloc(nI + 1);
-        int ok = keys && Rxyz && Rrgb && Rpix && mark;
+        or_grid Rg = {NULL, 0, 0};
+        if (grid && sc->jo_mode == 1)
+            Rg.e = malloc(sizeof(or_cell_entry) * (WH + 1));
+        int ok = keys && Rxyz && Rrgb && Rpix && mark && (!(grid && sc->jo_mode == 1) || Rg.e);
         if (!ok) {
 #pragma omp atomic write
             rc = -2;
@@ -491,21 +640,9 @@ int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t 
                 int32_t Jr = 0, nband = 0;
                 for (int64_t k = 0; k < L; k++) {
                     const float *q = Rxyz + 3 * k;
-                    int32_t qc0 = (int32_t)floorf(q[0] / sc->delta);
-                    int32_t qc1 = (int32_t)floorf(q[1] / sc->delta);
-                    int32_t qc2 = (int32_t)floorf(q[2] / sc->delta);
-                    float best = INFINITY;
-                    int64_t bj = -1;
+                    float best;
                     /* Eq. 2: nearest neighbour over all of I, ties to lowest index */
-                    for (int64_t j = 0; j < nI; j++) {
-                        const float *p = Ixyz + 3 * j;
-                        float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
-                        float d2 = (dx * dx + dy * dy) + dz * dz;
-                        if (d2 < best) { best = d2; bj = j; }
-                        const int32_t *pc = Icell + 3 * j;
-                        if (abs(pc[0] - qc0) <= 1 && abs(pc[1] - qc1) <= 1 && abs(pc[2] - qc2) <= 1)
-                            wk[5]++;
-                    }
+                    int64_t bj = or_nearest(Ixyz, nI, grid ? &Ig : NULL, Icell, q, sc->delta, &best, &wk[5]);
                     int explained = bj >= 0 && best <= delta2;
                     if (explained && sc->color_check) {
                         /* Eq. 4: colour of q against its nearest neighbour p'' */
@@ -525,6 +662,8 @@ int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t 
                     }
                 }
                 int32_t Jo = 0;
+                if (grid && sc->jo_mode == 1)
+                    or_grid_build(&Rg, Rxyz, L, sc->delta);
                 for (int64_t j = 0; j < nI; j++) {
                     if (!in_volume(sc, m, P, label, roi, Ipix[j], Ixyz + 3 * j))
                         continue;
@@ -537,14 +676,8 @@ int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t 
                          * pixel order) must lie within delta and, with the colour
                          * check on, differ from p by at most tau_c. */
                         const float *p = Ixyz + 3 * j;
-                        float best = INFINITY;
-                        int64_t bk = -1;
-                        for (int64_t k = 0; k < L; k++) {
-                            const float *q = Rxyz + 3 * k;
-                            float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
-                            float d2 = (dx * dx + dy * dy) + dz * dz;
-                            if (d2 < best) { best = d2; bk = k; }
-                        }
+                        float best;
+                        int64_t bk = or_nearest(Rxyz, L, grid ? &Rg : NULL, NULL, p, sc->delta, &best, NULL);
                         int inlier = bk >= 0 && best <= delta2;
                         if (inlier && sc->color_check) {
                             float lq[3], gap;
@@ -568,10 +701,18 @@ int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t 
                     memcpy(work + OR_NWORK * h, wk, sizeof(wk));
             }
         }
-        free(keys); free(Rxyz); free(Rrgb); free(Rpix); free(mark);
+        free(keys); free(Rxyz); free(Rrgb); free(Rpix); free(mark); free(Rg.e);
     }
-    free(Ixyz); free(Ilab); free(Ipix); free(Icell);
+    free(Ixyz); free(Ilab); free(Ipix); free(Icell); free(Ig.e);
     return rc;
+}
+
+/* or_score_nn with the brute-force nearest neighbours (Eq. 2 as written). */
+int or_score(const or_scene *sc, const or_mesh *m, int32_t label, const int32_t roi[4],
+             const float *poses, int64_t n, int32_t *costs, int32_t *band, int64_t *work,
+             int32_t n_threads)
+{
+    return or_score_nn(sc, m, label, roi, poses, n, costs, band, work, n_threads, 0);
 }
 
 /* C12: J = J_o + J_r; best = minimum J, ties to the lowest id (ids NULL: the

@@ -159,8 +159,9 @@ def score(scene: OracleScene, mesh: OracleMesh, poses, label=-1, roi=None, threa
           with_work=False, nn="brute"):
     """(costs (n,2) int32 [J_o, J_r], band (n,) int32[, work (n,8) int64]).
     nn: "brute" scans all of the other cloud for each nearest neighbour (Eq. 2
-    as written); "grid" scans the 5x5x5 cells of edge delta around the query
-    (the same neighbour within delta, far faster; pinned equal to "brute")."""
+    as written); "grid" scans the 27 cells of edge delta (1 + 1/32) around the
+    query (the same neighbour within delta, far faster; pinned equal to
+    "brute"; work column 5, the delta-cell candidates, is left at 0)."""
     if nn not in ("brute", "grid"):
         raise ValueError(nn)
     poses = np.ascontiguousarray(poses, np.float32).reshape(-1, 12)

@@ -432,28 +432,34 @@ static int in_volume(const or_scene *sc, const or_mesh *m, const float *P, int32
 /*
  * The grid mode finds the same nearest neighbour as the brute-force scan in
  * far less time, so that whole configurations can be checked:
- *   cells of edge delta, cell coordinate floorf(x / delta) per axis; the
- *   points sorted by (cell z, cell y, cell x, index); a query looks at the
- *   5 x 5 x 5 cells around its own.
+ *   cells of edge h = delta (1 + 1/32), cell coordinate floorf(x / h) per
+ *   axis; the points (copied) sorted by (cell z, cell y, cell x, index); a
+ *   query scans the 3 x 3 x 3 cells around its own.
  * Why that is exact: a point p with fl(d2) <= fl(delta^2) lies within
- * delta (1 + 2^-20) of q on every axis, and fl(x / delta) is within
- * |x / delta| 2^-24 < 2^-4 of x / delta for the coordinates accepted here
- * (|x / delta| < 2^20), so the cell coordinates of q and p differ by at most
- * 2.  Hence the nearest point within delta, if there is one, is among the
- * candidates and is their minimum (same d2 expression, same tie rule: the
- * lowest index); if there is none, no candidate passes the delta test
- * either.  Clouds with a larger coordinate fall back to the brute force.
+ * delta (1 + 2^-20) of q on every axis; fl(x / h) is within 2^-8 of x / h
+ * for the coordinates accepted here (|x / h| < 2^16), so the cell
+ * coordinates of q and p differ by at most
+ * floor((1 + 2^-20) / ((1 + 1/32)(1 - 2^-24)) + 2^-7) = floor(0.978) + 1,
+ * i.e. by at most one.  Hence the nearest point within delta, if there is
+ * one, is among the candidates and is their minimum (same d2 expression, same
+ * tie rule: the lowest index); if there is none, no candidate passes the
+ * delta test either.  Clouds with a larger coordinate fall back to the brute
+ * force.  (The work counter of delta-cell candidates is the brute force's
+ * alone.)
  */
 #define OR_GRID_BIAS (1 << 20)
+#define OR_GRID_LIMIT 65528.0f       /* |x / h| bound, 2^16 - 8 */
 
 typedef struct {
     int64_t key, idx;
+    float p[3];                /* the point, copied: the scan reads it in cell order */
 } or_cell_entry;
 
 typedef struct {
     or_cell_entry *e;          /* n entries sorted by (key, idx)            */
     int64_t n;
-    int usable;                /* 0: some |x / delta| too large, brute force */
+    int usable;                /* 0: some |x / h| too large, brute force    */
+    float h;                   /* cell edge                                 */
 } or_grid;
 
 static int64_t or_cell_key(int64_t cx, int64_t cy, int64_t cz)
@@ -469,10 +475,10 @@ static int or_cmp_entry(const void *a, const void *b)
     return x->idx < y->idx ? -1 : (x->idx > y->idx);
 }
 
-static int or_cell_of(float x, float delta, int32_t *c)
+static int or_cell_of(float x, float h, int32_t *c)
 {
-    float t = x / delta;
-    if (!(fabsf(t) < (float)(OR_GRID_BIAS - 8)))
+    float t = x / h;
+    if (!(fabsf(t) < OR_GRID_LIMIT))
         return 0;
     *c = (int32_t)floorf(t);
     return 1;
@@ -482,19 +488,32 @@ static int or_cell_of(float x, float delta, int32_t *c)
 static void or_grid_build(or_grid *g, const float *xyz, int64_t n, float delta)
 {
     g->n = n;
-    g->usable = 1;
+    g->h = delta * 1.03125f;
+    g->usable = g->h > 0.0f;
     for (int64_t j = 0; j < n && g->usable; j++) {
         int32_t c[3];
         for (int a = 0; a < 3 && g->usable; a++)
-            g->usable = or_cell_of(xyz[3 * j + a], delta, &c[a]);
+            g->usable = or_cell_of(xyz[3 * j + a], g->h, &c[a]);
         if (g->usable) {
             g->e[j].key = or_cell_key(c[0], c[1], c[2]);
             g->e[j].idx = j;
+            g->e[j].p[0] = xyz[3 * j];
+            g->e[j].p[1] = xyz[3 * j + 1];
+            g->e[j].p[2] = xyz[3 * j + 2];
         }
     }
     if (g->usable)
         qsort(g->e, (size_t)n, sizeof(or_cell_entry), or_cmp_entry);
 }
+
+/* The 9 row ranges [lo, hi) of the sorted entries around the last query
+ * cell, reused while consecutive queries fall in the same cell (the
+ * rendered points come in pixel order, so most do). */
+typedef struct {
+    int valid;
+    int32_t qc[3];
+    int64_t lo[9], hi[9];
+} or_grid_cache;
 
 /* First entry with key >= k. */
 static int64_t or_lower_bound(const or_grid *g, int64_t k)
@@ -513,19 +532,19 @@ static int64_t or_lower_bound(const or_grid *g, int64_t k)
 /* Nearest point of the cloud xyz (n points) to q: smallest
  * d2 = (dx dx + dy dy) + dz dz, ties to the lowest index; returns its index
  * (-1 for an empty cloud) and its d2 in *best_d2.  With a usable grid only
- * the 5 x 5 x 5 cells around q are scanned (exact for every point within
- * delta, see above); otherwise every point.  cand27 (may be NULL) counts the
- * points in the 27 cells of edge delta around q's cell. */
-static int64_t or_nearest(const float *xyz, int64_t n, const or_grid *g, const int32_t *cells,
-                          const float q[3], float delta, float *best_d2, int64_t *cand27)
+ * the 3 x 3 x 3 cells around q are scanned (exact for every point within
+ * delta, see above); otherwise every point, and then cand27 (may be NULL)
+ * counts the points whose cells (cells: floorf(x / delta) per point) are
+ * within one of q's on every axis. */
+static int64_t or_nearest(const float *xyz, int64_t n, const or_grid *g, or_grid_cache *gc,
+                          const int32_t *cells, const float q[3], float delta, float *best_d2, int64_t *cand27)
 {
     float best = INFINITY;
     int64_t bj = -1;
     int32_t qc[3];
-    int use_grid = g && g->usable && or_cell_of(q[0], delta, &qc[0]) && or_cell_of(q[1], delta, &qc[1]) &&
-                   or_cell_of(q[2], delta, &qc[2]);
+    int use_grid = g && g->usable && or_cell_of(q[0], g->h, &qc[0]) && or_cell_of(q[1], g->h, &qc[1]) &&
+                   or_cell_of(q[2], g->h, &qc[2]);
     if (!use_grid) {
-        /* cells (may be NULL): the points' floorf(x / delta), for the count */
         int32_t c0 = (int32_t)floorf(q[0] / delta), c1 = (int32_t)floorf(q[1] / delta),
                 c2 = (int32_t)floorf(q[2] / delta);
         for (int64_t j = 0; j < n; j++) {
@@ -542,22 +561,22 @@ static int64_t or_nearest(const float *xyz, int64_t n, const or_grid *g, const i
         *best_d2 = best;
         return bj;
     }
-    for (int dz = -2; dz <= 2; dz++)
-        for (int dy = -2; dy <= 2; dy++) {
-            int64_t k0 = or_cell_key(qc[0] - 2, qc[1] + dy, qc[2] + dz);
-            int64_t k1 = or_cell_key(qc[0] + 2, qc[1] + dy, qc[2] + dz);
-            for (int64_t i = or_lower_bound(g, k0); i < g->n && g->e[i].key <= k1; i++) {
-                int64_t j = g->e[i].idx;
-                const float *p = xyz + 3 * j;
-                float dx = q[0] - p[0], dy2 = q[1] - p[1], dz2 = q[2] - p[2];
-                float d2 = (dx * dx + dy2 * dy2) + dz2 * dz2;
-                if (d2 < best || (d2 == best && j < bj)) { best = d2; bj = j; }
-                if (cand27 && dz >= -1 && dz <= 1 && dy >= -1 && dy <= 1) {
-                    int64_t cx = (g->e[i].key & ((1 << 21) - 1)) - OR_GRID_BIAS;
-                    if (cx >= qc[0] - 1 && cx <= qc[0] + 1)
-                        (*cand27)++;
-                }
-            }
+    if (!gc->valid || gc->qc[0] != qc[0] || gc->qc[1] != qc[1] || gc->qc[2] != qc[2]) {
+        for (int r = 0; r < 9; r++) {
+            int dz = r / 3 - 1, dy = r % 3 - 1;
+            gc->lo[r] = or_lower_bound(g, or_cell_key(qc[0] - 1, qc[1] + dy, qc[2] + dz));
+            gc->hi[r] = or_lower_bound(g, or_cell_key(qc[0] + 1, qc[1] + dy, qc[2] + dz) + 1);
+        }
+        gc->valid = 1;
+        gc->qc[0] = qc[0]; gc->qc[1] = qc[1]; gc->qc[2] = qc[2];
+    }
+    for (int r = 0; r < 9; r++)
+        for (int64_t i = gc->lo[r]; i < gc->hi[r]; i++) {
+            int64_t j = g->e[i].idx;
+            const float *p = g->e[i].p;
+            float dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
+            float d2 = (dx * dx + dy * dy) + dz * dz;
+            if (d2 < best || (d2 == best && j < bj)) { best = d2; bj = j; }
         }
     *best_d2 = best;
     return bj;
@@ -583,7 +602,7 @@ int or_score_nn(const or_scene *sc, const or_mesh *m, int32_t label, const int32
     float *Ixyz = malloc(sizeof(float) * 3 * (WH + 1));
     float *Ilab = malloc(sizeof(float) * 3 * (WH + 1));
     int32_t *Ipix = malloc(sizeof(int32_t) * (WH + 1));
-    or_grid Ig = {NULL, 0, 0};
+    or_grid Ig = {NULL, 0, 0, 0.0f};
     if (grid)
         Ig.e = malloc(sizeof(or_cell_entry) * (WH + 1));
     if (!Ixyz || !Ilab || !Ipix || (grid && !Ig.e)) {
@@ -615,7 +634,7 @@ int or_score_nn(const or_scene *sc, const or_mesh *m, int32_t label, const int32
         uint8_t *Rrgb = malloc(3 * WH);
         int32_t *Rpix = malloc(sizeof(int32_t) * WH);
         uint8_t *mark = malloc(nI + 1);
-        or_grid Rg = {NULL, 0, 0};
+        or_grid Rg = {NULL, 0, 0, 0.0f};
         if (grid && sc->jo_mode == 1)
             Rg.e = malloc(sizeof(or_cell_entry) * (WH + 1));
         int ok = keys && Rxyz && Rrgb && Rpix && mark && (!(grid && sc->jo_mode == 1) || Rg.e);
@@ -638,11 +657,12 @@ int or_score_nn(const or_scene *sc, const or_mesh *m, int32_t label, const int32
                 wk[4] = L;
                 memset(mark, 0, nI + 1);
                 int32_t Jr = 0, nband = 0;
+                or_grid_cache gcache = {0}, rcache = {0};
                 for (int64_t k = 0; k < L; k++) {
                     const float *q = Rxyz + 3 * k;
                     float best;
                     /* Eq. 2: nearest neighbour over all of I, ties to lowest index */
-                    int64_t bj = or_nearest(Ixyz, nI, grid ? &Ig : NULL, Icell, q, sc->delta, &best, &wk[5]);
+                    int64_t bj = or_nearest(Ixyz, nI, grid ? &Ig : NULL, &gcache, Icell, q, sc->delta, &best, &wk[5]);
                     int explained = bj >= 0 && best <= delta2;
                     if (explained && sc->color_check) {
                         /* Eq. 4: colour of q against its nearest neighbour p'' */
@@ -677,7 +697,7 @@ int or_score_nn(const or_scene *sc, const or_mesh *m, int32_t label, const int32
                          * check on, differ from p by at most tau_c. */
                         const float *p = Ixyz + 3 * j;
                         float best;
-                        int64_t bk = or_nearest(Rxyz, L, grid ? &Rg : NULL, NULL, p, sc->delta, &best, NULL);
+                        int64_t bk = or_nearest(Rxyz, L, grid ? &Rg : NULL, &rcache, NULL, p, sc->delta, &best, NULL);
                         int inlier = bk >= 0 && best <= delta2;
                         if (inlier && sc->color_check) {
                             float lq[3], gap;

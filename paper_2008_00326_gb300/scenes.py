@@ -15,8 +15,9 @@ Workloads (the paper's datasets are not available; these stand in for them):
 * ``tabletop_3obj``   - 3-DoF, an ellipsoid (20k triangles) and two cylinders of
   the same shape but different colour (10k triangles each) on a table, 640x480,
   fx=fy=615, depth noise N(0, 3 mm), 20 % random occluder pixels, 43x43
-  positions (1 cm) x 16 yaws = 29,584 hypotheses per object, colour check on.
-  (Sec. VI-A: same-shape objects of different colour, occlusion.)
+  positions (1 cm) x 16 yaws = 29,584 hypotheses per object around the ground
+  truth (on the grid), colour check on.  (Sec. VI-A: same-shape objects of
+  different colour, occlusion.)
 * ``sixdof_5obj``     - 6-DoF, five 30k-triangle meshes at 0.7-1.0 m in front of
   a wall, labels from perturbed ground-truth masks, ROI = mask bounding box,
   4,096 hypotheses per object = GT + N(0, 2 cm) translation + N(0, 15 deg)
@@ -119,14 +120,20 @@ def colour_gradient(extent, base=(60.0, 60.0, 60.0), span=(180.0, 180.0, 180.0),
     return fn
 
 
-def colour_wheel(hue0: float, sat: float, val: float, height: float):
-    """RGB from the angle around the z axis (one full hue turn) plus a height ramp."""
+def colour_wheel(hue0: float, sat: float, val: float, height: float, radius: float | None = None,
+                 turns: int = 1):
+    """RGB from the angle around the z axis (`turns` hue turns per revolution,
+    negative: the hue runs the other way round) plus a height ramp.  With a
+    radius, the saturation fades linearly to grey towards the axis (full at
+    the radius), so that the end caps' vertex colours -- a fan around a centre
+    vertex -- interpolate to the same colour the ray caster sees."""
     def fn(p):
         ang = np.arctan2(p[:, 1], p[:, 0])
-        hue = (ang / (2 * math.pi) + hue0) % 1.0
+        hue = (turns * ang / (2 * math.pi) + hue0) % 1.0
         v = val * (0.75 + 0.25 * np.clip(p[:, 2] / height, 0.0, 1.0))
+        s = sat if radius is None else sat * np.clip(np.hypot(p[:, 0], p[:, 1]) / radius, 0.0, 1.0)
         k = (np.array([5.0, 3.0, 1.0])[None, :] + hue[:, None] * 6.0) % 6.0
-        rgb = v[:, None] - v[:, None] * sat * np.clip(np.minimum(k, 4.0 - k), 0.0, 1.0)
+        rgb = v[:, None] - (v * s)[:, None] * np.clip(np.minimum(k, 4.0 - k), 0.0, 1.0)
         return 255.0 * rgb
     return fn
 
@@ -448,31 +455,46 @@ def tabletop_small(seed=1001, noise_m=0.002, colour=False, on_grid=True, W=160, 
     return Scene("tabletop_small", W, H, f, f, cx, cy, depth, rgb, None, params, [box], [req], [gt])
 
 
+# Table-frame positions (m) of the three tabletop objects: the ellipsoid on
+# the left, the two cans on the right.  The ellipsoid is the shorter object, so
+# it is the one a pose could hide completely behind (or inside) a can; its
+# centre is kept more than 25 cm (Chebyshev, in the table plane) from both
+# cans, so that no pose of its +-21 cm grid comes near one.  Equal-height
+# objects cannot hide each other from this camera (the farther top shows).
+_TABLETOP_LAYOUT = ((-0.15, 0.01), (0.12, -0.09), (0.11, 0.08))
+# Camera distance of the 3-object tabletop: far enough that every pose of
+# every grid lies wholly inside the 640x480 image (a pose partly outside the
+# image has fewer points to pay for and would undercut the true one).
+_TABLETOP_3OBJ_DIST = 1.05
+
+
 def tabletop_3obj(seed=1002, noise_m=0.003, occluder_frac=0.2, grid_half=21, n_yaw=16,
                   W=640, H=480, tri_scale=1.0):
     """Ellipsoid + two same-shape cylinders of different colour on a table.
 
-    Hypotheses per object: (2*grid_half+1)^2 positions at 1 cm x n_yaw yaws,
-    centred on the object's ground-truth position rounded to the centimetre.
+    Ground truth on the hypothesis grid: positions on the 1 cm lattice (the
+    layout above plus a seeded offset of -1..1 cm) and yaws from the n_yaw
+    set, so that Request.gt_index names the true pose.  Hypotheses per
+    object: (2*grid_half+1)^2 positions at 1 cm x n_yaw yaws centred on the
+    object's position.
     """
     rng = np.random.default_rng(seed)
     f = 615.0 * W / 640.0
     cx, cy = W / 2.0, H / 2.0
-    r_wc, t_wc = look_at(0.8, 50.0)
+    r_wc, t_wc = look_at(_TABLETOP_3OBJ_DIST, 50.0)
     nlon = max(8, int(round(100 * math.sqrt(tri_scale))))
     nseg = max(8, int(round(128 * math.sqrt(tri_scale))))
     ell = ellipsoid_mesh(0.04, 0.03, 0.05, nlon + 1, nlon, name="ellipsoid", vol_r=0.03, vol_h=0.10)
     nrow = max(2, int(round(38 * math.sqrt(tri_scale))))
-    can_a = cylinder_mesh(0.033, 0.12, nseg, nrow, colour_wheel(0.0, 0.75, 0.95, 0.12), name="can_a")
-    can_b = cylinder_mesh(0.033, 0.12, nseg, nrow, colour_wheel(0.45, 0.55, 0.80, 0.12), name="can_b")
+    can_a = cylinder_mesh(0.033, 0.12, nseg, nrow, colour_wheel(0.0, 0.75, 0.95, 0.12, 0.033), name="can_a")
+    # same shape, different colour: no yaw of one can matches the other's
+    # colours (its hue wheel runs the other way round, and it is darker)
+    can_b = cylinder_mesh(0.033, 0.12, nseg, nrow, colour_wheel(0.45, 0.6, 0.62, 0.12, 0.033, turns=-1),
+                          name="can_b")
     meshes = [ell, can_a, can_b]
-    # non-overlapping placements on the table
-    pos = []
-    while len(pos) < 3:
-        p = rng.uniform(-0.15, 0.15, size=2)
-        if all(np.linalg.norm(p - q) > 0.12 for q in pos):
-            pos.append(p)
-    yaws_gt = rng.uniform(0, 2 * math.pi, size=3)
+    pos = [np.round((np.array(xy) + 0.01 * rng.integers(-1, 2, size=2)) * 100) / 100 for xy in _TABLETOP_LAYOUT]
+    yaw_index = rng.integers(0, n_yaw, size=3)
+    yaws_gt = yaw_index * (2 * math.pi / n_yaw)
     objs, gts = [], []
     for k, m in enumerate(meshes):
         g = tabletop_pose(r_wc, t_wc, pos[k][0], pos[k][1], yaws_gt[k])
@@ -493,9 +515,10 @@ def tabletop_3obj(seed=1002, noise_m=0.003, occluder_frac=0.2, grid_half=21, n_y
     yaws = np.arange(n_yaw) * (2 * math.pi / n_yaw)
     reqs = []
     for k in range(3):
-        cxg, cyg = np.round(pos[k] * 100) / 100
+        cxg, cyg = pos[k]
         poses = _grid_poses(r_wc, t_wc, cxg + steps, cyg + steps, yaws)
-        reqs.append(Request(k, -1, (0, 0, W, H), poses))
+        gt_index = int((grid_half * len(steps) + grid_half) * n_yaw + yaw_index[k])
+        reqs.append(Request(k, -1, (0, 0, W, H), poses, gt_index))
     return Scene("tabletop_3obj", W, H, f, f, cx, cy, depth, rgb, None, params, meshes, reqs, gts)
 
 

@@ -23,9 +23,12 @@ batched / served / refine / tree / other_configs : the batched form (64
         path vs server), GICP refinement then scoring (6-DoF), the tree search
         of variant 2.0-B, and the other synthetic configurations.
 
-N > 1 (torchrun): every rank scores its own copy of the batch (independent
-problems, weak scaling, no data-path collective); value = all ranks' hypotheses
-/ the slowest rank's time.
+N > 1 (torchrun): the search of each object is sharded -- N times finer in yaw
+(16 N yaws), rank r scoring 43^2 positions x the yaws (k + r / N) 22.5 deg with
+the scene and meshes replicated; each step ends with one all-reduce MIN (NCCL)
+of the three per-object packed (J << 32 | global id) keys from perch_best_key,
+which is the whole search's argmin (weak scaling: fixed work per GPU); value =
+all ranks' hypotheses / the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -111,12 +114,13 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(grid_half):
+def _workload(grid_half, yaw_phase=0.0):
     from paper_2008_00326_gb300 import scenes
-    sc = scenes.tabletop_3obj(grid_half=grid_half)
+    sc = scenes.tabletop_3obj(grid_half=grid_half, yaw_phase=yaw_phase)
     desc = (f"tabletop_3obj: 640x480 RGB-D, ellipsoid 20k + 2 same-shape cylinders 10k tris, "
             f"{len(sc.requests)}x{len(sc.requests[0].poses)} 3-DoF hypotheses "
-            f"({2 * grid_half + 1}^2 positions x 16 yaws), colour check on, 20% occluder pixels")
+            f"({2 * grid_half + 1}^2 positions x 16 yaws, ground truth on the grid), colour check on, "
+            f"20% occluder pixels, camera 1.05 m")
     return sc, desc
 
 
@@ -550,6 +554,7 @@ def _served_rates(P, ctx, kinds, rates, max_requests, seed, window_s=2.0):
         for t in tickets:
             a_ns, b_ns = srv.times(t)
             slat.append((b_ns - a_ns) / 1e9)
+            srv.release(t)
         srv.stop()
 
         def stats(v, span):
@@ -578,9 +583,12 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    from paper_2008_00326_gb300 import build, perch as P
+    from paper_2008_00326_gb300 import build, perch as P, shard
     build.build()
-    sc, desc = _workload(a.grid_half)
+    # N > 1: the search of each object is N times finer in yaw (16 N yaws),
+    # rank r scoring the yaws (k + r / N) 22.5 deg; one all-reduce MIN of the
+    # three packed (J, global id) keys per step picks the winners
+    sc, desc = _workload(a.grid_half, yaw_phase=rank / world if world > 1 else 0.0)
     ctx = P.Context(local)
     sid = ctx.set_observation(sc)
     mids = [ctx.load_mesh(m) for m in sc.meshes]
@@ -592,14 +600,24 @@ def main():
     d_bi = torch.empty(len(reqs), dtype=torch.int64, device=dev)
     d_bc = torch.empty(len(reqs), dtype=torch.int32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    d_keys = torch.empty(len(reqs), dtype=torch.int64, device=dev)
+    d_gids = []
+    for r in reqs:
+        # global id of local hypothesis i = (position, yaw k): position 16 N + k N + rank
+        i = np.arange(len(r.poses), dtype=np.int64)
+        d_gids.append(torch.from_numpy((i // 16) * 16 * world + (i % 16) * world + rank).to(dev))
 
     def step_device(ev_obj=None):
         for k, r in enumerate(reqs):
             P.perch_score_hypotheses(ctx.ctx, sid, mids[k], r.label, r.roi, d_poses[k], d_costs[k],
                                      stream)
             P.perch_best(ctx.ctx, d_costs[k], None, stream, d_bi[k:k + 1], d_bc[k:k + 1])
+            if world > 1:
+                P.perch_best_key(ctx.ctx, d_costs[k], d_keys[k:k + 1], ids=d_gids[k], stream=stream)
             if ev_obj is not None:
                 ev_obj[k].record(stream)
+        if world > 1:
+            shard.reduce_keys(d_keys, dist)
 
     with torch.cuda.stream(stream):
         for _ in range(a.warmup):
@@ -644,6 +662,21 @@ def main():
                 score_ms.append((k, s0.elapsed_time(s1)))
     ms_step = max_over_ranks(total_ms / a.steps, dist, dev)
     value = whole_job_rate(n_step, world, ms_step)
+    # the search result of the last timed step, per object: the best pose's
+    # cost and distance from the ground truth (on the grid), and the truth's cost
+    argmin = []
+    bi_h, bc_h = d_bi.cpu().numpy(), d_bc.cpu().numpy()
+    if world > 1:
+        argmin = [dict(zip(("object", "best_J", "best_global_id"), (sc.meshes[r.mesh_index].name,)
+                           + shard.unpack(int(key)))) for r, key in zip(reqs, d_keys.cpu().tolist())]
+    for k, r in enumerate(reqs if world == 1 else ()):
+        c = d_costs[k].cpu().numpy()
+        t = r.poses[:, [3, 7, 11]].astype(np.float64)
+        b = int(bi_h[k])
+        argmin.append({"object": sc.meshes[r.mesh_index].name, "best_index": b, "best_J": int(bc_h[k]),
+                       "gt_index": r.gt_index, "gt_J": int(c[r.gt_index].sum()),
+                       "best_translation_error_mm": 1000.0 * float(np.linalg.norm(t[b] - t[r.gt_index])),
+                       "best_yaw_equals_gt": (b - r.gt_index) % 16 == 0})
 
     # ---- e2e through the public API with host buffers (pinned)
     pinned = [torch.from_numpy(r.poses).pin_memory().numpy() for r in reqs]
@@ -733,13 +766,17 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "hypotheses_per_step": n_step, "l2": "flushed between steps (512 MiB write)",
+        "config": {"workload": desc, "hypotheses_per_step": n_step * world, "l2": "flushed between steps (512 MiB write)",
+                   "sharding": ("one GPU" if world == 1 else
+                                f"{world} ranks: each scores 43^2 positions x 16 yaws per object of a "
+                                f"{16 * world}-yaw grid; one all-reduce MIN of 3 packed (J, id) keys per step"),
                    "launch": {"threads": 256, "zbuf_words": 8192, "mark_bits": 65536}},
+        "argmin": argmin,
         "latency_ms": {"search_p50": lat[len(lat) // 2], "search_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "what": f"one object's {len(reqs[0].poses):,}-hypothesis search (score + argmin), device-timed"},
         "e2e": {"value": whole_job_rate(n_step, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": a.steps * 2 * len(reqs),
+        "gpu_launches": a.steps * (2 if world == 1 else 3) * len(reqs),
         "clocks": clk,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -31,7 +31,15 @@
  * as PERCH_E_CUDA.  There is no CPU fallback: a context cannot be created
  * without a CUDA device.
  *
- * Threading: a context may be used by one host thread at a time.
+ * Threading: a context may be used by one host thread at a time, with one
+ * exception: while a served-form server runs on it (its own threads use the
+ * context), other threads may load and release meshes and observations; every
+ * other call on the context returns PERCH_E_BUSY until the server is stopped.
+ *
+ * Lifetime: releasing a mesh or an observation returns PERCH_E_BUSY, and
+ * changes nothing, while anything may still read it -- a queued or running
+ * served request, a batch graph that has not been destroyed, or an
+ * asynchronous call (cuda_stream != NULL) whose stream has not yet passed it.
  */
 #ifndef PERCH_H
 #define PERCH_H
@@ -130,7 +138,8 @@ PERCH_API perch_status perch_load_mesh(perch_ctx *ctx, const float *verts_xyz, c
                              int32_t n_verts, const int32_t *tris, int32_t n_tris,
                              float vol_radius_m, float vol_height_m, int32_t *mesh_id);
 
-/* Release a mesh and its device memory. */
+/* Release a mesh and its device memory.  PERCH_E_BUSY while it is in use
+ * (see "Lifetime" above); PERCH_E_NOTFOUND for an unknown id. */
 PERCH_API perch_status perch_release_mesh(perch_ctx *ctx, int32_t mesh_id);
 
 /* Upload an observation (Sec. III-B: the input cloud I from the RGB-D image and
@@ -150,7 +159,8 @@ PERCH_API perch_status perch_set_observation(perch_ctx *ctx, const uint16_t *dep
                                    float fy, float cx, float cy, const perch_params *params,
                                    int32_t *scene_id);
 
-/* Release an observation and its device memory. */
+/* Release an observation and its device memory.  PERCH_E_BUSY while it is
+ * in use (see "Lifetime" above); PERCH_E_NOTFOUND for an unknown id. */
 PERCH_API perch_status perch_release_scene(perch_ctx *ctx, int32_t scene_id);
 
 /* Score n pose hypotheses of one mesh against one observation.
@@ -175,9 +185,32 @@ PERCH_API perch_status perch_score_hypotheses(perch_ctx *ctx, int32_t scene_id, 
  *   costs n*2 int32, ids n uint64 or NULL, n >= 1 (n < 2^31).
  *   best_index (int64) and best_cost (int32) receive the winner.
  * cuda_stream NULL: all pointers are host pointers; otherwise all are device
- * pointers and the result is written when the stream reaches the call. */
+ * pointers and the result is written when the stream reaches the call.  The
+ * context's argmin launches share one scratch buffer, so each is ordered on
+ * the GPU after the context's previous one (an event), whatever the streams. */
 PERCH_API perch_status perch_best(perch_ctx *ctx, const int32_t *costs, const uint64_t *ids, int64_t n,
                         int64_t *best_index, int32_t *best_cost, void *cuda_stream);
+
+/* The argmin of perch_best as one 64-bit key, (J << 32) | id, for combining
+ * searches sharded over several processes or GPUs: every shard computes its
+ * key, and the minimum of the keys (one min-reduce, e.g. an all-reduce MIN) is
+ * the key of the whole search's winner -- smallest J, ties to the lowest id,
+ * exactly as one perch_best over all hypotheses decides (Sec. IV-A "Parallel
+ * Search").  costs (n*2 int32), ids (n uint64, each below 2^32: the
+ * hypotheses' ids in the whole search; NULL uses the index) and key (one
+ * uint64) are DEVICE pointers on cuda_stream (required), ordered like
+ * perch_best's launches.  1 <= n <= 2^31-1. */
+PERCH_API perch_status perch_best_key(perch_ctx *ctx, const int32_t *costs, const uint64_t *ids, int64_t n,
+                                      uint64_t *key, void *cuda_stream);
+
+/* Wait for cuda_stream (NULL: the context's own stream) and report what the
+ * kernels of earlier asynchronous calls found: the scoring kernels keep a
+ * device error word (a hash table too small, a depth key out of range, a
+ * bitset over capacity, a GICP source cloud over max_source_points) that an
+ * asynchronous call cannot return.  PERCH_OK, or the status the synchronous
+ * call would have returned (PERCH_E_CUDA or PERCH_E_INVALID, message in
+ * perch_last_error); the word is cleared.  Synchronous calls check it too. */
+PERCH_API perch_status perch_sync(perch_ctx *ctx, void *cuda_stream);
 
 /* The same argmin as perch_best, for callers that cannot allocate device
  * memory -- for example a serving process that reserves all of its HBM at
@@ -284,7 +317,10 @@ PERCH_API perch_status perch_autotune(perch_ctx *ctx, const perch_work_item *ite
  * stay resident in the context; each slot's device staging for
  * max_batch_hypotheses poses and costs is allocated at start-up and charged
  * to the context's HBM budget, so admission is bounded by that budget.
- * While a server runs, the context may be used only through the server calls. */
+ * While a server runs, other threads may load and release meshes and
+ * observations (a release that a queued or running request still needs is
+ * refused with PERCH_E_BUSY); every other call on the context returns
+ * PERCH_E_BUSY until perch_server_stop. */
 typedef struct perch_server perch_server;
 
 typedef struct perch_server_config {
@@ -321,6 +357,14 @@ PERCH_API perch_status perch_wait(perch_server *srv, uint64_t ticket, int64_t ti
 /* Steady-clock times (ns) of submission and completion of a finished ticket. */
 PERCH_API perch_status perch_ticket_times(perch_server *srv, uint64_t ticket, int64_t *submit_ns,
                                           int64_t *done_ns);
+/* Forget a finished ticket (its status and times).  The server keeps every
+ * ticket until it is released or the server is stopped, so a long-running
+ * caller releases each one once it has read it.  PERCH_E_BUSY while the
+ * request is queued or running, PERCH_E_NOTFOUND for an unknown ticket. */
+PERCH_API perch_status perch_ticket_release(perch_server *srv, uint64_t ticket);
+/* Number of tickets the server holds (queued, running and finished but not
+ * yet released). */
+PERCH_API perch_status perch_server_tickets(perch_server *srv, int64_t *held);
 /* Finish every queued request, stop the threads and free the server. */
 PERCH_API perch_status perch_server_stop(perch_server *srv);
 

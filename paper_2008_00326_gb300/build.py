@@ -18,6 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libperch.so")
 BUILD_DIR = os.path.join(PKG, "_build")
+# debug build: every scorer index checked before use (PERCH_CHECKS), violations
+# reported through the device error word; same ABI, slower
+LIB_CHECKS = os.path.join(PKG, "libperch_checks.so")
+BUILD_DIR_CHECKS = os.path.join(PKG, "_build_checks")
 SOURCES = ["perch_api.cu", "perch_batch.cu", "perch_serve.cu", "perch_refine.cu", "perch_tree.cu", "perch_kernels.cu",
            "perch_noalloc.cu", "perch_microbench.cu", "perch_metrics.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,23 +44,28 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile the CUDA sources and link libperch.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checks: bool = False) -> str:
+    """Compile the CUDA sources and link libperch.so (checks=True: the debug
+    library libperch_checks.so, with -DPERCH_CHECKS); returns its path."""
+    lib = LIB_CHECKS if checks else LIB
+    build_dir = BUILD_DIR_CHECKS if checks else BUILD_DIR
+    if checks:
+        extra_flags = (*extra_flags, "-DPERCH_CHECKS=1")
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-I", INCLUDE, "-I", CSRC, "-c",
                os.path.join(CSRC, src), "-o", obj]
@@ -72,14 +81,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             failed.append(cmd[-3])
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     link = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
     if verbose:
         print(" ".join(link), flush=True)
     subprocess.check_call(link)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, checks="--checks" in sys.argv)

@@ -203,6 +203,75 @@ perch_status make_job(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t l
     return PERCH_OK;
 }
 
+perch_status refuse_while_serving(perch_ctx* c)
+{
+    if (c->servers.load() > 0)
+        return fail(c, PERCH_E_BUSY, "a server is running on this context: use the server calls, or "
+                                     "load and release meshes and observations, until it is stopped");
+    return PERCH_OK;
+}
+
+static void drop_finished(UseTrack& u)
+{
+    size_t k = 0;
+    for (cudaEvent_t ev : u.pending) {
+        if (cudaEventQuery(ev) == cudaErrorNotReady) {
+            u.pending[k++] = ev;
+        } else {
+            cudaGetLastError();
+            cudaEventDestroy(ev);
+        }
+    }
+    u.pending.resize(k);
+}
+
+bool in_use(UseTrack& u)
+{
+    drop_finished(u);
+    return u.users > 0 || !u.pending.empty();
+}
+
+static perch_status track(perch_ctx* c, UseTrack& u, cudaStream_t st)
+{
+    drop_finished(u);
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (!e) e = cudaEventRecord(ev, st);
+    if (e) {
+        if (ev) cudaEventDestroy(ev);
+        return cuda_fail(c, e, "recording an asynchronous use");
+    }
+    u.pending.push_back(ev);
+    return PERCH_OK;
+}
+
+perch_status note_async_use(perch_ctx* c, int32_t scene_id, int32_t mesh_id, cudaStream_t st)
+{
+    perch_status r = PERCH_OK;
+    auto si = c->scenes.find(scene_id);
+    if (si != c->scenes.end()) r = track(c, si->second.use, st);
+    auto mi = c->meshes.find(mesh_id);
+    if (r == PERCH_OK && mi != c->meshes.end()) r = track(c, mi->second.use, st);
+    return r;
+}
+
+void count_users(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int d)
+{
+    auto si = c->scenes.find(scene_id);
+    if (si != c->scenes.end()) si->second.use.users += d;
+    auto mi = c->meshes.find(mesh_id);
+    if (mi != c->meshes.end()) mi->second.use.users += d;
+}
+
+static void free_tracking(UseTrack& u)
+{
+    for (cudaEvent_t ev : u.pending) {
+        cudaEventSynchronize(ev);
+        cudaEventDestroy(ev);
+    }
+    u.pending.clear();
+}
+
 // Launch the persistent scorer once per job, on stream st after every
 // earlier run that used X.  Each launch gets the whole resident grid; with
 // several jobs the launches go round-robin over X's side streams, so the
@@ -215,6 +284,7 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
                       int mark_words, const perch::ScoreConfig& cfg_in, cudaStream_t st,
                       unsigned long long* dump, const AfterJob* after_job)
 {
+    Range r("perch: scoring launches");
     long long total = 0;
     int max_verts = 0;
     bool small_images = true;
@@ -384,6 +454,10 @@ perch_status perch_create(perch_ctx** out, int32_t device, uint64_t hbm_budget_b
         c->d_best_cost = (int32_t*)((char*)p + 32);
     }
     if (st == PERCH_OK) st = scratch_init(c, c->plain);
+    if (st == PERCH_OK && (e = cudaEventCreateWithFlags(&c->best_last, cudaEventDisableTiming)) != cudaSuccess)
+        st = cuda_fail(c, e, "cudaEventCreate");
+    if (st == PERCH_OK && (e = cudaEventRecord(c->best_last, c->stream)) != cudaSuccess)
+        st = cuda_fail(c, e, "cudaEventRecord");
     if (st == PERCH_OK) {
         cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
         cudaMemsetAsync(c->d_best_ticket, 0, 64, c->stream);
@@ -402,8 +476,15 @@ perch_status perch_create(perch_ctx** out, int32_t device, uint64_t hbm_budget_b
 perch_status perch_destroy(perch_ctx* c)
 {
     if (!c) return PERCH_OK;
+    if (c->servers.load() > 0) return refuse_while_serving(c);
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->scenes) free_tracking(kv.second.use);
+    for (auto& kv : c->meshes) free_tracking(kv.second.use);
+    if (c->best_last) {
+        cudaEventSynchronize(c->best_last);
+        cudaEventDestroy(c->best_last);
+    }
     scratch_free(c, c->plain);
     for (auto& kv : c->allocs) cudaFree(kv.first);
     c->allocs.clear();
@@ -458,6 +539,8 @@ perch_status perch_load_mesh(perch_ctx* c, const float* verts_xyz, const uint8_t
         t4[4 * i + 3] = 0;
     }
     DeviceGuard g(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    Range r("perch: mesh upload");
     perch_status st = dalloc(c, v4.size() * sizeof(float), &rec.verts);
     if (st != PERCH_OK) return st;
     if ((st = dalloc(c, t4.size() * sizeof(int32_t), &rec.tris)) != PERCH_OK) {
@@ -492,9 +575,14 @@ perch_status perch_load_mesh(perch_ctx* c, const float* verts_xyz, const uint8_t
 perch_status perch_release_mesh(perch_ctx* c, int32_t mesh_id)
 {
     if (!c) return PERCH_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->meshes.find(mesh_id);
     if (it == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
     DeviceGuard g(c->device);
+    if (in_use(it->second.use))
+        return fail(c, PERCH_E_BUSY, "mesh %d is in use (%d served requests or batch graphs, %zu unfinished "
+                                     "asynchronous calls)", mesh_id, it->second.use.users,
+                    it->second.use.pending.size());
     cudaStreamSynchronize(c->stream);
     dfree(c, it->second.verts);
     dfree(c, it->second.tris);
@@ -528,6 +616,8 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     if (xmax > lim || ymax > lim || zmax > lim)
         return fail(c, PERCH_E_INVALID, "perch_set_observation: delta too small for the field of view");
 
+    std::lock_guard<std::mutex> lk(c->mu);
+    Range r("perch: observation build (cloud, CIELAB, voxel hash)");
     long long npx = (long long)W * H;
     long long n_valid = 0;
     for (long long i = 0; i < npx; ++i) {
@@ -644,13 +734,17 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
 perch_status perch_release_scene(perch_ctx* c, int32_t scene_id)
 {
     if (!c) return PERCH_E_INVALID;
+    std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->scenes.find(scene_id);
     if (it == c->scenes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown scene %d", scene_id);
     DeviceGuard g(c->device);
-    cudaStreamSynchronize(c->stream);
     SceneRec& s = it->second;
+    if (in_use(s.use))
+        return fail(c, PERCH_E_BUSY, "scene %d is in use (%d served requests or batch graphs, %zu unfinished "
+                                     "asynchronous calls)", scene_id, s.use.users, s.use.pending.size());
+    cudaStreamSynchronize(c->stream);
     dfree(c, s.depth); dfree(c, s.labels); dfree(c, s.lab); dfree(c, s.pts); dfree(c, s.table); dfree(c, s.nrm);
-        dfree(c, s.near);
+    dfree(c, s.near);
     c->scenes.erase(it);
     return PERCH_OK;
 }
@@ -664,14 +758,17 @@ perch_status perch_score_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mesh
     if (n < 0) return fail(c, PERCH_E_INVALID, "n < 0");
     if (n == 0) return PERCH_OK;
     if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
+    perch_status st = refuse_while_serving(c);
+    if (st != PERCH_OK) return st;
     DeviceGuard g(c->device);
     perch::Job J;
     int mw;
-    perch_status st = make_job(c, scene_id, mesh_id, label, roi, poses, costs, n, &J, &mw, nullptr, nullptr);
+    st = make_job(c, scene_id, mesh_id, label, roi, poses, costs, n, &J, &mw, nullptr, nullptr);
     if (st != PERCH_OK) return st;
     if (cuda_stream) {
         std::vector<perch::Job> jobs(1, J);
-        return run_jobs(c, c->plain, jobs, mw, c->cfg, (cudaStream_t)cuda_stream, nullptr);
+        st = run_jobs(c, c->plain, jobs, mw, c->cfg, (cudaStream_t)cuda_stream, nullptr);
+        return st != PERCH_OK ? st : note_async_use(c, scene_id, mesh_id, (cudaStream_t)cuda_stream);
     }
     const long long chunk = 1 << 20;
     if ((st = ensure_stage(c, (size_t)std::min<long long>(n, chunk) * (48 + 8))) != PERCH_OK) return st;
@@ -700,19 +797,26 @@ perch_status perch_best(perch_ctx* c, const int32_t* costs, const uint64_t* ids,
     c->err.clear();
     if (!costs || !best_index || !best_cost) return fail(c, PERCH_E_INVALID, "null pointer");
     if (n < 1 || n > 0x7FFFFFFFll) return fail(c, PERCH_E_INVALID, "n out of range");
+    perch_status rs = refuse_while_serving(c);
+    if (rs != PERCH_OK) return rs;
     DeviceGuard g(c->device);
+    Range r("perch: argmin");
     perch::BestArgs a{};
     a.n = n;
     a.partial = c->d_best_partial;
     a.ticket = c->d_best_ticket;
     cudaError_t e;
     if (cuda_stream) {
+        // every argmin of the context shares its scratch: run after the previous one
+        cudaStream_t s = (cudaStream_t)cuda_stream;
         a.costs = costs;
         a.ids = (const unsigned long long*)ids;
         a.best_index = (long long*)best_index;
         a.best_cost = best_cost;
-        if ((e = perch::launch_best(a, (cudaStream_t)cuda_stream)) != cudaSuccess)
-            return cuda_fail(c, e, "perch_best launch");
+        e = cudaStreamWaitEvent(s, c->best_last, 0);
+        if (!e) e = perch::launch_best(a, s);
+        if (!e) e = cudaEventRecord(c->best_last, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "perch_best launch");
         return PERCH_OK;
     }
     size_t need = (size_t)n * 8 + (ids ? (size_t)n * 8 : 0);
@@ -726,7 +830,9 @@ perch_status perch_best(perch_ctx* c, const int32_t* costs, const uint64_t* ids,
     a.ids = d_ids;
     a.best_index = c->d_best_index;
     a.best_cost = c->d_best_cost;
+    if (!e) e = cudaStreamWaitEvent(c->stream, c->best_last, 0);
     if (!e) e = perch::launch_best(a, c->stream);
+    if (!e) e = cudaEventRecord(c->best_last, c->stream);
     long long bi = -1;
     int32_t bc = 0;
     if (!e) e = cudaMemcpyAsync(&bi, c->d_best_index, 8, cudaMemcpyDeviceToHost, c->stream);
@@ -738,11 +844,49 @@ perch_status perch_best(perch_ctx* c, const int32_t* costs, const uint64_t* ids,
     return PERCH_OK;
 }
 
+perch_status perch_best_key(perch_ctx* c, const int32_t* costs, const uint64_t* ids, int64_t n, uint64_t* key,
+                            void* cuda_stream)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (!costs || !key || !cuda_stream) return fail(c, PERCH_E_INVALID, "null costs, key or stream");
+    if (n < 1 || n > 0x7FFFFFFFll) return fail(c, PERCH_E_INVALID, "n out of range");
+    perch_status rs = refuse_while_serving(c);
+    if (rs != PERCH_OK) return rs;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    perch::BestArgs a{};
+    a.costs = costs;
+    a.ids = (const unsigned long long*)ids;
+    a.n = n;
+    a.partial = c->d_best_partial;
+    a.ticket = c->d_best_ticket;
+    a.key = (unsigned long long*)key;
+    cudaError_t e = cudaStreamWaitEvent(s, c->best_last, 0);
+    if (!e) e = perch::launch_best(a, s);
+    if (!e) e = cudaEventRecord(c->best_last, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "perch_best_key launch");
+    return PERCH_OK;
+}
+
+perch_status perch_sync(perch_ctx* c, void* cuda_stream)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    perch_status st = refuse_while_serving(c);
+    if (st != PERCH_OK) return st;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(cuda_stream ? (cudaStream_t)cuda_stream : c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "perch_sync");
+    return check_device_error(c);
+}
+
 perch_status perch_set_launch_config(perch_ctx* c, int32_t threads, int32_t zbuf_words,
                                      int32_t mark_bits)
 {
     if (!c) return PERCH_E_INVALID;
     c->err.clear();
+    if (refuse_while_serving(c) != PERCH_OK) return PERCH_E_BUSY;
     if (mark_bits == 0) mark_bits = kMarkBitsDefault;
     if ((threads != 128 && threads != 256 && threads != 512) || zbuf_words < 1024 ||
         zbuf_words > 49152 || mark_bits < 1024 || mark_bits > (1 << 22))
@@ -768,6 +912,7 @@ perch_status perch_pose_proposals(perch_ctx* c, int32_t scene_id, int32_t mesh_i
     auto mi = c->meshes.find(mesh_id);
     if (mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
     if (label < 0 || !si->second.labels) return fail(c, PERCH_E_INVALID, "proposals need a label and labels");
+    if (refuse_while_serving(c) != PERCH_OK) return PERCH_E_BUSY;
     DeviceGuard g(c->device);
     perch::ProposalArgs a{};
     a.sc = si->second.ds;
@@ -783,7 +928,8 @@ perch_status perch_pose_proposals(perch_ctx* c, int32_t scene_id, int32_t mesh_i
         a.poses = poses;
         a.z_out = z_range;
         cudaError_t e = perch::launch_proposals(a, (cudaStream_t)cuda_stream);
-        return e ? cuda_fail(c, e, "perch_pose_proposals") : PERCH_OK;
+        if (e) return cuda_fail(c, e, "perch_pose_proposals");
+        return note_async_use(c, scene_id, -1, (cudaStream_t)cuda_stream);
     }
     a.poses = (float*)c->stage;
     a.z_out = (int32_t*)(a.zr + 2);
@@ -804,12 +950,14 @@ perch_status perch_add_s(perch_ctx* c, int32_t mesh_id, const float* poses, cons
     if (!poses || !poses_true || !add) return fail(c, PERCH_E_INVALID, "null pointer");
     auto mi = c->meshes.find(mesh_id);
     if (mi == c->meshes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown mesh %d", mesh_id);
+    if (refuse_while_serving(c) != PERCH_OK) return PERCH_E_BUSY;
     DeviceGuard g(c->device);
     const perch::DevMesh& m = mi->second.dm;
     if (cuda_stream) {
         cudaError_t e = perch::launch_add_s(m.verts, m.n_verts, poses, poses_true, n, symmetric ? 1 : 0, add,
                                             (cudaStream_t)cuda_stream);
-        return e ? cuda_fail(c, e, "perch_add_s") : PERCH_OK;
+        if (e) return cuda_fail(c, e, "perch_add_s");
+        return note_async_use(c, -1, mesh_id, (cudaStream_t)cuda_stream);
     }
     perch_status st = ensure_stage(c, (size_t)n * (48 + 48 + 8));
     if (st != PERCH_OK) return st;
@@ -839,8 +987,10 @@ perch_status perch_debug_render_keys(perch_ctx* c, int32_t scene_id, int32_t mes
     if (!c) return PERCH_E_INVALID;
     c->err.clear();
     if (!pose || !keys) return fail(c, PERCH_E_INVALID, "null pose or keys");
+    perch_status st = refuse_while_serving(c);
+    if (st != PERCH_OK) return st;
     DeviceGuard g(c->device);
-    perch_status st = ensure_stage(c, 64);
+    st = ensure_stage(c, 64);
     if (st != PERCH_OK) return st;
     float* d_pose = (float*)c->stage;
     int32_t* d_cost = (int32_t*)((char*)c->stage + 48);

@@ -52,6 +52,8 @@ perch_status perch_score_batch(perch_ctx* c, const perch_work_item* items, int32
     if (!c) return PERCH_E_INVALID;
     c->err.clear();
     if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
+    perch_status st = refuse_while_serving(c);
+    if (st != PERCH_OK) return st;
     DeviceGuard g(c->device);
     std::vector<perch::Job> jobs;
     int mw;
@@ -59,11 +61,15 @@ perch_status perch_score_batch(perch_ctx* c, const perch_work_item* items, int32
     long long extent = 0;
     for (int32_t i = 0; items && i < n_items; ++i) extent = std::max<long long>(extent, items[i].pose_offset + items[i].n);
     if (cuda_stream) {
-        perch_status st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
+        st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
         if (st != PERCH_OK) return st;
-        return run_jobs(c, c->plain, jobs, mw, c->cfg, (cudaStream_t)cuda_stream, nullptr);
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        st = run_jobs(c, c->plain, jobs, mw, c->cfg, s, nullptr);
+        for (int32_t i = 0; i < n_items && st == PERCH_OK; ++i)
+            if (items[i].n > 0) st = note_async_use(c, items[i].scene_id, items[i].mesh_id, s);
+        return st;
     }
-    perch_status st = ensure_stage(c, (size_t)std::max<long long>(1, extent) * (48 + 8));
+    st = ensure_stage(c, (size_t)std::max<long long>(1, extent) * (48 + 8));
     if (st != PERCH_OK) return st;
     float* d_poses = (float*)c->stage;
     int32_t* d_costs = (int32_t*)((char*)c->stage + (size_t)extent * 48);
@@ -87,11 +93,13 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
     c->err.clear();
     *out = nullptr;
     if (!poses || !costs) return fail(c, PERCH_E_INVALID, "null poses or costs");
+    perch_status st = refuse_while_serving(c);
+    if (st != PERCH_OK) return st;
     DeviceGuard g(c->device);
     std::vector<perch::Job> jobs;
     int mw;
     long long total;
-    perch_status st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
+    st = batch_jobs(c, items, n_items, poses, costs, &jobs, &mw, &total);
     if (st != PERCH_OK) return st;
     if (total == 0) return fail(c, PERCH_E_INVALID, "empty batch");
     perch::ScoreConfig cfg = c->cfg;
@@ -154,11 +162,18 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
         e = perch::add_score_node(G->graph, &dep, 1, a, cfg, resident, &nodes[j]);
     }
     if (st == PERCH_OK && !e) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+    if (st == PERCH_OK && !e) e = cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming);
     if (st == PERCH_OK && e) st = cuda_fail(c, e, "perch_batch_graph_create");
     if (st != PERCH_OK) {
         perch_batch_graph_destroy(G);
         return st;
     }
+    // the graph reads its items' scenes and meshes until it is destroyed
+    for (int32_t i = 0; i < n_items; ++i)
+        if (items[i].n > 0) {
+            G->uses.push_back({items[i].scene_id, items[i].mesh_id});
+            count_users(c, items[i].scene_id, items[i].mesh_id, +1);
+        }
     *out = G;
     return PERCH_OK;
 }
@@ -168,6 +183,7 @@ perch_status perch_batch_graph_launch(perch_batch_graph* G, void* cuda_stream)
     if (!G || !G->exec) return PERCH_E_INVALID;
     DeviceGuard g(G->ctx->device);
     cudaError_t e = cudaGraphLaunch(G->exec, (cudaStream_t)cuda_stream);
+    if (!e) e = cudaEventRecord(G->done, (cudaStream_t)cuda_stream);
     if (e) return cuda_fail(G->ctx, e, "perch_batch_graph_launch");
     return PERCH_OK;
 }
@@ -177,7 +193,15 @@ perch_status perch_batch_graph_destroy(perch_batch_graph* G)
     if (!G) return PERCH_OK;
     perch_ctx* c = G->ctx;
     DeviceGuard g(c->device);
-    cudaDeviceSynchronize();
+    // waits for the graph's last launch only, not for the rest of the device
+    if (G->done) {
+        cudaEventSynchronize(G->done);
+        cudaEventDestroy(G->done);
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (const auto& u : G->uses) count_users(c, u.first, u.second, -1);
+    }
     if (G->exec) cudaGraphExecDestroy(G->exec);
     if (G->graph) cudaGraphDestroy(G->graph);
     dfree(c, G->next);
@@ -192,6 +216,8 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
     if (!c || !threads || !zbuf_words) return PERCH_E_INVALID;
     c->err.clear();
     if (!items || n_items < 1 || !poses || !costs) return fail(c, PERCH_E_INVALID, "empty batch");
+    perch_status rs = refuse_while_serving(c);
+    if (rs != PERCH_OK) return rs;
     DeviceGuard g(c->device);
     // class of the batch: largest ROI area and triangle count, as powers of two
     long long max_area = 0, max_tris = 0;

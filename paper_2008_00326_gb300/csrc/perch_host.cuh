@@ -7,20 +7,33 @@
 #include "perch_internal.cuh"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
+#include <atomic>
 #include <cstdint>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
 
 namespace perch_host {
 
+// Who still reads a resident mesh or observation: queued or running served
+// requests and batch graphs (users), and asynchronous calls on the callers'
+// streams (an event recorded after each, dropped once it has completed).
+// Releasing the object is refused (PERCH_E_BUSY) while any is outstanding.
+struct UseTrack {
+    int users = 0;
+    std::vector<cudaEvent_t> pending;
+};
+
 struct MeshRec {
     perch::DevMesh dm{};
     void* verts = nullptr;
     void* tris = nullptr;
+    UseTrack use;
 };
 
 struct SceneRec {
@@ -34,6 +47,7 @@ struct SceneRec {
     void* nrm = nullptr;           // observed normals (GICP targets), made on first use
     int nrm_jump = -1;             // the normal_max_jump_units they were made with
     void* near = nullptr;          // near-cell bitmap (DevScene::near_bits)
+    UseTrack use;
 };
 
 // Everything one chain of scoring launches needs besides its inputs: one
@@ -54,6 +68,17 @@ struct ScoreScratch {
     cudaEvent_t fork = nullptr;
     cudaEvent_t join[kSideStreams] = {};
     cudaEvent_t last = nullptr;
+};
+
+// An NVTX range over the rest of the enclosing scope: the host stages of
+// each call show up by name in a profiler's timeline (header-only NVTX v3:
+// free when no tool is attached).
+class Range {
+public:
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
 };
 
 class DeviceGuard {
@@ -97,9 +122,16 @@ struct perch_ctx {
     unsigned* d_best_ticket = nullptr;
     long long* d_best_index = nullptr;
     int32_t* d_best_cost = nullptr;
+    cudaEvent_t best_last = nullptr;                // the last argmin launch (they share the scratch)
     perch_host::ScoreScratch plain;                    // scratch of the context's own scoring launches
     std::map<uint64_t, perch::ScoreConfig> tuned;   // autotuner results by batch class
     perch::ScoreConfig cfg{256, 8192, 1 << 16};
+    // A running server's threads share the context: they and the calls that
+    // may overlap them (loading and releasing meshes and observations) hold
+    // mu around the maps, the budget and the allocations.  Every other call
+    // is refused while a server runs.
+    std::mutex mu;
+    std::atomic<int> servers{0};
 };
 
 struct perch_batch_graph {
@@ -108,6 +140,8 @@ struct perch_batch_graph {
     void* vcache = nullptr;                // and vertex-cache pool
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;            // recorded after each launch
+    std::vector<std::pair<int32_t, int32_t>> uses;   // (scene, mesh) of its items, counted as users
 };
 
 namespace perch_host {
@@ -129,6 +163,15 @@ int mark_words_for(const SceneRec& s, int label, const int roi[4], int cap_bits)
 perch_status fit_config(perch_ctx* c, int mark_words, perch::ScoreConfig* cfg);
 perch_status scratch_init(perch_ctx* c, ScoreScratch& X);
 void scratch_free(perch_ctx* c, ScoreScratch& X);
+// PERCH_E_BUSY (with a message) while a server runs on the context.
+perch_status refuse_while_serving(perch_ctx* c);
+// Remember an asynchronous call on stream st that reads scene_id and/or
+// mesh_id (-1: none), so that releasing them waits for it to finish.
+perch_status note_async_use(perch_ctx* c, int32_t scene_id, int32_t mesh_id, cudaStream_t st);
+// True while the object has users or unfinished asynchronous calls.
+bool in_use(UseTrack& u);
+// Add d (+1 / -1) to the users of a scene and a mesh (ids that exist).
+void count_users(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int d);
 // Build the device description of one work item.
 perch_status make_job(perch_ctx* c, int32_t scene_id, int32_t mesh_id, int32_t label,
                       const int32_t* roi, const float* poses, int32_t* costs, long long n,

@@ -83,7 +83,25 @@ struct ScoreArgs {
 };
 
 // Error bits written by kernels into the context's error word.
-enum : int { kErrKeyRange = 1, kErrMarkCap = 2, kErrHashFull = 4, kErrSourceCap = 8, kErrNoSlot = 16 };
+enum : int { kErrKeyRange = 1, kErrMarkCap = 2, kErrHashFull = 4, kErrSourceCap = 8, kErrNoSlot = 16,
+             kErrCheck = 32 };
+
+// Debug builds (PERCH_CHECKS defined: build.py's checks=True, libperch_checks.so)
+// test shared- and global-memory indexes of the scorer before each access:
+// PERCH_CHECKED(cond, err) is false when cond fails, after setting kErrCheck
+// in the error word (err may be null), so the caller skips the access and
+// the host reports the violation.  Nothing traps.  In normal builds it is
+// the constant true and costs nothing.
+#ifdef PERCH_CHECKS
+__device__ __forceinline__ bool perch_checked(bool ok, int* err)
+{
+    if (!ok && err) atomicOr(err, kErrCheck);
+    return ok;
+}
+#define PERCH_CHECKED(cond, err) ::perch::perch_checked((cond), (err))
+#else
+#define PERCH_CHECKED(cond, err) true
+#endif
 
 // Launch configuration of the scoring kernel (chosen by the host; the
 // autotuner searches over these).
@@ -170,6 +188,7 @@ struct BestArgs {
     int32_t* best_cost;
     unsigned long long* partial;    // scratch: 3 words per block, 3 * kBestMaxBlocks words
     unsigned int* ticket;           // scratch: 1 word, zero on entry, zero on exit
+    unsigned long long* key;        // or nullptr: the winner as (J << 32) | low 32 bits of its id
 };
 int best_blocks(long long n);
 cudaError_t launch_best(const BestArgs& a, cudaStream_t s);

@@ -622,6 +622,7 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
 struct MarkBand {
     uint32_t* marks;
     int u0, u1, v0, v1, vw;
+    int* err;                     // debug builds: where index violations are reported
 };
 
 // Candidates j, j + k, ... of a staged chunk of n against query q, folded
@@ -717,11 +718,13 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
                 const int ci = c0 + lane, cj = ci + 32;
                 if (ci < T) {
                     while (W.runs[g][r].y <= ci) ++r;
-                    W.stage[lane] = __ldg(&sc.pts[W.runs[g][r].x + ci]);
+                    if (PERCH_CHECKED((unsigned)(W.runs[g][r].x + ci) < (unsigned)sc.n_pts, mb.err))
+                        W.stage[lane] = __ldg(&sc.pts[W.runs[g][r].x + ci]);
                 }
                 if (cj < T) {
                     while (W.runs[g][r].y <= cj) ++r;
-                    W.stage[lane + 32] = __ldg(&sc.pts[W.runs[g][r].x + cj]);
+                    if (PERCH_CHECKED((unsigned)(W.runs[g][r].x + cj) < (unsigned)sc.n_pts, mb.err))
+                        W.stage[lane + 32] = __ldg(&sc.pts[W.runs[g][r].x + cj]);
                 }
                 __syncwarp();
                 const int n = min(64, T - c0);
@@ -921,7 +924,8 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
                              (w1 > 0 || (w1 == 0 && (e.owns & 2))) &&
                              (w2 > 0 || (w2 == 0 && (e.owns & 4)));
             unsigned d;
-            if (cov && sample_depth(w0, w1, w2, e.iz, e.A, d))
+            if (cov && sample_depth(w0, w1, w2, e.iz, e.A, d) &&
+                PERCH_CHECKED((unsigned)((v - tv0) * tw + (u - tu0)) < (unsigned)(tw * (tv1 - tv0)), err))
                 zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, e.tri, err);
         }
         __syncwarp();
@@ -1063,7 +1067,7 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
             const int nbx = (nu + 7) / 8, nby = (nv + 3) / 4;
             const int nblocks = nbx * nby;
             KeptPoint* wq = S.kept + warp * kWarpQueue;
-            const MarkBand mband = {S.marks, vbox[0], vbox[2], mv0, mv1, vw};
+            const MarkBand mband = {S.marks, vbox[0], vbox[2], mv0, mv1, vw, a.err};
             // the raster stage shared these bytes: start with an empty lookup cache
             for (int i = lane; i < kCellCache; i += 32) WP.cache[i] = make_uint4(~0u, ~0u, 0u, 0u);
             __syncwarp();
@@ -1082,7 +1086,8 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                         int zi = (v - tv0) * tw + (u - tu0);
                         unsigned d = 0;
                         int tri = -1;
-                        if (K32) {
+                        if (!PERCH_CHECKED((unsigned)zi < (unsigned)(tw * (tv1 - tv0)), a.err)) {
+                        } else if (K32) {
                             uint32_t w = zbuf[zi];
                             if (w != empty32) { d = w >> 16; tri = (int)(w & 0xFFFFu); }
                         } else {
@@ -1147,7 +1152,8 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                         } else if (!EQ3) {
                             if (pu >= vbox[0] && pu < vbox[2] && pv >= mv0 && pv < mv1) {
                                 int bit = (pv - mv0) * vw + (pu - vbox[0]);
-                                atomicOr(&S.marks[bit >> 5], 1u << (bit & 31));
+                                if (PERCH_CHECKED((unsigned)bit < 32u * (unsigned)a.mark_words, a.err))
+                                    atomicOr(&S.marks[bit >> 5], 1u << (bit & 31));
                             }
                         }
                     }
@@ -1286,6 +1292,8 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
                 }
                 ++n_in;
                 int bit = (v - mv0) * vw + (u - s_vbox[0]);
+                if (!PERCH_CHECKED((unsigned)bit < (jo1 ? (unsigned)a.mark_words / 2u : 32u * (unsigned)a.mark_words), a.err))
+                    continue;
                 unsigned mk = jo1 ? (reinterpret_cast<const unsigned long long*>(S.marks)[bit] != kEmptyKey)
                                   : (S.marks[bit >> 5] >> (bit & 31)) & 1u;
                 if (TREE && !mk) mk = (__ldg(&J.tree.mark[pix >> 5]) >> (pix & 31)) & 1u;
@@ -1835,7 +1843,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_gicp(GicpArgs a)
     if (s_slot < 0) return;
     const unsigned long long* vc = a.vcache ? a.vcache + (size_t)s_slot * a.vstride : nullptr;
     float4* src = a.src + (size_t)s_slot * 2 * (size_t)a.src_cap;
-    const MarkBand nomark = {nullptr, 0, 0, 0, 0, 0};
+    const MarkBand nomark = {nullptr, 0, 0, 0, 0, 0, a.err};
     for (;;) {
         if (threadIdx.x == 0) s_h = (long long)atomicAdd(a.next, 1u);
         __syncthreads();
@@ -2164,8 +2172,10 @@ __global__ void __launch_bounds__(kBestThreads) k_best(BestArgs a)
     __syncthreads();
     m = block_best(m, sh);
     if (threadIdx.x == 0) {
-        *a.best_index = m.idx;
-        *a.best_cost = (int32_t)(m.hi >> 32);
+        if (a.best_index) *a.best_index = m.idx;
+        if (a.best_cost) *a.best_cost = (int32_t)(m.hi >> 32);
+        // (J << 32) | id: the smallest such key over several shards is their winner
+        if (a.key) *a.key = m.hi | (m.id & 0xFFFFFFFFull);
         *a.ticket = 0u;
     }
 }

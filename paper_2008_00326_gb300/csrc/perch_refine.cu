@@ -125,10 +125,13 @@ perch_status perch_refine_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mes
     if (!finite(gp.stop_rotation_rad) || !finite(gp.stop_translation_m) || gp.stop_rotation_rad < 0.0f ||
         gp.stop_translation_m < 0.0f)
         return fail(c, PERCH_E_INVALID, "stop thresholds must be finite and >= 0");
+    perch_status st = refuse_while_serving(c);
+    if (st != PERCH_OK) return st;
     DeviceGuard g(c->device);
+    Range r("perch: GICP refinement");
     perch::Job J;
     int mw;
-    perch_status st = make_job(c, scene_id, mesh_id, label, roi, poses, nullptr, n, &J, &mw, nullptr, nullptr);
+    st = make_job(c, scene_id, mesh_id, label, roi, poses, nullptr, n, &J, &mw, nullptr, nullptr);
     if (st != PERCH_OK) return st;
     J.sc.jo_mode = 0;
     // observed normals of the scene for this jump threshold (made once, synchronously)
@@ -142,7 +145,10 @@ perch_status perch_refine_hypotheses(perch_ctx* c, int32_t scene_id, int32_t mes
         S.nrm_jump = gp.normal_max_jump_units;
     }
     const float4* nrm = (const float4*)S.nrm;
-    if (cuda_stream) return run_gicp(c, c->plain, J, gp, nrm, poses_out, info, (cudaStream_t)cuda_stream);
+    if (cuda_stream) {
+        st = run_gicp(c, c->plain, J, gp, nrm, poses_out, info, (cudaStream_t)cuda_stream);
+        return st != PERCH_OK ? st : note_async_use(c, scene_id, mesh_id, (cudaStream_t)cuda_stream);
+    }
     const long long chunk = 1 << 18;
     const long long k0 = std::min<long long>(n, chunk);
     if ((st = ensure_stage(c, (size_t)k0 * (48 + 48 + 8))) != PERCH_OK) return st;

@@ -24,6 +24,7 @@ int64_t now_ns()
 
 struct ServedRequest {
     uint64_t ticket = 0;
+    int32_t scene_id = 0, mesh_id = 0;   // counted as users of both until the request completes
     perch::Job tmpl{};              // scene, mesh, label, ROI (pointers filled per launch)
     int mark_words = 0;
     std::vector<float> poses;       // copy of the caller's poses
@@ -54,8 +55,7 @@ struct perch_server {
     perch_ctx* c = nullptr;
     perch_server_config cfg{};
     std::vector<Slot> slots;
-    std::mutex mu;                  // queue, slots, tickets
-    std::mutex ctx_mu;              // context state used by submit and the scheduler
+    std::mutex mu;                  // queue, slots, tickets (the context's own state: c->mu)
     std::condition_variable cv_sched, cv_done, cv_wait;
     std::deque<std::shared_ptr<ServedRequest>> pending;
     int64_t pending_hyps = 0;
@@ -141,7 +141,7 @@ void serve_schedule(perch_server* S)
                                                 cudaMemcpyDeviceToHost, js);
                 return r ? r : cudaEventRecord(slot.req_done[j], js);
             };
-            std::lock_guard<std::mutex> g(S->ctx_mu);
+            std::lock_guard<std::mutex> g(S->c->mu);
             st = run_jobs(S->c, slot.X, jobs, mw, S->c->cfg, slot.stream, nullptr, &readback);
         }
         cudaEventRecord(slot.done, slot.stream);
@@ -174,6 +174,11 @@ void serve_complete(perch_server* S)
             if (e != cudaSuccess && r->status == PERCH_OK) r->status = PERCH_E_CUDA;
             if (r->status == PERCH_OK)
                 std::memcpy(r->user_costs, slot.h_costs + 2 * slot.offsets[k], r->n * 2 * sizeof(int32_t));
+            {
+                // its scene and mesh may be released from now on
+                std::lock_guard<std::mutex> g(S->c->mu);
+                count_users(S->c, r->scene_id, r->mesh_id, -1);
+            }
             r->t_done = now_ns();
             std::lock_guard<std::mutex> g(S->mu);
             r->done = true;
@@ -238,6 +243,7 @@ perch_status perch_server_start(perch_ctx* c, const perch_server_config* cfg, pe
         delete S;
         return st;
     }
+    c->servers.fetch_add(1);
     S->sched = std::thread(serve_schedule, S);
     S->completer = std::thread(serve_complete, S);
     *out = S;
@@ -250,19 +256,25 @@ perch_status perch_submit(perch_server* S, const perch_request* req, uint64_t* t
     if (!req->poses || !req->costs || req->n < 1) return PERCH_E_INVALID;
     if (req->n > S->cfg.max_batch_hypotheses) return PERCH_E_BUDGET;
     auto r = std::make_shared<ServedRequest>();
+    r->poses.assign(req->poses, req->poses + 12 * req->n);
+    r->user_costs = req->costs;
+    r->n = req->n;
+    r->scene_id = req->scene_id;
+    r->mesh_id = req->mesh_id;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stopping) return PERCH_E_BUSY;
     {
-        std::lock_guard<std::mutex> g(S->ctx_mu);
+        // validated and counted as a user of its scene and mesh under the
+        // context's lock, so a concurrent release either precedes it (the
+        // ids are gone: PERCH_E_NOTFOUND) or is refused (PERCH_E_BUSY)
+        std::lock_guard<std::mutex> g(S->c->mu);
         const int32_t* roi = (req->roi[2] > req->roi[0] && req->roi[3] > req->roi[1]) ? req->roi : nullptr;
         perch_status st = make_job(S->c, req->scene_id, req->mesh_id, req->label, roi, nullptr, nullptr,
                                    req->n, &r->tmpl, &r->mark_words, nullptr, nullptr);
         if (st != PERCH_OK) return st;
+        count_users(S->c, req->scene_id, req->mesh_id, +1);
     }
-    r->poses.assign(req->poses, req->poses + 12 * req->n);
-    r->user_costs = req->costs;
-    r->n = req->n;
     r->t_submit = now_ns();
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (S->stopping) return PERCH_E_BUSY;
     r->ticket = S->next_ticket++;
     S->tickets[r->ticket] = r;
     S->pending.push_back(r);
@@ -309,6 +321,25 @@ perch_status perch_ticket_times(perch_server* S, uint64_t ticket, int64_t* submi
     return PERCH_OK;
 }
 
+perch_status perch_ticket_release(perch_server* S, uint64_t ticket)
+{
+    if (!S) return PERCH_E_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return PERCH_E_NOTFOUND;
+    if (!it->second->done) return PERCH_E_BUSY;
+    S->tickets.erase(it);
+    return PERCH_OK;
+}
+
+perch_status perch_server_tickets(perch_server* S, int64_t* held)
+{
+    if (!S || !held) return PERCH_E_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *held = (int64_t)S->tickets.size();
+    return PERCH_OK;
+}
+
 perch_status perch_server_stop(perch_server* S)
 {
     if (!S) return PERCH_OK;
@@ -332,6 +363,7 @@ perch_status perch_server_stop(perch_server* S)
         if (slot.done) cudaEventDestroy(slot.done);
         for (auto ev : slot.req_done) cudaEventDestroy(ev);
     }
+    c->servers.fetch_sub(1);
     delete S;
     return PERCH_OK;
 }

@@ -18,6 +18,8 @@ perch_status perch_tree_search(perch_ctx* c, int32_t scene_id, const perch_tree_
     if (!objects || !order || !pose_index || !level_cost) return fail(c, PERCH_E_INVALID, "null argument");
     if (K < 1 || K > 64) return fail(c, PERCH_E_INVALID, "K must be in [1, 64]");
     if (beam_width < 1 || beam_width > 4096) return fail(c, PERCH_E_INVALID, "beam_width must be in [1, 4096]");
+    if (refuse_while_serving(c) != PERCH_OK) return PERCH_E_BUSY;
+    Range r("perch: tree search");
     auto si = c->scenes.find(scene_id);
     if (si == c->scenes.end()) return fail(c, PERCH_E_NOTFOUND, "unknown scene %d", scene_id);
     if (si->second.ds.jo_mode != 0) return fail(c, PERCH_E_INVALID, "the tree search needs jo_mode 0");

@@ -30,7 +30,8 @@ EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_
            "perch_autotune", "perch_server_start", "perch_submit", "perch_poll", "perch_wait",
            "perch_ticket_times", "perch_server_stop", "perch_pose_proposals",
            "perch_default_gicp_params", "perch_refine_hypotheses", "perch_tree_search",
-           "perch_measure_smem_atomics", "perch_add_s", "perch_add_s_auc")
+           "perch_measure_smem_atomics", "perch_add_s", "perch_add_s_auc", "perch_sync",
+           "perch_ticket_release", "perch_server_tickets", "perch_best_key")
 
 
 class PerchError(RuntimeError):
@@ -106,6 +107,20 @@ class Server:
             raise PerchError(st, "perch_wait")
         return self._keep.pop(ticket)
 
+    def release(self, ticket):
+        """Forget a finished ticket (perch_ticket_release)."""
+        st = load().perch_ticket_release(self.h, ticket)
+        if st != PERCH_OK:
+            raise PerchError(st, "perch_ticket_release")
+
+    def held(self):
+        """Tickets the server holds (perch_server_tickets)."""
+        n = C.c_int64()
+        st = load().perch_server_tickets(self.h, C.byref(n))
+        if st != PERCH_OK:
+            raise PerchError(st, "perch_server_tickets")
+        return n.value
+
     def times(self, ticket):
         a = C.c_int64()
         b = C.c_int64()
@@ -148,11 +163,13 @@ _lib = None
 
 
 def load(path: str | None = None):
-    """Load libperch.so (in-tree).  Raises if it is missing: build it first."""
+    """Load libperch.so (in-tree; PERCH_LIB=checks in the environment loads
+    the debug build libperch_checks.so instead).  Raises if it is missing:
+    build it first."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or (_build.LIB_CHECKS if os.environ.get("PERCH_LIB") == "checks" else LIB_PATH)
     if not os.path.exists(path):
         raise RuntimeError(f"libperch.so not found at {path}; run __graft_entry__.build() "
                            "(the scoring path has no CPU fallback)")
@@ -192,6 +209,10 @@ def load(path: str | None = None):
         "perch_measure_smem_atomics": ([I32, P, P], I32),
         "perch_add_s": ([P, I32, P, P, I64, I32, P, P], I32),
         "perch_add_s_auc": ([P, I64, C.c_double, P], I32),
+        "perch_sync": ([P, P], I32),
+        "perch_best_key": ([P, P, P, I64, P, P], I32),
+        "perch_ticket_release": ([P, U64], I32),
+        "perch_server_tickets": ([P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -337,6 +358,14 @@ def _require_cuda(name, t, dtypes, min_numel=1):
         raise TypeError(f"{name} has dtype {t.dtype}; expected one of {dtypes}")
     if t.numel() < min_numel:
         raise ValueError(f"{name} needs at least {min_numel} elements")
+
+
+def perch_best_key(ctx, costs, key, ids=None, stream=None):
+    """The winner of costs as the packed key (J << 32) | id, written to the
+    one-element int64 CUDA tensor `key` on `stream` (device mode only)."""
+    n = costs.numel() // 2
+    _check(ctx, load().perch_best_key(ctx, _ptr_of(costs), None if ids is None else _ptr_of(ids), n,
+                                       _ptr_of(key), getattr(stream, "cuda_stream", stream)))
 
 
 def perch_best_noalloc(costs, ids, out_index, out_cost, stream=None):
@@ -501,6 +530,12 @@ def perch_measure_smem_atomics(device=0):
     if st != PERCH_OK:
         raise PerchError(st, "perch_measure_smem_atomics")
     return a.value, b.value
+
+
+def perch_sync(ctx, stream=None):
+    """Wait for `stream` (None: the context's stream) and raise if the kernels
+    of earlier asynchronous calls reported an error."""
+    _check(ctx, load().perch_sync(ctx, getattr(stream, "cuda_stream", stream)))
 
 
 def perch_set_launch_config(ctx, threads, zbuf_words, mark_bits=0):

@@ -469,14 +469,16 @@ _TABLETOP_3OBJ_DIST = 1.05
 
 
 def tabletop_3obj(seed=1002, noise_m=0.003, occluder_frac=0.2, grid_half=21, n_yaw=16,
-                  W=640, H=480, tri_scale=1.0):
+                  W=640, H=480, tri_scale=1.0, yaw_phase=0.0):
     """Ellipsoid + two same-shape cylinders of different colour on a table.
 
     Ground truth on the hypothesis grid: positions on the 1 cm lattice (the
     layout above plus a seeded offset of -1..1 cm) and yaws from the n_yaw
     set, so that Request.gt_index names the true pose.  Hypotheses per
     object: (2*grid_half+1)^2 positions at 1 cm x n_yaw yaws centred on the
-    object's position.
+    object's position.  yaw_phase (a fraction of the yaw step) shifts the
+    hypotheses' yaws, not the scene: shards of a finer yaw grid for several
+    processes; gt_index is then -1.
     """
     rng = np.random.default_rng(seed)
     f = 615.0 * W / 640.0
@@ -512,12 +514,12 @@ def tabletop_3obj(seed=1002, noise_m=0.003, occluder_frac=0.2, grid_half=21, n_y
     depth = depth.astype(np.uint16)
     params = Params(delta_m=0.01, tau_c=12.5, color_check=1, occ_margin_units=100)
     steps = np.arange(-grid_half, grid_half + 1) * 0.01
-    yaws = np.arange(n_yaw) * (2 * math.pi / n_yaw)
+    yaws = (np.arange(n_yaw) + yaw_phase) * (2 * math.pi / n_yaw)
     reqs = []
     for k in range(3):
         cxg, cyg = pos[k]
         poses = _grid_poses(r_wc, t_wc, cxg + steps, cyg + steps, yaws)
-        gt_index = int((grid_half * len(steps) + grid_half) * n_yaw + yaw_index[k])
+        gt_index = int((grid_half * len(steps) + grid_half) * n_yaw + yaw_index[k]) if yaw_phase == 0 else -1
         reqs.append(Request(k, -1, (0, 0, W, H), poses, gt_index))
     return Scene("tabletop_3obj", W, H, f, f, cx, cy, depth, rgb, None, params, meshes, reqs, gts)
 

@@ -504,8 +504,9 @@ def served_leg(P, dev, seed=9):
         sid = ctx.set_observation(sc)
         mids = [ctx.load_mesh(m) for m in sc.meshes]
         kinds.append([(sid, mids[r.mesh_index], r.label, r.roi, r.poses) for r in sc.requests])
-    mixed = _served_rates(P, ctx, kinds, (5, 20, 50, 100, 200), 120, seed)
-    small = _served_rates(P, ctx, [kinds[0], kinds[2]], (50, 200, 500, 1000), 300, seed + 1)
+    # enough requests per rate that p99 is not just the slowest one or two
+    mixed = _served_rates(P, ctx, kinds, (5, 20, 50, 100, 200), 300, seed, window_s=3.0)
+    small = _served_rates(P, ctx, [kinds[0], kinds[2]], (50, 200, 500, 1000), 600, seed + 1, window_s=3.0)
     resident = ctx.hbm_used
     ctx.close()
     return {"server": {"slots": 2, "max_batch_hypotheses": 1 << 16, "hbm_budget_bytes": budget,

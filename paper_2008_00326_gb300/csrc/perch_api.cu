@@ -369,6 +369,55 @@ using namespace perch_host;
 
 namespace {
 
+// Dense cell index over the near-cell box (at most 2^24 cells): the cloud
+// re-sorted by cell (z-major, then y, then x) with each cell's start, so that
+// the radius search reads a row of three cells as one run instead of probing
+// the hash table for each of 27 cells.  The hash table is then no longer
+// needed and is freed.  A larger box keeps the hash table.
+perch_status build_dense_cells(perch_ctx* c, SceneRec& s, long long cells)
+{
+    perch::DevScene& d = s.ds;
+    d.cell_start = nullptr;
+    if (d.n_pts <= 0 || cells > (1ll << 24)) return PERCH_OK;
+    const size_t n = (size_t)cells, n_tiles = (n + 1023) / 1024;
+    void *count = nullptr, *cursor = nullptr, *sums = nullptr, *out = nullptr;
+    auto cleanup = [&]() { dfree(c, count); dfree(c, cursor); dfree(c, sums); dfree(c, out); };
+    perch_status st;
+    if ((st = dalloc(c, (n + 1) * 4, &s.cstart)) || (st = dalloc(c, n * 4, &count)) ||
+        (st = dalloc(c, n * 4, &cursor)) || (st = dalloc(c, n_tiles * 4, &sums)) ||
+        (st = dalloc(c, (size_t)d.n_pts * sizeof(float4), &out))) {
+        cleanup();
+        dfree(c, s.cstart);
+        s.cstart = nullptr;
+        return st;
+    }
+    const uint32_t last = (uint32_t)d.n_pts;
+    cudaError_t e = cudaMemsetAsync(count, 0, n * 4, c->stream);
+    if (!e) e = cudaMemsetAsync(cursor, 0, n * 4, c->stream);
+    if (!e) e = perch::launch_dense_cells(d, (uint32_t*)count, (uint32_t*)cursor, (uint32_t*)sums,
+                                          (uint32_t*)s.cstart, (float4*)out, c->stream);
+    if (!e) e = cudaMemcpyAsync((uint32_t*)s.cstart + n, &last, 4, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) {
+        cleanup();
+        dfree(c, s.cstart);
+        s.cstart = nullptr;
+        return cuda_fail(c, e, "dense cell index");
+    }
+    dfree(c, count);
+    dfree(c, cursor);
+    dfree(c, sums);
+    dfree(c, s.pts);
+    dfree(c, s.table);
+    s.pts = out;
+    s.table = nullptr;
+    d.pts = (const float4*)out;
+    d.table = nullptr;
+    d.table_mask = 0;
+    d.cell_start = (const uint32_t*)s.cstart;
+    return PERCH_OK;
+}
+
 // Near-cell bitmap of an observation: one bit per hash cell of the observed
 // points' cell box grown by one, set iff one of the cell's 27 neighbours holds
 // a point.  Skipped (no filter) when the box exceeds 2^27 cells.
@@ -406,7 +455,7 @@ perch_status build_near_cells(perch_ctx* c, SceneRec& s)
     dfree(c, occ);
     if (e) return cuda_fail(c, e, "near-cell bitmap");
     d.near_bits = (const uint32_t*)s.near;
-    return PERCH_OK;
+    return build_dense_cells(c, s, cells);
 }
 
 }  // namespace
@@ -639,11 +688,11 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     };
     auto cleanup_scene = [&]() {
         dfree(c, s.depth); dfree(c, s.labels); dfree(c, s.lab); dfree(c, s.pts); dfree(c, s.table); dfree(c, s.nrm);
-        dfree(c, s.near);
+        dfree(c, s.near); dfree(c, s.cstart); dfree(c, s.pxyz);
     };
     if ((st = dalloc(c, npx * sizeof(uint16_t), &s.depth)) ||
         (labels && (st = dalloc(c, npx * sizeof(int32_t), &s.labels))) ||
-        (st = dalloc(c, npx * sizeof(float4), &s.lab)) ||
+        (st = dalloc(c, npx * sizeof(float4), &s.lab)) || (st = dalloc(c, npx * sizeof(float4), &s.pxyz)) ||
         (st = dalloc(c, std::max<long long>(1, n_valid) * sizeof(float4), &s.pts)) ||
         (st = dalloc(c, (size_t)cap * sizeof(uint4), &big)) ||
         (st = dalloc(c, npx * 3, &d_rgb)) || (st = dalloc(c, npx * sizeof(int32_t), &slot)) ||
@@ -662,6 +711,7 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     d.delta = p.delta_m;
     d.delta2 = p.delta_m * p.delta_m;
     d.cell = cell;
+    d.inv_cell = 1.0f / cell;
     d.tau_c = p.tau_c;
     d.z_near = p.z_near_m;
     d.color_check = p.color_check;
@@ -671,6 +721,7 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     d.depth = (const uint16_t*)s.depth;
     d.labels = (const int32_t*)s.labels;
     d.lab = (const float4*)s.lab;
+    d.pxyz = (const float4*)s.pxyz;
     d.pts = (const float4*)s.pts;
     d.table = (const uint4*)big;
     d.table_mask = cap - 1;
@@ -683,6 +734,7 @@ perch_status perch_set_observation(perch_ctx* c, const uint16_t* depth, const ui
     b.start = (uint32_t*)start;
     b.n_valid = (int*)nvalid;
     b.lab = (float4*)s.lab;
+    b.pxyz = (float4*)s.pxyz;
     b.pts = (float4*)s.pts;
     b.table = (uint4*)big;
     if (!e) e = perch::launch_build(d, b, cap, (const uint8_t*)d_rgb, c->d_err, c->stream);
@@ -744,7 +796,7 @@ perch_status perch_release_scene(perch_ctx* c, int32_t scene_id)
                                      "asynchronous calls)", scene_id, s.use.users, s.use.pending.size());
     cudaStreamSynchronize(c->stream);
     dfree(c, s.depth); dfree(c, s.labels); dfree(c, s.lab); dfree(c, s.pts); dfree(c, s.table); dfree(c, s.nrm);
-    dfree(c, s.near);
+    dfree(c, s.near); dfree(c, s.cstart); dfree(c, s.pxyz);
     c->scenes.erase(it);
     return PERCH_OK;
 }

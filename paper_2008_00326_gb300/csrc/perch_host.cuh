@@ -42,11 +42,13 @@ struct SceneRec {
     void* depth = nullptr;
     void* labels = nullptr;
     void* lab = nullptr;
+    void* pxyz = nullptr;          // per-pixel observed points (DevScene::pxyz)
     void* pts = nullptr;
     void* table = nullptr;
     void* nrm = nullptr;           // observed normals (GICP targets), made on first use
     int nrm_jump = -1;             // the normal_max_jump_units they were made with
     void* near = nullptr;          // near-cell bitmap (DevScene::near_bits)
+    void* cstart = nullptr;        // dense cell index (DevScene::cell_start)
     UseTrack use;
 };
 

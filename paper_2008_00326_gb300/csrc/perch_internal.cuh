@@ -16,12 +16,13 @@ constexpr double kMaxCellCoord = 1.0e5;        // |coordinate / cell| bound for 
 struct DevScene {
     int W, H;
     float fx, fy, cx, cy;
-    float delta, delta2, cell, tau_c, z_near;
+    float delta, delta2, cell, inv_cell, tau_c, z_near;   // inv_cell = fl(1 / cell)
     int color_check, stride, occ_margin;
     int jo_mode;              // 0: NN marks (Sec. IV-A kernel); 1: Eq. 3 with the Eq. 2 test
     const uint16_t* depth;    // H*W
     const int32_t* labels;    // H*W or nullptr
     const float4* lab;        // H*W: (L, a, b, 0)
+    const float4* pxyz;       // H*W: back-projected point of each pixel of I, w = 1 (w = 0: not in I)
     const float4* pts;        // n_pts, grouped by hash cell: (x, y, z, (v << 16 | u) bits)
     const uint4* table;       // hash slots: (key lo, key hi, start, count)
     uint32_t table_mask;
@@ -31,6 +32,11 @@ struct DevScene {
     // cells outside the box have none.  nullptr: no filter.
     const uint32_t* near_bits;
     int near_lo[3], near_n[3];
+    // dense cell index over the same box (z-major, then y, then x): pts is
+    // sorted by cell and cell c holds pts[cell_start[c], cell_start[c + 1]),
+    // so the three cells x-1..x+1 of a row are one contiguous run.  nullptr:
+    // the box is too large, the hash table is used instead.
+    const uint32_t* cell_start;
 };
 
 // Device-resident mesh.
@@ -164,6 +170,7 @@ struct BuildBuffers {
     int* n_valid;             // 2: valid points, occupied cells
     // outputs (owned by the scene)
     float4* lab;              // H*W
+    float4* pxyz;             // H*W
     float4* pts;              // n_points capacity (H*W)
     uint4* table;             // table capacity
 };
@@ -175,6 +182,12 @@ cudaError_t launch_compact_table(const uint4* big, uint32_t cap_big, uint4* smal
 cudaError_t launch_cell_bounds(const DevScene& sc, int* bounds, cudaStream_t s);
 // Fill sc.near_bits (zeroed) through the occupancy bitmap occ (zeroed, same size).
 cudaError_t launch_near_cells(const DevScene& sc, uint32_t* occ, uint32_t* near_bits, cudaStream_t s);
+// Dense cell index over the near-cell box: cell_start (n_cells + 1 words;
+// the last one is written by the caller) and the points re-sorted by cell
+// into out.  count and cursor (n_cells words each) and tile_sums
+// ((n_cells + 1023) / 1024 words) are zeroed scratch.
+cudaError_t launch_dense_cells(const DevScene& sc, uint32_t* count, uint32_t* cursor, uint32_t* tile_sums,
+                               uint32_t* cell_start, float4* out, cudaStream_t s);
 
 // Argmin of J = J_o + J_r (ties to the lowest id / index).  The kernel
 // launches at most kBestMaxBlocks blocks; each leaves three 64-bit words

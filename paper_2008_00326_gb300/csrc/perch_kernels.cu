@@ -117,9 +117,14 @@ __device__ __forceinline__ float3 back_project(const DevScene& sc, int u, int v,
     return make_float3(x, y, z);
 }
 
-__device__ __forceinline__ int cell_coord(float x, float cell)
+// Hash-cell coordinate floor(x / cell), taken as floor(fl(x * fl(1 / cell))):
+// for two points within delta of each other on an axis the two products
+// differ by at most delta (1 + 2^-22) / cell + 2 * 1e5 * 2^-24 < 0.997 (cell =
+// delta (1 + 1/64), coordinates below 1e5 cells), so their cells are at most
+// one apart -- the radius search's 27 cells hold every point within delta.
+__device__ __forceinline__ int cell_coord(float x, float inv_cell)
 {
-    return __float2int_rd(__fdiv_rn(x, cell));
+    return __float2int_rd(__fmul_rn(x, inv_cell));
 }
 
 __device__ __forceinline__ unsigned long long cell_key(int cx, int cy, int cz)
@@ -143,7 +148,7 @@ __device__ __forceinline__ uint32_t hash_slot(unsigned long long k, uint32_t mas
 // observation build: per-pixel CIELAB, cloud I, voxel hash (cell = delta*(1+1/64))
 // ---------------------------------------------------------------------------
 
-__global__ void k_obs_insert(DevScene sc, const uint8_t* __restrict__ rgb, float4* lab,
+__global__ void k_obs_insert(DevScene sc, const uint8_t* __restrict__ rgb, float4* lab, float4* pxyz,
                              int32_t* slot_of_pixel, unsigned long long* keys, uint32_t* count,
                              uint32_t mask, int* n_valid, int* err)
 {
@@ -155,10 +160,12 @@ __global__ void k_obs_insert(DevScene sc, const uint8_t* __restrict__ rgb, float
     lab[i] = make_float4(L.x, L.y, L.z, 0.0f);
     unsigned d = sc.depth[i];
     int slot = -1;
+    pxyz[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (d != 0 && u % sc.stride == 0 && v % sc.stride == 0) {
         float3 p = back_project(sc, u, v, d);
-        unsigned long long k = cell_key(cell_coord(p.x, sc.cell), cell_coord(p.y, sc.cell),
-                                        cell_coord(p.z, sc.cell));
+        pxyz[i] = make_float4(p.x, p.y, p.z, 1.0f);
+        unsigned long long k = cell_key(cell_coord(p.x, sc.inv_cell), cell_coord(p.y, sc.inv_cell),
+                                        cell_coord(p.z, sc.inv_cell));
         uint32_t h = hash_slot(k, mask);
         for (uint32_t probe = 0; probe <= mask; ++probe) {
             unsigned long long prev = atomicCAS(&keys[h], kEmptyKey, k);
@@ -273,7 +280,7 @@ __global__ void k_cell_bounds(DevScene sc, int* bounds)
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sc.n_pts; i += gridDim.x * blockDim.x) {
         const float4 p = sc.pts[i];
-        const int c[3] = {cell_coord(p.x, sc.cell), cell_coord(p.y, sc.cell), cell_coord(p.z, sc.cell)};
+        const int c[3] = {cell_coord(p.x, sc.inv_cell), cell_coord(p.y, sc.inv_cell), cell_coord(p.z, sc.inv_cell)};
 #pragma unroll
         for (int a = 0; a < 3; ++a) { lo[a] = min(lo[a], c[a]); hi[a] = max(hi[a], c[a]); }
     }
@@ -302,8 +309,8 @@ __global__ void k_cell_occupancy(DevScene sc, uint32_t* occ)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sc.n_pts; i += gridDim.x * blockDim.x) {
         const float4 p = sc.pts[i];
-        const long long b = near_index(sc, cell_coord(p.x, sc.cell), cell_coord(p.y, sc.cell),
-                                       cell_coord(p.z, sc.cell));
+        const long long b = near_index(sc, cell_coord(p.x, sc.inv_cell), cell_coord(p.y, sc.inv_cell),
+                                       cell_coord(p.z, sc.inv_cell));
         if (b >= 0) atomicOr(&occ[b >> 5], 1u << (b & 31));
     }
 }
@@ -338,6 +345,49 @@ cudaError_t launch_near_cells(const DevScene& sc, uint32_t* occ, uint32_t* near_
     k_cell_occupancy<<<min(1024, (sc.n_pts + 255) / 256), 256, 0, s>>>(sc, occ);
     const long long n = (long long)sc.near_n[0] * sc.near_n[1] * sc.near_n[2];
     k_cell_dilate<<<(unsigned)std::min<long long>(4096, (n + 255) / 256), 256, 0, s>>>(sc, occ, near_bits);
+    return cudaGetLastError();
+}
+
+// ---- dense cell index: count per cell, exclusive scan, scatter by cell
+
+__global__ void k_dense_count(DevScene sc, uint32_t* count)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sc.n_pts; i += gridDim.x * blockDim.x) {
+        const float4 p = sc.pts[i];
+        const long long c = near_index(sc, cell_coord(p.x, sc.inv_cell), cell_coord(p.y, sc.inv_cell),
+                                       cell_coord(p.z, sc.inv_cell));
+        if (c >= 0) atomicAdd(&count[c], 1u);
+    }
+}
+
+__global__ void k_add_tile_offsets(uint32_t* start, const uint32_t* tile_offsets, uint32_t n)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) start[i] += tile_offsets[i >> 10];
+}
+
+__global__ void k_dense_scatter(DevScene sc, const uint32_t* start, uint32_t* cursor, float4* out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sc.n_pts; i += gridDim.x * blockDim.x) {
+        const float4 p = sc.pts[i];
+        const long long c = near_index(sc, cell_coord(p.x, sc.inv_cell), cell_coord(p.y, sc.inv_cell),
+                                       cell_coord(p.z, sc.inv_cell));
+        if (c >= 0) out[start[c] + atomicAdd(&cursor[c], 1u)] = p;
+    }
+}
+
+cudaError_t launch_dense_cells(const DevScene& sc, uint32_t* count, uint32_t* cursor, uint32_t* tile_sums,
+                               uint32_t* cell_start, float4* out, cudaStream_t s)
+{
+    const long long n = (long long)sc.near_n[0] * sc.near_n[1] * sc.near_n[2];
+    if (sc.n_pts <= 0 || n <= 0 || n > 0xFFFFFFFFll) return cudaErrorInvalidValue;
+    const unsigned blocks_pts = (unsigned)std::min(1024, (sc.n_pts + 255) / 256);
+    k_dense_count<<<blocks_pts, 256, 0, s>>>(sc, count);
+    const uint32_t n_tiles = (uint32_t)((n + 1023) / 1024);
+    k_scan_tiles<<<n_tiles, 1024, 0, s>>>(count, cell_start, tile_sums, (uint32_t)n);
+    k_scan_sums<<<1, 1024, 0, s>>>(tile_sums, n_tiles);
+    k_add_tile_offsets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cell_start, tile_sums, (uint32_t)n);
+    k_dense_scatter<<<blocks_pts, 256, 0, s>>>(sc, cell_start, cursor, out);
     return cudaGetLastError();
 }
 
@@ -388,7 +438,7 @@ cudaError_t launch_build(const DevScene& sc, const BuildBuffers& b, uint32_t cap
     if ((e = cudaMemsetAsync(b.cursor, 0, sizeof(uint32_t) * cap, s))) return e;
     if ((e = cudaMemsetAsync(b.n_valid, 0, 2 * sizeof(int), s))) return e;
     int blocks = (npx + 255) / 256;
-    k_obs_insert<<<blocks, 256, 0, s>>>(sc, rgb_dev, b.lab, b.slot_of_pixel, b.keys, b.count,
+    k_obs_insert<<<blocks, 256, 0, s>>>(sc, rgb_dev, b.lab, b.pxyz, b.slot_of_pixel, b.keys, b.count,
                                         cap - 1, b.n_valid, err);
     uint32_t n_tiles = (cap + 1023) / 1024;
     // the tile sums of the scan live just past the cursors
@@ -436,10 +486,27 @@ __device__ __forceinline__ bool owns(int dx, int dy)
 __device__ __forceinline__ int floor16(int x) { return x >> 4; }         // arithmetic shift
 __device__ __forceinline__ int ceil16(int x) { return -((-x) >> 4); }
 
-// Triangle set-up at a pose: transform, near/guard-band cull, projection,
-// 4-bit snap, orientation.  Returns false if culled or degenerate.
-__device__ __forceinline__ bool setup_triangle(const DevScene& sc, const DevMesh& m,
-                                               const float* P, int t, TriSetup& o)
+// Doubled area and orientation of a loaded triangle: a negative area swaps
+// vertices 1 and 2 (two-sided rendering).  False if degenerate (A == 0).
+__device__ __forceinline__ bool orient_triangle(TriSetup& o)
+{
+    int A = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], o.x[2], o.y[2]);
+    if (A == 0) return false;
+    if (A < 0) {
+        int tx = o.x[1], ty = o.y[1], tvid = o.vid[1];
+        float ti = o.iz[1];
+        o.x[1] = o.x[2]; o.y[1] = o.y[2]; o.iz[1] = o.iz[2]; o.vid[1] = o.vid[2];
+        o.x[2] = tx; o.y[2] = ty; o.iz[2] = ti; o.vid[2] = tvid;
+        A = -A;
+    }
+    o.A = A;
+    return true;
+}
+
+// Triangle loaded at a pose: transform, near/guard-band cull, projection,
+// 4-bit snap (orient_triangle completes the set-up).  False if culled.
+__device__ __forceinline__ bool load_triangle(const DevScene& sc, const DevMesh& m,
+                                              const float* P, int t, TriSetup& o)
 {
     int4 tv = __ldg(&m.tris[t]);
     int vids[3] = {tv.x, tv.y, tv.z};
@@ -461,19 +528,9 @@ __device__ __forceinline__ bool setup_triangle(const DevScene& sc, const DevMesh
         if (!(sx >= gx0) || !(sx < gx1) || !(sy >= gy0) || !(sy < gy1)) return false;
         o.x[k] = __float2int_rn(sx);
         o.y[k] = __float2int_rn(sy);
-        o.iz[k] = __fdiv_rn(1.0f, Z);
+        o.iz[k] = __frcp_rn(Z);        // = fl(1 / Z), as the division would give
         o.vid[k] = vids[k];
     }
-    int A = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], o.x[2], o.y[2]);
-    if (A == 0) return false;
-    if (A < 0) {
-        int tx = o.x[1], ty = o.y[1], tvid = o.vid[1];
-        float ti = o.iz[1];
-        o.x[1] = o.x[2]; o.y[1] = o.y[2]; o.iz[1] = o.iz[2]; o.vid[1] = o.vid[2];
-        o.x[2] = tx; o.y[2] = ty; o.iz[2] = ti; o.vid[2] = tvid;
-        A = -A;
-    }
-    o.A = A;
     return true;
 }
 
@@ -543,11 +600,13 @@ static_assert(kWarpScratch % 16 == 0, "per-warp scratch keeps 16-byte alignment"
 static_assert(sizeof(WarpProbe) % 16 == 0, "per-warp scratch keeps 16-byte alignment");
 
 // Warp-cooperative lookup of the 27-cell neighbourhoods of up to kGroups
-// query cells at once: lane j < 27 probes neighbour j of every cell, issuing
-// all first-slot loads before resolving any (the table lives in L2, so the
-// loads overlap).  Group g's non-empty runs are stored in neighbour order with
-// a running candidate count so that candidate i of the group is point
-// runs[r].x + i for the first run r with i < runs[r].y.
+// query cells at once.  With the dense cell index, lane j < 9 reads the two
+// bounds of one row's three cells (they are contiguous); otherwise lane
+// j < 27 probes the hash table for neighbour j, issuing all first-slot loads
+// before resolving any (the table lives in L2, so the loads overlap).  Group
+// g's non-empty runs are stored in order with a running candidate count so
+// that candidate i of the group is point runs[r].x + i for the first run r
+// with i < runs[r].y.
 __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, const int* gy,
                                              const int* gz, int ng, WarpProbe& W, int lane)
 {
@@ -556,39 +615,53 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
     for (int g = 0; g < kGroups; ++g) {
         if (g >= ng) break;
         uint32_t start = 0, cnt = 0;
-        bool hit = false;
-        unsigned long long key = kEmptyKey;
-        uint32_t cs = 0;
-        if (lane < 27) {
-            key = cell_key(gx[g] + dx, gy[g] + dy, gz[g] + dz);
-            // neighbouring query cells share most of their 27 neighbours: look in
-            // the warp's cache of recent lookups before going to the table
-            cs = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 58) & (kCellCache - 1);
-            const uint4 c = W.cache[cs];
-            hit = ((unsigned long long)c.x | ((unsigned long long)c.y << 32)) == key;
-            if (hit) {
-                start = c.z;
-                cnt = c.w;
-            } else {
-                uint32_t slot = hash_slot(key, sc.table_mask);
-                for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
-                    const uint4 x = __ldg(&sc.table[slot]);
-                    unsigned long long k = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
-                    if (k == key) {
-                        start = x.z;
-                        cnt = x.w;
-                        break;
-                    }
-                    if (k == kEmptyKey) break;
-                    slot = (slot + 1) & sc.table_mask;
+        if (sc.cell_start) {
+            // dense index: lane j < 9 takes row (y + j % 3 - 1, z + j / 3 - 1),
+            // whose cells x-1..x+1 are one run of the cell-sorted points
+            if (lane < 9) {
+                const int ry = gy[g] + lane % 3 - 1 - sc.near_lo[1], rz = gz[g] + lane / 3 - 1 - sc.near_lo[2];
+                const int x0 = max(gx[g] - 1 - sc.near_lo[0], 0), x1 = min(gx[g] + 1 - sc.near_lo[0], sc.near_n[0] - 1);
+                if (ry >= 0 && ry < sc.near_n[1] && rz >= 0 && rz < sc.near_n[2] && x0 <= x1) {
+                    const long long row = ((long long)rz * sc.near_n[1] + ry) * sc.near_n[0];
+                    start = __ldg(&sc.cell_start[row + x0]);
+                    cnt = __ldg(&sc.cell_start[row + x1 + 1]) - start;
                 }
             }
-        }
-        // fill the cache: one writer per cache slot among the lanes that missed
-        const unsigned miss = __ballot_sync(0xffffffffu, lane < 27 && !hit);
-        if (lane < 27 && !hit) {
-            const unsigned same = __match_any_sync(miss, cs);
-            if (lane == __ffs(same) - 1) W.cache[cs] = make_uint4((uint32_t)key, (uint32_t)(key >> 32), start, cnt);
+        } else {
+            bool hit = false;
+            unsigned long long key = kEmptyKey;
+            uint32_t cs = 0;
+            if (lane < 27) {
+                key = cell_key(gx[g] + dx, gy[g] + dy, gz[g] + dz);
+                // neighbouring query cells share most of their 27 neighbours: look in
+                // the warp's cache of recent lookups before going to the table
+                cs = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 58) & (kCellCache - 1);
+                const uint4 c = W.cache[cs];
+                hit = ((unsigned long long)c.x | ((unsigned long long)c.y << 32)) == key;
+                if (hit) {
+                    start = c.z;
+                    cnt = c.w;
+                } else {
+                    uint32_t slot = hash_slot(key, sc.table_mask);
+                    for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
+                        const uint4 x = __ldg(&sc.table[slot]);
+                        unsigned long long k = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+                        if (k == key) {
+                            start = x.z;
+                            cnt = x.w;
+                            break;
+                        }
+                        if (k == kEmptyKey) break;
+                        slot = (slot + 1) & sc.table_mask;
+                    }
+                }
+            }
+            // fill the cache: one writer per cache slot among the lanes that missed
+            const unsigned miss = __ballot_sync(0xffffffffu, lane < 27 && !hit);
+            if (lane < 27 && !hit) {
+                const unsigned same = __match_any_sync(miss, cs);
+                if (lane == __ffs(same) - 1) W.cache[cs] = make_uint4((uint32_t)key, (uint32_t)(key >> 32), start, cnt);
+            }
         }
         uint32_t incl = cnt;
 #pragma unroll
@@ -600,7 +673,7 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
         if (cnt != 0)
             W.runs[g][__popc(nonempty & ((1u << lane) - 1u))] =
                 make_int2((int)start - (int)(incl - cnt), (int)incl);
-        if (lane == 26) W.total[g] = (int)incl;
+        if (lane == 31) W.total[g] = (int)incl;
     }
 }
 
@@ -663,9 +736,9 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
     int cx = 0, cy = 0, cz = 0;
     unsigned long long key = kEmptyKey;
     if (valid) {
-        cx = cell_coord(qx, sc.cell);
-        cy = cell_coord(qy, sc.cell);
-        cz = cell_coord(qz, sc.cell);
+        cx = cell_coord(qx, sc.inv_cell);
+        cy = cell_coord(qy, sc.inv_cell);
+        cz = cell_coord(qz, sc.inv_cell);
         if (sc.near_bits) {
             // no observed point in the 27 cells: nothing to look up
             const long long b = near_index(sc, cx, cy, cz);
@@ -816,15 +889,15 @@ __device__ __forceinline__ void vertex_pass(const DevScene& sc, const DevMesh& m
                 uint32_t xs = (uint16_t)(int16_t)__float2int_rn(sx);
                 uint32_t ys = (uint16_t)(int16_t)__float2int_rn(sy);
                 rec = (unsigned long long)(xs | (ys << 16)) |
-                      ((unsigned long long)__float_as_uint(__fdiv_rn(1.0f, Z)) << 32);
+                      ((unsigned long long)__float_as_uint(__frcp_rn(Z)) << 32);
             }
         }
         vc[i] = rec;
     }
 }
 
-__device__ __forceinline__ bool setup_cached(const DevMesh& m, const unsigned long long* vc, int t,
-                                             TriSetup& o)
+__device__ __forceinline__ bool load_cached(const DevMesh& m, const unsigned long long* vc, int t,
+                                            TriSetup& o)
 {
     int4 tv = __ldg(&m.tris[t]);
     int vids[3] = {tv.x, tv.y, tv.z};
@@ -838,61 +911,94 @@ __device__ __forceinline__ bool setup_cached(const DevMesh& m, const unsigned lo
         o.iz[k] = __uint_as_float((uint32_t)(r >> 32));
         o.vid[k] = vids[k];
     }
-    int A = edge_fn(o.x[0], o.y[0], o.x[1], o.y[1], o.x[2], o.y[2]);
-    if (A == 0) return false;
-    if (A < 0) {
-        int tx = o.x[1], ty = o.y[1], tvid = o.vid[1];
-        float ti = o.iz[1];
-        o.x[1] = o.x[2]; o.y[1] = o.y[2]; o.iz[1] = o.iz[2]; o.vid[1] = o.vid[2];
-        o.x[2] = tx; o.y[2] = ty; o.iz[2] = ti; o.vid[2] = tvid;
-        A = -A;
-    }
-    o.A = A;
     return true;
 }
 
 template <bool VC>
+__device__ __forceinline__ bool load_tri(const DevScene& sc, const DevMesh& m, const float* P,
+                                         const unsigned long long* vc, int t, TriSetup& o)
+{
+    if (VC) return load_cached(m, vc, t, o);
+    return load_triangle(sc, m, P, t, o);
+}
+
+// Full set-up of triangle t at pose P: load, then orientation.  False if
+// culled or degenerate.
+template <bool VC>
 __device__ __forceinline__ bool get_triangle(const DevScene& sc, const DevMesh& m, const float* P,
                                              const unsigned long long* vc, int t, TriSetup& o)
 {
-    if (VC) return setup_cached(m, vc, t, o);
-    return setup_triangle(sc, m, P, t, o);
+    return load_tri<VC>(sc, m, P, vc, t, o) && orient_triangle(o);
+}
+
+// Coverage (edge functions and the ownership rule), depth and the z-buffer
+// update of sample (u, v) of a set-up triangle (vertices in 1/16 px, 1/Z,
+// doubled area A > 0, owns bits per edge), in the tile at (tu0, tv0).
+template <bool K32>
+__device__ __forceinline__ void raster_sample(const int* x, const int* y, const float* iz, int A, int owns_bits,
+                                              int tri, int u, int v, uint32_t* zbuf, int tu0, int tv0, int tw,
+                                              int tcap, int* err)
+{
+    const int sx = 16 * u, sy = 16 * v;
+    const int w0 = edge_fn(x[1], y[1], x[2], y[2], sx, sy);
+    const int w1 = edge_fn(x[2], y[2], x[0], y[0], sx, sy);
+    const int w2 = edge_fn(x[0], y[0], x[1], y[1], sx, sy);
+    const bool cov = (w0 > 0 || (w0 == 0 && (owns_bits & 1))) &&
+                     (w1 > 0 || (w1 == 0 && (owns_bits & 2))) &&
+                     (w2 > 0 || (w2 == 0 && (owns_bits & 4)));
+    unsigned d;
+    const int idx = (v - tv0) * tw + (u - tu0);
+    if (cov && sample_depth(w0, w1, w2, iz, A, d) && PERCH_CHECKED((unsigned)idx < (unsigned)tcap, err))
+        zmin<K32>(zbuf, idx, d, tri, err);
 }
 
 // Rasterise every triangle of mesh m at pose P into the z-buffer tile
 // [tu0,tu1) x [tv0,tv1) (row pitch tw).  A warp sets up 32 triangles (one per
-// lane), stages them in shared memory (TS, 32 entries per warp) and spreads
-// the pixels of their boxes evenly over its lanes (a prefix sum of the box
-// areas, then a binary search per pixel for its triangle).  No barrier inside.
+// lane); a triangle with one sample in its box is tested in its own lane, the
+// others are staged in shared memory (TS, 32 entries per warp) and the
+// samples of their boxes spread evenly over the lanes (a prefix sum of the box
+// areas, then a binary search per sample for its triangle).  No barrier inside.
 template <int NT, bool K32, bool VC>
 __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& mesh, const float* P,
                                             const unsigned long long* vc, TriStage* TS, uint32_t* zbuf,
                                             int tu0, int tv0, int tu1, int tv1, int tw, int* err)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tcap = tw * (tv1 - tv0);
     for (int base = warp * 32; base < mesh.n_tris; base += NT) {
         const int t = base + lane;
         int area = 0;
         TriSetup o;
-        if (t < mesh.n_tris && get_triangle<VC>(sc, mesh, P, vc, t, o)) {
+        // the sample box does not depend on the orientation: test it first, so
+        // that the many triangles covering no sample of the tile skip the rest
+        if (t < mesh.n_tris && load_tri<VC>(sc, mesh, P, vc, t, o)) {
             int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
             int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
             int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
             int v0 = max(ceil16(ymin), tv0), v1 = min(floor16(ymax), tv1 - 1);
-            if (u0 <= u1 && v0 <= v1) {
-                area = (u1 - u0 + 1) * (v1 - v0 + 1);
-                TriStage& e = TS[lane];
-                for (int k = 0; k < 3; ++k) { e.x[k] = o.x[k]; e.y[k] = o.y[k]; e.iz[k] = o.iz[k]; }
-                e.A = o.A;
-                e.tri = t;
-                e.u0 = u0;
-                e.v0 = v0;
-                e.bw = u1 - u0 + 1;
-                e.owns = (owns(o.x[2] - o.x[1], o.y[2] - o.y[1]) ? 1 : 0) |
-                         (owns(o.x[0] - o.x[2], o.y[0] - o.y[2]) ? 2 : 0) |
-                         (owns(o.x[1] - o.x[0], o.y[1] - o.y[0]) ? 4 : 0);
+            if (u0 <= u1 && v0 <= v1 && orient_triangle(o)) {
+                const int owns_bits = (owns(o.x[2] - o.x[1], o.y[2] - o.y[1]) ? 1 : 0) |
+                                      (owns(o.x[0] - o.x[2], o.y[0] - o.y[2]) ? 2 : 0) |
+                                      (owns(o.x[1] - o.x[0], o.y[1] - o.y[0]) ? 4 : 0);
+                if (u0 == u1 && v0 == v1) {
+                    // one sample in the box (most triangles of a fine mesh):
+                    // test it in this lane, no staging
+                    raster_sample<K32>(o.x, o.y, o.iz, o.A, owns_bits, t, u0, v0, zbuf, tu0, tv0, tw, tcap, err);
+                } else {
+                    area = (u1 - u0 + 1) * (v1 - v0 + 1);
+                    TriStage& e = TS[lane];
+                    for (int k = 0; k < 3; ++k) { e.x[k] = o.x[k]; e.y[k] = o.y[k]; e.iz[k] = o.iz[k]; }
+                    e.A = o.A;
+                    e.tri = t;
+                    e.u0 = u0;
+                    e.v0 = v0;
+                    e.bw = u1 - u0 + 1;
+                    e.owns = owns_bits;
+                }
             }
         }
+        // the larger boxes: their samples spread evenly over the lanes
+        if (__ballot_sync(0xffffffffu, area > 0) == 0u) continue;
         int incl = area;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -915,18 +1021,8 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
             const TriStage& e = TS[j];
             const int local = f - (j > 0 ? excl : 0);
             const int dv = local / e.bw;
-            const int u = e.u0 + (local - dv * e.bw), v = e.v0 + dv;
-            const int sx = 16 * u, sy = 16 * v;
-            const int w0 = edge_fn(e.x[1], e.y[1], e.x[2], e.y[2], sx, sy);
-            const int w1 = edge_fn(e.x[2], e.y[2], e.x[0], e.y[0], sx, sy);
-            const int w2 = edge_fn(e.x[0], e.y[0], e.x[1], e.y[1], sx, sy);
-            const bool cov = (w0 > 0 || (w0 == 0 && (e.owns & 1))) &&
-                             (w1 > 0 || (w1 == 0 && (e.owns & 2))) &&
-                             (w2 > 0 || (w2 == 0 && (e.owns & 4)));
-            unsigned d;
-            if (cov && sample_depth(w0, w1, w2, e.iz, e.A, d) &&
-                PERCH_CHECKED((unsigned)((v - tv0) * tw + (u - tu0)) < (unsigned)(tw * (tv1 - tv0)), err))
-                zmin<K32>(zbuf, (v - tv0) * tw + (u - tu0), d, e.tri, err);
+            raster_sample<K32>(e.x, e.y, e.iz, e.A, e.owns, e.tri, e.u0 + (local - dv * e.bw), e.v0 + dv, zbuf,
+                               tu0, tv0, tw, tcap, err);
         }
         __syncwarp();
     }
@@ -946,12 +1042,20 @@ __device__ __forceinline__ uint32_t interp_colour(const DevMesh& m, const TriSet
     const uint32_t c1 = __float_as_uint(__ldg(&m.verts[o.vid[1]].w));
     const uint32_t c2 = __float_as_uint(__ldg(&m.verts[o.vid[2]].w));
     const long long half = o.A / 2;
+    // floor(num / A) without a 64-bit division: a binary32 estimate from the
+    // reciprocal of A (relative error a few 2^-24, and the quotient is below
+    // 256, so the estimate is off by at most one) corrected exactly with
+    // integer arithmetic
+    const float rA = __frcp_rn(__int2float_rn(o.A));
     uint32_t crgb = 0;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         const long long num = w0 * ((c0 >> (8 * ch)) & 255) + w1 * ((c1 >> (8 * ch)) & 255) +
                               w2 * ((c2 >> (8 * ch)) & 255) + half;
-        crgb |= (uint32_t)(num / o.A) << (8 * ch);
+        long long q = __float2ll_rz(__fmul_rn(__ll2float_rn(num), rA));
+        const long long r = num - q * o.A;
+        q += (r >= o.A) - (r < 0);
+        crgb |= (uint32_t)q << (8 * ch);
     }
     return crgb;
 }
@@ -1272,13 +1376,13 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         for (int k = threadIdx.x; k < nu * nv; k += NT) {
             int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
             int pix = v * sc.W + u;
-            unsigned d = __ldg(&sc.depth[pix]);
-            if (d == 0) continue;
+            // the observed point of the pixel, back-projected once per scene
+            const float4 p = __ldg(&sc.pxyz[pix]);
+            if (p.w == 0.0f) continue;
             bool in;
             if (J.label >= 0) {
                 in = __ldg(&sc.labels[pix]) == J.label;
             } else {
-                float3 p = back_project(sc, u, v, d);
                 float e0 = __fsub_rn(p.x, P[3]), e1 = __fsub_rn(p.y, P[7]), e2 = __fsub_rn(p.z, P[11]);
                 float q0 = __fadd_rn(__fadd_rn(__fmul_rn(P[0], e0), __fmul_rn(P[4], e1)), __fmul_rn(P[8], e2));
                 float q1 = __fadd_rn(__fadd_rn(__fmul_rn(P[1], e0), __fmul_rn(P[5], e1)), __fmul_rn(P[9], e2));

@@ -506,9 +506,8 @@ __device__ __forceinline__ bool orient_triangle(TriSetup& o)
 // Triangle loaded at a pose: transform, near/guard-band cull, projection,
 // 4-bit snap (orient_triangle completes the set-up).  False if culled.
 __device__ __forceinline__ bool load_triangle(const DevScene& sc, const DevMesh& m,
-                                              const float* P, int t, TriSetup& o)
+                                              const float* P, int4 tv, TriSetup& o)
 {
-    int4 tv = __ldg(&m.tris[t]);
     int vids[3] = {tv.x, tv.y, tv.z};
     const float gx0 = (float)(-16 * sc.W), gx1 = (float)(32 * sc.W);
     const float gy0 = (float)(-16 * sc.H), gy1 = (float)(32 * sc.H);
@@ -873,6 +872,7 @@ __device__ __forceinline__ void vertex_pass(const DevScene& sc, const DevMesh& m
 {
     const float gx0 = (float)(-16 * sc.W), gx1 = (float)(32 * sc.W);
     const float gy0 = (float)(-16 * sc.H), gy1 = (float)(32 * sc.H);
+#pragma unroll 2
     for (int i = threadIdx.x; i < m.n_verts; i += nt) {
         float4 v = __ldg(&m.verts[i]);
         float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(P[0], v.x), __fmul_rn(P[1], v.y)),
@@ -896,30 +896,34 @@ __device__ __forceinline__ void vertex_pass(const DevScene& sc, const DevMesh& m
     }
 }
 
-__device__ __forceinline__ bool load_cached(const DevMesh& m, const unsigned long long* vc, int t,
-                                            TriSetup& o)
+__device__ __forceinline__ bool load_cached(const unsigned long long* vc, int4 tv, TriSetup& o)
 {
-    int4 tv = __ldg(&m.tris[t]);
-    int vids[3] = {tv.x, tv.y, tv.z};
+    // the three records are loaded before any is tested, so that all three
+    // loads are in flight together
+    const unsigned long long rec[3] = {vc[tv.x], vc[tv.y], vc[tv.z]};
+    const int vids[3] = {tv.x, tv.y, tv.z};
+    bool ok = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        unsigned long long r = vc[vids[k]];
-        int xs = (int16_t)(uint16_t)(r & 0xFFFFu);
-        if (xs == kCulledX) return false;
+        const unsigned long long r = rec[k];
+        const int xs = (int16_t)(uint16_t)(r & 0xFFFFu);
+        ok = ok && xs != kCulledX;
         o.x[k] = xs;
         o.y[k] = (int16_t)(uint16_t)((r >> 16) & 0xFFFFu);
         o.iz[k] = __uint_as_float((uint32_t)(r >> 32));
         o.vid[k] = vids[k];
     }
-    return true;
+    return ok;
 }
 
+// Triangle t (its vertex ids tv) loaded at pose P: from the vertex cache, or
+// transformed and snapped here.  False if culled.
 template <bool VC>
 __device__ __forceinline__ bool load_tri(const DevScene& sc, const DevMesh& m, const float* P,
-                                         const unsigned long long* vc, int t, TriSetup& o)
+                                         const unsigned long long* vc, int4 tv, TriSetup& o)
 {
-    if (VC) return load_cached(m, vc, t, o);
-    return load_triangle(sc, m, P, t, o);
+    if (VC) return load_cached(vc, tv, o);
+    return load_triangle(sc, m, P, tv, o);
 }
 
 // Full set-up of triangle t at pose P: load, then orientation.  False if
@@ -928,7 +932,7 @@ template <bool VC>
 __device__ __forceinline__ bool get_triangle(const DevScene& sc, const DevMesh& m, const float* P,
                                              const unsigned long long* vc, int t, TriSetup& o)
 {
-    return load_tri<VC>(sc, m, P, vc, t, o) && orient_triangle(o);
+    return load_tri<VC>(sc, m, P, vc, __ldg(&m.tris[t]), o) && orient_triangle(o);
 }
 
 // Coverage (edge functions and the ownership rule), depth and the z-buffer
@@ -965,13 +969,17 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tcap = tw * (tv1 - tv0);
+    // vertex ids of the lane's next triangle, loaded one iteration ahead
+    int4 tv_next = warp * 32 + lane < mesh.n_tris ? __ldg(&mesh.tris[warp * 32 + lane]) : make_int4(0, 0, 0, 0);
     for (int base = warp * 32; base < mesh.n_tris; base += NT) {
         const int t = base + lane;
+        const int4 tv = tv_next;
+        if (t + NT < mesh.n_tris) tv_next = __ldg(&mesh.tris[t + NT]);
         int area = 0;
         TriSetup o;
         // the sample box does not depend on the orientation: test it first, so
         // that the many triangles covering no sample of the tile skip the rest
-        if (t < mesh.n_tris && load_tri<VC>(sc, mesh, P, vc, t, o)) {
+        if (t < mesh.n_tris && load_tri<VC>(sc, mesh, P, vc, tv, o)) {
             int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
             int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
             int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);

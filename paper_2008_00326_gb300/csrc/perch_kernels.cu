@@ -544,11 +544,11 @@ __device__ __forceinline__ bool sample_depth(int w0, int w1, int w2, const float
                           __fmul_rn(__int2float_rn(w2), iz[2]));
     float z = __fdiv_rn(__int2float_rn(A), num);
     float dz = __fmul_rn(z, 10000.0f);
+    // z >= 0 here (A > 0 and every 1/Z > 0), so dz in [0, 2^32) rounds to
+    // nearest in 32 bits (the largest binary32 below 2^32 is an integer)
     if (!(dz < 4294967296.0f)) return false;
-    long long dd = __float2ll_rn(dz);
-    if (dd < 1 || dd > 0xFFFFFFFFll) return false;
-    d = (unsigned)dd;
-    return true;
+    d = __float2uint_rn(dz);
+    return d >= 1u;
 }
 
 template <bool K32>
@@ -1060,7 +1060,11 @@ __device__ __forceinline__ uint32_t interp_colour(const DevMesh& m, const TriSet
     for (int ch = 0; ch < 3; ++ch) {
         const long long num = w0 * ((c0 >> (8 * ch)) & 255) + w1 * ((c1 >> (8 * ch)) & 255) +
                               w2 * ((c2 >> (8 * ch)) & 255) + half;
-        long long q = __float2ll_rz(__fmul_rn(__ll2float_rn(num), rA));
+        // num < 2^41: its binary32 value from two 32-bit halves (the
+        // estimate needs only relative accuracy, the correction makes it exact)
+        const float numf = __fadd_rn(__fmul_rn(__int2float_rn((int)(num >> 16)), 65536.0f),
+                                     __int2float_rn((int)(num & 0xFFFF)));
+        long long q = __float2int_rz(__fmul_rn(numf, rA));
         const long long r = num - q * o.A;
         q += (r >= o.A) - (r < 0);
         crgb |= (uint32_t)q << (8 * ch);

@@ -492,7 +492,7 @@ def tree_leg(P, torch, dev, beam=4):
     return out
 
 
-def served_leg(P, dev, seed=9):
+def served_leg(P, dev, seed=9, slots=2, max_batch=1 << 15):
     """Poisson request traces; serial plain path vs the continuous-batching
     server.  Latency = submission (arrival) to results.  Two mixes: all three
     workloads (large searches), and the two small ones only."""
@@ -505,11 +505,13 @@ def served_leg(P, dev, seed=9):
         mids = [ctx.load_mesh(m) for m in sc.meshes]
         kinds.append([(sid, mids[r.mesh_index], r.label, r.roi, r.poses) for r in sc.requests])
     # enough requests per rate that p99 is not just the slowest one or two
-    mixed = _served_rates(P, ctx, kinds, (5, 20, 50, 100, 200), 300, seed, window_s=3.0)
-    small = _served_rates(P, ctx, [kinds[0], kinds[2]], (50, 200, 500, 1000), 600, seed + 1, window_s=3.0)
+    mixed = _served_rates(P, ctx, kinds, (5, 20, 50, 100, 200), 300, seed, window_s=3.0, slots=slots,
+                          max_batch=max_batch)
+    small = _served_rates(P, ctx, [kinds[0], kinds[2]], (50, 200, 500, 1000), 600, seed + 1, window_s=3.0,
+                          slots=slots, max_batch=max_batch)
     resident = ctx.hbm_used
     ctx.close()
-    return {"server": {"slots": 2, "max_batch_hypotheses": 1 << 16, "hbm_budget_bytes": budget,
+    return {"server": {"slots": slots, "max_batch_hypotheses": max_batch, "hbm_budget_bytes": budget,
                        "hbm_resident_bytes": resident},
             "mixed": {"mix": "uniform over tabletop_small (968 hyp), one tabletop_3obj object "
                              "(29,584 hyp), one sixdof_5obj object (4,096 hyp); scenes resident",
@@ -518,7 +520,7 @@ def served_leg(P, dev, seed=9):
                              "(4,096 hyp); scenes resident", "rates": small}}
 
 
-def _served_rates(P, ctx, kinds, rates, max_requests, seed, window_s=2.0):
+def _served_rates(P, ctx, kinds, rates, max_requests, seed, window_s=2.0, slots=2, max_batch=1 << 15):
     rng = np.random.default_rng(seed)
     out = []
     for rate in rates:
@@ -540,7 +542,7 @@ def _served_rates(P, ctx, kinds, rates, max_requests, seed, window_s=2.0):
             lat.append(time.perf_counter() - t0 - at)
         span_plain = time.perf_counter() - t0
         # served: submitted at arrival, continuous batching
-        srv = P.Server(ctx, slots=2, max_batch_hypotheses=1 << 16, max_wait_us=0)
+        srv = P.Server(ctx, slots=slots, max_batch_hypotheses=max_batch, max_wait_us=0)
         tickets = []
         t0 = time.perf_counter()
         for at, req in zip(arrivals, trace):

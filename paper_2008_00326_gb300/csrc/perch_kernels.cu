@@ -935,6 +935,16 @@ __device__ __forceinline__ bool get_triangle(const DevScene& sc, const DevMesh& 
     return load_tri<VC>(sc, m, P, vc, __ldg(&m.tris[t]), o) && orient_triangle(o);
 }
 
+// n / d for 0 <= n < 2^24 and 1 <= d < 2^24 without an integer division: a
+// binary32 estimate (both operands exact, error below one) corrected once.
+__device__ __forceinline__ int div_small(int n, int d)
+{
+    int q = __float2int_rz(__fmul_rn(__int2float_rn(n), __frcp_rn(__int2float_rn(d))));
+    const int r = n - q * d;
+    q += (r >= d) - (r < 0);
+    return q;
+}
+
 // Coverage (edge functions and the ownership rule), depth and the z-buffer
 // update of sample (u, v) of a set-up triangle (vertices in 1/16 px, 1/Z,
 // doubled area A > 0, owns bits per edge), in the tile at (tu0, tv0).
@@ -1028,7 +1038,7 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
             if (f >= total) continue;
             const TriStage& e = TS[j];
             const int local = f - (j > 0 ? excl : 0);
-            const int dv = local / e.bw;
+            const int dv = div_small(local, e.bw);
             raster_sample<K32>(e.x, e.y, e.iz, e.A, e.owns, e.tri, e.u0 + (local - dv * e.bw), e.v0 + dv, zbuf,
                                tu0, tv0, tw, tcap, err);
         }
@@ -1385,8 +1395,15 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         const int us0 = ((s_vbox[0] + s - 1) / s) * s, vs0 = ((mv0 + s - 1) / s) * s;
         const int nu = us0 < s_vbox[2] ? (s_vbox[2] - 1 - us0) / s + 1 : 0;
         const int nv = vs0 < mv1 ? (mv1 - 1 - vs0) / s + 1 : 0;
+        // pixel k = (row k / nu, column k % nu), the row and column carried
+        // from one k to the next (k advances by NT) instead of divided out
+        int kr = nu > 0 ? div_small(threadIdx.x, nu) : 0, kc = threadIdx.x - kr * nu;
+        const int rstep = nu > 0 ? div_small(NT, nu) : 0, cstep = NT - rstep * nu;
         for (int k = threadIdx.x; k < nu * nv; k += NT) {
-            int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
+            const int u = us0 + kc * s, v = vs0 + kr * s;
+            kc += cstep;
+            kr += rstep;
+            if (kc >= nu) { kc -= nu; ++kr; }
             int pix = v * sc.W + u;
             // the observed point of the pixel, back-projected once per scene
             const float4 p = __ldg(&sc.pxyz[pix]);
@@ -1801,6 +1818,19 @@ __device__ __forceinline__ bool gicp_terms(const float* Rf, float3 p, float4 na,
     return ok;
 }
 
+// rint(v) as a 64-bit integer for |v| < 2^46 without a 64-bit conversion:
+// below 2^31 a 32-bit round to nearest even; above, v is already an integer
+// (its ulp is at least 2^8) and splits exactly as 2^16 h + l, h = trunc(v /
+// 2^16) (the scaling is exact) and l = v - 2^16 h (exact: a multiple of 2^8
+// below 2^16 in magnitude).
+__device__ __forceinline__ long long rint_to_ll(float v)
+{
+    if (fabsf(v) < 2147483648.0f) return (long long)__float2int_rn(v);
+    const float h = truncf(__fmul_rn(v, 1.0f / 65536.0f));
+    const float l = __fsub_rn(v, __fmul_rn(h, 65536.0f));
+    return (long long)__float2int_rz(h) * 65536ll + (long long)__float2int_rz(l);
+}
+
 // H xi = -g from the fixed-point sums, by Cholesky in binary64 (one thread).
 __device__ bool gicp_solve(const unsigned long long* S, double* xi)
 {
@@ -2032,7 +2062,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_gicp(GicpArgs a)
                 if (bal) {
 #pragma unroll
                     for (int j = 0; j < kGicpTerms; ++j) {
-                        long long q = ok ? __float2ll_rn(__fmul_rn(terms[j], kGicpScale)) : 0ll;
+                        long long q = ok ? rint_to_ll(__fmul_rn(terms[j], kGicpScale)) : 0ll;
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
                         if (lane == j) acc += q;

@@ -470,7 +470,7 @@ struct TriStage {                 // a set-up triangle staged for its warp (64 b
     int A, tri;                   // doubled area, triangle id
     int u0, v0, bw;               // pixel box origin and width (in the tile)
     int owns;                     // bit i: edge i owns samples lying on it
-    int pad;
+    float izmax;                  // largest 1/Z of the three vertices
 };
 
 __device__ __forceinline__ int edge_fn(int ax, int ay, int bx, int by, int px, int py)
@@ -951,8 +951,26 @@ __device__ __forceinline__ int div_small(int n, int d)
 template <bool K32>
 __device__ __forceinline__ void raster_sample(const int* x, const int* y, const float* iz, int A, int owns_bits,
                                               int tri, int u, int v, uint32_t* zbuf, int tu0, int tv0, int tw,
-                                              int tcap, int* err)
+                                              int tcap, float izmax, int* err)
 {
+    const int idx = (v - tv0) * tw + (u - tu0);
+    if (!PERCH_CHECKED((unsigned)idx < (unsigned)tcap, err)) return;
+    // Early out for a sample that cannot beat the depth already stored here:
+    // its depth is at least 1e4 / max(1/Z) less a few 2^-24 relative, so if
+    // max(1/Z) (d_here + 2) < 9999 its depth is at least d_here + 2 and its
+    // key is larger.  The stored key only decreases, so reading it while other
+    // samples update it can only make this test skip less.
+    {
+        unsigned dh;
+        if (K32) {
+            const uint32_t w = zbuf[idx];
+            dh = w == 0xFFFFFFFFu ? 0xFFFFFFFFu : (w >> 16);
+        } else {
+            const unsigned long long w = reinterpret_cast<const unsigned long long*>(zbuf)[idx];
+            dh = w == kEmptyKey ? 0xFFFFFFFFu : (unsigned)(w >> 32);
+        }
+        if (dh < 0xFFFFFFF0u && __fmul_rn(izmax, __uint2float_rn(dh + 2u)) < 9999.0f) return;
+    }
     const int sx = 16 * u, sy = 16 * v;
     const int w0 = edge_fn(x[1], y[1], x[2], y[2], sx, sy);
     const int w1 = edge_fn(x[2], y[2], x[0], y[0], sx, sy);
@@ -961,9 +979,7 @@ __device__ __forceinline__ void raster_sample(const int* x, const int* y, const 
                      (w1 > 0 || (w1 == 0 && (owns_bits & 2))) &&
                      (w2 > 0 || (w2 == 0 && (owns_bits & 4)));
     unsigned d;
-    const int idx = (v - tv0) * tw + (u - tu0);
-    if (cov && sample_depth(w0, w1, w2, iz, A, d) && PERCH_CHECKED((unsigned)idx < (unsigned)tcap, err))
-        zmin<K32>(zbuf, idx, d, tri, err);
+    if (cov && sample_depth(w0, w1, w2, iz, A, d)) zmin<K32>(zbuf, idx, d, tri, err);
 }
 
 // Rasterise every triangle of mesh m at pose P into the z-buffer tile
@@ -998,10 +1014,12 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
                 const int owns_bits = (owns(o.x[2] - o.x[1], o.y[2] - o.y[1]) ? 1 : 0) |
                                       (owns(o.x[0] - o.x[2], o.y[0] - o.y[2]) ? 2 : 0) |
                                       (owns(o.x[1] - o.x[0], o.y[1] - o.y[0]) ? 4 : 0);
+                const float izmax = fmaxf(o.iz[0], fmaxf(o.iz[1], o.iz[2]));
                 if (u0 == u1 && v0 == v1) {
                     // one sample in the box (most triangles of a fine mesh):
                     // test it in this lane, no staging
-                    raster_sample<K32>(o.x, o.y, o.iz, o.A, owns_bits, t, u0, v0, zbuf, tu0, tv0, tw, tcap, err);
+                    raster_sample<K32>(o.x, o.y, o.iz, o.A, owns_bits, t, u0, v0, zbuf, tu0, tv0, tw, tcap, izmax,
+                                       err);
                 } else {
                     area = (u1 - u0 + 1) * (v1 - v0 + 1);
                     TriStage& e = TS[lane];
@@ -1012,6 +1030,7 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
                     e.v0 = v0;
                     e.bw = u1 - u0 + 1;
                     e.owns = owns_bits;
+                    e.izmax = izmax;
                 }
             }
         }
@@ -1040,7 +1059,7 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
             const int local = f - (j > 0 ? excl : 0);
             const int dv = div_small(local, e.bw);
             raster_sample<K32>(e.x, e.y, e.iz, e.A, e.owns, e.tri, e.u0 + (local - dv * e.bw), e.v0 + dv, zbuf,
-                               tu0, tv0, tw, tcap, err);
+                               tu0, tv0, tw, tcap, e.izmax, err);
         }
         __syncwarp();
     }

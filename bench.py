@@ -16,8 +16,9 @@ roofline : the scoring kernel against the 32-bit ALU issue peak; algorithmic
         the operations each takes (OPS); DRAM traffic from the committed ncu
         capture while the kernel source matches it; the rasteriser's shared-
         memory atomics against their measured rate.
-cpu_baseline : the plain C oracle on a bounded sample of the same workload
-        (all host threads and one), and of the other configurations.
+cpu_baseline : the plain C oracle (grid nearest-neighbour mode) on a bounded
+        sample of the same workload (all host threads and one), and of the
+        other configurations.
 batched / served / refine / tree / other_configs : the batched form (64
         uneven scenes, autotuned), the served form (Poisson traces, serial
         path vs server), GICP refinement then scoring (6-DoF), the tree search
@@ -178,43 +179,52 @@ class ClockSampler:
 
 
 def cpu_baseline(sc, seconds, rng_seed=0):
-    """The oracle, as it stands, on a bounded random sample of the workload."""
+    """The oracle, as it stands, on a bounded random sample of the workload:
+    timed with its grid nearest-neighbour mode (the faster of its two, equal
+    to the brute force by test) on all host threads and on one; the algorithmic
+    work counts of the roofline from a small brute-force sample (the mode that
+    counts the delta-cell candidates)."""
     from oracle import oracle as O
     threads = O.num_threads()
     rng = np.random.default_rng(rng_seed)
-    per = max(1, threads)
-    total_h, total_t, work = 0, 0.0, []
+    per = max(1, 8 * threads)
+    osc = O.OracleScene.from_scene(sc)
+    oms = {r.mesh_index: O.OracleMesh.from_mesh(sc.meshes[r.mesh_index]) for r in sc.requests}
+    total_h, total_t = 0, 0.0
     deadline = time.perf_counter() + seconds
     rounds = 0
     while True:
         for req in sc.requests:
             pick = rng.choice(len(req.poses), per, replace=False)
-            osc = O.OracleScene.from_scene(sc)
-            om = O.OracleMesh.from_mesh(sc.meshes[req.mesh_index])
             t0 = time.perf_counter()
-            _, _, w = O.score(osc, om, req.poses[pick], label=req.label, roi=req.roi, with_work=True)
+            O.score(osc, oms[req.mesh_index], req.poses[pick], label=req.label, roi=req.roi, nn="grid")
             total_t += time.perf_counter() - t0
             total_h += len(pick)
-            work.append(np.concatenate([w, np.full((len(w), 1), req.mesh_index, np.int64)], axis=1))
         rounds += 1
         if time.perf_counter() >= deadline:
             break
-    work = np.concatenate(work)
-    # the same oracle on one core: at least 16 hypotheses in all
+    # the same on one core: at least 64 hypotheses in all
     t1, n1 = 0.0, 0
-    per1 = -(-16 // len(sc.requests))
+    per1 = -(-64 // len(sc.requests))
     for req in sc.requests:
         pick = rng.choice(len(req.poses), per1, replace=False)
-        osc = O.OracleScene.from_scene(sc)
-        om = O.OracleMesh.from_mesh(sc.meshes[req.mesh_index])
         t0 = time.perf_counter()
-        O.score(osc, om, req.poses[pick], label=req.label, roi=req.roi, threads=1)
+        O.score(osc, oms[req.mesh_index], req.poses[pick], label=req.label, roi=req.roi, threads=1, nn="grid")
         t1 += time.perf_counter() - t0
         n1 += len(pick)
+    # work counts: brute force on a few hypotheses per object
+    work = []
+    for req in sc.requests:
+        pick = rng.choice(len(req.poses), max(1, threads), replace=False)
+        _, _, w = O.score(osc, oms[req.mesh_index], req.poses[pick], label=req.label, roi=req.roi,
+                          with_work=True, nn="brute")
+        work.append(np.concatenate([w, np.full((len(w), 1), req.mesh_index, np.int64)], axis=1))
+    work = np.concatenate(work)
     return {"value": total_h / total_t, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{total_h} random hypotheses ({rounds} rounds x {per} per object) of the same "
-                      f"workload, brute-force nearest neighbours, {total_t:.1f} s",
-            "value_1core": n1 / t1, "sample_1core": f"{n1} hypotheses ({per1} per object), {t1:.1f} s"}, work
+                      f"workload, grid nearest neighbours, {total_t:.1f} s",
+            "value_1core": n1 / t1, "sample_1core": f"{n1} hypotheses ({per1} per object), {t1:.1f} s",
+            "work_sample": f"{len(work)} hypotheses, brute-force nearest neighbours (delta-cell candidate counts)"}, work
 
 
 def _other_config_scenes():
@@ -272,7 +282,7 @@ def cpu_baseline_other_configs(cores, seconds=4.0):
             pick = rng.choice(len(r.poses), min(per, len(r.poses)), replace=False)
             om = O.OracleMesh.from_mesh(sc.meshes[r.mesh_index])
             t0 = time.perf_counter()
-            O.score(osc, om, r.poses[pick], label=r.label, roi=r.roi, threads=per)
+            O.score(osc, om, r.poses[pick], label=r.label, roi=r.roi, threads=per, nn="grid")
             t_cpu += time.perf_counter() - t0
             n_cpu += len(pick)
         out[sc.name] = {"value": n_cpu / t_cpu, "unit": UNIT, "cores": per,
@@ -289,7 +299,7 @@ def reference_arm(a):
     sc, desc = _workload(a.grid_half)
     threads = O.num_threads()
     rng = np.random.default_rng(7)
-    per = max(1, threads)
+    per = max(1, 8 * threads)
     oscs = [O.OracleScene.from_scene(sc) for _ in sc.requests]
     oms = [O.OracleMesh.from_mesh(sc.meshes[r.mesh_index]) for r in sc.requests]
 
@@ -297,7 +307,7 @@ def reference_arm(a):
         n = 0
         for k, req in enumerate(sc.requests):
             pick = rng.choice(len(req.poses), per, replace=False)
-            O.score(oscs[k], oms[k], req.poses[pick], label=req.label, roi=req.roi)
+            O.score(oscs[k], oms[k], req.poses[pick], label=req.label, roi=req.roi, nn="grid")
             n += len(pick)
         return n
 
@@ -314,7 +324,7 @@ def reference_arm(a):
         "data": "synthetic",
         "config": {"workload": desc, "sample_per_step": f"{per} hypotheses per object"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{per} random hypotheses per object per step"},
+                         "sample": f"{per} random hypotheses per object per step, grid nearest neighbours"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 

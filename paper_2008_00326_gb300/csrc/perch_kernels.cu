@@ -464,7 +464,7 @@ struct TriSetup {
     int A;                        // doubled area > 0
 };
 
-struct TriStage {                 // a set-up triangle staged for its warp (64 bytes)
+struct __align__(16) TriStage {   // a set-up triangle staged for its warp (64 bytes, 4 x 16-byte moves)
     int x[3], y[3];               // snapped positions, 1/16 px
     float iz[3];                  // 1/Z
     int A, tri;                   // doubled area, triangle id
@@ -1022,7 +1022,7 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
                                        err);
                 } else {
                     area = (u1 - u0 + 1) * (v1 - v0 + 1);
-                    TriStage& e = TS[lane];
+                    TriStage e;
                     for (int k = 0; k < 3; ++k) { e.x[k] = o.x[k]; e.y[k] = o.y[k]; e.iz[k] = o.iz[k]; }
                     e.A = o.A;
                     e.tri = t;
@@ -1031,6 +1031,7 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
                     e.bw = u1 - u0 + 1;
                     e.owns = owns_bits;
                     e.izmax = izmax;
+                    TS[lane] = e;                  // whole-record store
                 }
             }
         }
@@ -1055,7 +1056,7 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
             }
             const int excl = __shfl_sync(0xffffffffu, incl, j > 0 ? j - 1 : 0);
             if (f >= total) continue;
-            const TriStage& e = TS[j];
+            const TriStage e = TS[j];              // whole-record load
             const int local = f - (j > 0 ? excl : 0);
             const int dv = div_small(local, e.bw);
             raster_sample<K32>(e.x, e.y, e.iz, e.A, e.owns, e.tri, e.u0 + (local - dv * e.bw), e.v0 + dv, zbuf,

@@ -570,7 +570,18 @@ __device__ __forceinline__ void zmin(uint32_t* zbuf, int idx, unsigned d, int tr
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
 constexpr int kGroups = 1;        // distinct query cells looked up together per warp
-constexpr int kCellCache = 64;    // per-warp cache of recent 27-cell lookups (direct mapped)
+constexpr int kCellCache = 32;    // per-warp cache of recent 27-cell lookups (hash index; direct mapped)
+
+// A group of G queries shares a 27-cell candidate list; k = floor(32 / G)
+// lanes test each query's candidates.  Lane l serves query floor(l / k),
+// taken as (l * ceil(1024 / k)) >> 10 (exact for l < 32 and k <= 32), so the
+// split needs no integer division.
+__constant__ unsigned char c_lanes_per_query[33] = {
+    32, 32, 16, 10, 8, 6, 5, 4, 4, 3, 3, 2, 2, 2, 2, 2, 2,
+    1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+__constant__ unsigned short c_lane_div[33] = {
+    1024, 1024, 512, 342, 256, 205, 171, 147, 128, 114, 103, 94, 86, 79, 74, 69, 64,
+    61, 57, 54, 52, 49, 47, 45, 43, 41, 40, 38, 37, 36, 35, 34, 32};
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
     float x, y, z;
@@ -728,6 +739,25 @@ __device__ __forceinline__ unsigned long long scan_staged(const DevScene& sc, co
     return local;
 }
 
+// Candidates c0 .. c0 + 63 of group g's runs staged in the warp's shared
+// memory (two coalesced loads per lane); r is the lane's run cursor, carried
+// from chunk to chunk.
+__device__ __forceinline__ void stage_chunk(const DevScene& sc, WarpProbe& W, int g, int c0, int T, int lane, int& r,
+                                            int* err)
+{
+    const int ci = c0 + lane, cj = ci + 32;
+    if (ci < T) {
+        while (W.runs[g][r].y <= ci) ++r;
+        if (PERCH_CHECKED((unsigned)(W.runs[g][r].x + ci) < (unsigned)sc.n_pts, err))
+            W.stage[lane] = __ldg(&sc.pts[W.runs[g][r].x + ci]);
+    }
+    if (cj < T) {
+        while (W.runs[g][r].y <= cj) ++r;
+        if (PERCH_CHECKED((unsigned)(W.runs[g][r].x + cj) < (unsigned)sc.n_pts, err))
+            W.stage[lane + 32] = __ldg(&sc.pts[W.runs[g][r].x + cj]);
+    }
+}
+
 template <bool MARK>
 __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float qx, float qy,
                                           float qz, uint32_t qpix, WarpProbe& W, int lane, const MarkBand& mb)
@@ -780,28 +810,19 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
             // candidates j, j + k, ... of each staged chunk and keeps its
             // minimum in a register
             const int G = __popc(W.mask[g]);
-            const int k = 32 / G;
+            const int k = c_lanes_per_query[G];
+            const int qj = (lane * (int)c_lane_div[k]) >> 10;
             const bool active = lane < G * k;
-            const int ql = active ? W.qlist[g][lane / k] : 0;
+            const int ql = active ? W.qlist[g][qj] : 0;
             const float4 q = W.q[ql];
             unsigned long long local = kEmptyKey;
             int r = 0;
             for (int c0 = 0; c0 < T; c0 += 64) {
-                const int ci = c0 + lane, cj = ci + 32;
-                if (ci < T) {
-                    while (W.runs[g][r].y <= ci) ++r;
-                    if (PERCH_CHECKED((unsigned)(W.runs[g][r].x + ci) < (unsigned)sc.n_pts, mb.err))
-                        W.stage[lane] = __ldg(&sc.pts[W.runs[g][r].x + ci]);
-                }
-                if (cj < T) {
-                    while (W.runs[g][r].y <= cj) ++r;
-                    if (PERCH_CHECKED((unsigned)(W.runs[g][r].x + cj) < (unsigned)sc.n_pts, mb.err))
-                        W.stage[lane + 32] = __ldg(&sc.pts[W.runs[g][r].x + cj]);
-                }
+                stage_chunk(sc, W, g, c0, T, lane, r, mb.err);
                 __syncwarp();
                 const int n = min(64, T - c0);
                 if (active)
-                    local = scan_staged<MARK>(sc, q, W.stage, n, lane % k, k, mb, local);
+                    local = scan_staged<MARK>(sc, q, W.stage, n, lane - qj * k, k, mb, local);
                 __syncwarp();
             }
             if (active && local != kEmptyKey) atomicMin(&W.best[ql], local);
@@ -1226,7 +1247,8 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                 if (more) {
                     bool kept = false;
                     KeptPoint kp;
-                    const int lu = (blk % nbx) * 8 + (lane & 7), lv = (blk / nbx) * 4 + (lane >> 3);
+                    const int by = div_small(blk, nbx);
+                    const int lu = (blk - by * nbx) * 8 + (lane & 7), lv = by * 4 + (lane >> 3);
                     if (lu < nu && lv < nv) {
                         int u = us0 + lu * s, v = vs0 + lv * s;
                         int zi = (v - tv0) * tw + (u - tu0);

@@ -244,7 +244,7 @@ PERCH_API perch_status perch_best_noalloc(const int32_t *costs, const uint64_t *
  * than 65536 triangles and the hypothesis lies within 6.5 m, else a 64-bit key
  * per pixel), and the capacity in bits of the bitset that marks nearest
  * neighbours inside the admissible box (1024 <= mark_bits <= 2^22, 0 = the
- * default 32768).  Pixel boxes larger than the z-buffer are processed in
+ * default 65536).  Pixel boxes larger than the z-buffer are processed in
  * tiles, admissible boxes larger than the bitset in row bands.  Results do not
  * depend on these choices; only speed and shared memory do.  The autotuner of
  * the batched form calls it.  PERCH_E_INVALID outside the ranges. */

@@ -103,10 +103,7 @@ private:
 // the admissible box.  Boxes larger than this are processed in row bands (each
 // band repeats the render and search), so the capacity only trades shared
 // memory against that rare repetition.  At least one image row always fits.
-// 32,768 bits keep the default block (256 threads, 8,192-word z-buffer) at
-// 64 KB, so three blocks fit a 196 KB shared-memory carve-out and leave 60 KB
-// of L1 per SM (28 KB at 65,536 bits): 2 % faster on the bench workload.
-constexpr int kMarkBitsDefault = 1 << 15;
+constexpr int kMarkBitsDefault = 1 << 16;
 
 }  // namespace perch_host
 

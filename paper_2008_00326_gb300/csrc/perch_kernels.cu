@@ -40,10 +40,16 @@ cudaError_t init_device_tables(cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The colour test only decides whether a difference exceeds tau_c, and the
+// parity contract leaves the decisions within 1e-3 of tau_c to rounding (the
+// band): the constants' divisions are multiplications by reciprocals, the
+// other divisions approximate (__fdividef), the angles in half-turns
+// (sinpif / cospif reduce their argument exactly) -- a few 1e-6 relative at
+// most, far inside the band.
 __device__ __forceinline__ float cie_f(float t)
 {
     // cube root above (6/29)^3, the linear toe below it
-    return (t > 0.0088564517f) ? cbrtf(t) : (t * 903.29630f + 16.0f) / 116.0f;
+    return (t > 0.0088564517f) ? cbrtf(t) : (t * 903.29630f + 16.0f) * (1.0f / 116.0f);
 }
 
 __device__ __forceinline__ float3 srgb8_to_lab(uint32_t r8, uint32_t g8, uint32_t b8)
@@ -52,24 +58,24 @@ __device__ __forceinline__ float3 srgb8_to_lab(uint32_t r8, uint32_t g8, uint32_
     float x = 0.4124564f * r + 0.3575761f * g + 0.1804375f * b;
     float y = 0.2126729f * r + 0.7151522f * g + 0.0721750f * b;
     float z = 0.0193339f * r + 0.1191920f * g + 0.9503041f * b;
-    float fx = cie_f(x / 0.95047f), fy = cie_f(y), fz = cie_f(z / 1.08883f);
+    float fx = cie_f(x * (1.0f / 0.95047f)), fy = cie_f(y), fz = cie_f(z * (1.0f / 1.08883f));
     return make_float3(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz));
 }
 
 // CIEDE2000 with kL = kC = kH = 1, angles in degrees.
 __device__ __forceinline__ float ciede2000(float3 p, float3 q)
 {
-    const float kRad = 0.017453292519943295f;
+    const float kDeg = 57.295779513082321f;      // degrees per radian
     const float k25p7 = 6103515625.0f;
     float c1 = sqrtf(p.y * p.y + p.z * p.z);
     float c2 = sqrtf(q.y * q.y + q.z * q.z);
     float cm = 0.5f * (c1 + c2);
     float cm2 = cm * cm, cm7 = cm2 * cm2 * cm2 * cm;
-    float g = 0.5f * (1.0f - sqrtf(cm7 / (cm7 + k25p7)));
+    float g = 0.5f * (1.0f - sqrtf(__fdividef(cm7, cm7 + k25p7)));
     float ap1 = p.y * (1.0f + g), ap2 = q.y * (1.0f + g);
     float cp1 = sqrtf(ap1 * ap1 + p.z * p.z), cp2 = sqrtf(ap2 * ap2 + q.z * q.z);
-    float hp1 = (ap1 == 0.0f && p.z == 0.0f) ? 0.0f : atan2f(p.z, ap1) / kRad;
-    float hp2 = (ap2 == 0.0f && q.z == 0.0f) ? 0.0f : atan2f(q.z, ap2) / kRad;
+    float hp1 = (ap1 == 0.0f && p.z == 0.0f) ? 0.0f : atan2f(p.z, ap1) * kDeg;
+    float hp2 = (ap2 == 0.0f && q.z == 0.0f) ? 0.0f : atan2f(q.z, ap2) * kDeg;
     if (hp1 < 0.0f) hp1 += 360.0f;
     if (hp2 < 0.0f) hp2 += 360.0f;
     float prod = cp1 * cp2;
@@ -86,21 +92,22 @@ __device__ __forceinline__ float ciede2000(float3 p, float3 q)
     }
     float dL = q.x - p.x;
     float dC = cp2 - cp1;
-    float dH = 2.0f * sqrtf(prod) * sinf(0.5f * dh * kRad);
+    float dH = 2.0f * sqrtf(prod) * sinpif(dh * (1.0f / 360.0f));     // sin(dh / 2 degrees)
     float lm = 0.5f * (p.x + q.x) - 50.0f;
     float lm2 = lm * lm;
     float cpm = 0.5f * (cp1 + cp2);
-    float t = 1.0f - 0.17f * cosf((hm - 30.0f) * kRad) + 0.24f * cosf(2.0f * hm * kRad)
-              + 0.32f * cosf((3.0f * hm + 6.0f) * kRad) - 0.20f * cosf((4.0f * hm - 63.0f) * kRad);
-    float e = (hm - 275.0f) / 25.0f;
-    float dtheta = 30.0f * expf(-e * e);
+    float t = 1.0f - 0.17f * cospif((hm - 30.0f) * (1.0f / 180.0f)) + 0.24f * cospif(hm * (1.0f / 90.0f))
+              + 0.32f * cospif((3.0f * hm + 6.0f) * (1.0f / 180.0f))
+              - 0.20f * cospif((4.0f * hm - 63.0f) * (1.0f / 180.0f));
+    float e = (hm - 275.0f) * (1.0f / 25.0f);
+    float dtheta = 30.0f * __expf(-e * e);
     float cpm2 = cpm * cpm, cpm7 = cpm2 * cpm2 * cpm2 * cpm;
-    float rc = 2.0f * sqrtf(cpm7 / (cpm7 + k25p7));
-    float sl = 1.0f + 0.015f * lm2 / sqrtf(20.0f + lm2);
+    float rc = 2.0f * sqrtf(__fdividef(cpm7, cpm7 + k25p7));
+    float sl = 1.0f + __fdividef(0.015f * lm2, sqrtf(20.0f + lm2));
     float sc = 1.0f + 0.045f * cpm;
     float sh = 1.0f + 0.015f * cpm * t;
-    float rt = -sinf(2.0f * dtheta * kRad) * rc;
-    float a = dL / sl, b = dC / sc, c = dH / sh;
+    float rt = -sinpif(dtheta * (1.0f / 90.0f)) * rc;                  // sin(2 dtheta degrees)
+    float a = __fdividef(dL, sl), b = __fdividef(dC, sc), c = __fdividef(dH, sh);
     return sqrtf(a * a + b * b + c * c + rt * b * c);
 }
 
@@ -585,7 +592,7 @@ __constant__ unsigned short c_lane_div[33] = {
 
 struct __align__(16) KeptPoint {  // a rendered point of R \ C waiting for its radius search
     float x, y, z;
-    uint32_t rgb;                 // interpolated colour, r | g << 8 | b << 16
+    uint32_t pix;                 // its pixel u | v << 16 (the colour is interpolated only if needed)
 };
 
 // Per-warp scratch of the radius search (shared memory).
@@ -1123,18 +1130,6 @@ __device__ __forceinline__ uint32_t interp_colour(const DevMesh& m, const TriSet
     return crgb;
 }
 
-// The pixel (v << 16 | u) of a rendered point recovered from its
-// back-projection x = ((u - cx) z) / fx, y = ((v - cy) z) / fy: x fx / z + cx
-// equals u up to a relative error of a few 2^-24 on |u - cx| plus the rounding
-// of the sum, together below 0.2 pixel for any image of at most 466033 pixels
-// a side, so rounding to the nearest integer gives u exactly (and v alike).
-__device__ __forceinline__ uint32_t recover_pixel(const DevScene& sc, float x, float y, float z)
-{
-    const int u = __float2int_rn(__fadd_rn(__fdiv_rn(__fmul_rn(x, sc.fx), z), sc.cx));
-    const int v = __float2int_rn(__fadd_rn(__fdiv_rn(__fmul_rn(y, sc.fy), z), sc.cy));
-    return ((uint32_t)v << 16) | (uint32_t)u;
-}
-
 // jo_mode 1 with the colour check (Eq. 3 with Eq. 4 applied from the observed
 // side): every observed point p of rows [mv0, mv1) of the admissible box
 // holds the key of its nearest rendered point q; p stays an inlier iff the
@@ -1279,10 +1274,8 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                                             (unsigned long long)dobs + (unsigned)sc.occ_margin < d &&
                                             (J.label < 0 || __ldg(&sc.labels[pix]) != J.label);
                             if (!occluded) {
-                                TriSetup o;
-                                get_triangle<VC>(sc, J.m, P, vc, tri, o);
                                 float3 q = back_project(sc, u, v, d);
-                                kp.x = q.x; kp.y = q.y; kp.z = q.z; kp.rgb = interp_colour(J.m, o, u, v);
+                                kp.x = q.x; kp.y = q.y; kp.z = q.z; kp.pix = (uint32_t)u | ((uint32_t)v << 16);
                                 kept = true;
                             }
                         }
@@ -1300,15 +1293,23 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                     if (valid) kq = wq[(wq_head + lane) % kWarpQueue];
                     wq_head = (wq_head + nb) % kWarpQueue;
                     wq_count -= nb;
-                    const uint32_t qpix = (EQ3 && valid) ? recover_pixel(sc, kq.x, kq.y, kq.z) : 0u;
+                    const uint32_t qpix = (EQ3 && valid) ? kq.pix : 0u;
                     const unsigned long long nn = probe_batch<EQ3>(sc, valid, kq.x, kq.y, kq.z, qpix, WP, lane, mband);
                     if (valid) {
                         bool explained = nn != kEmptyKey;
                         const int pnn = (int)(uint32_t)nn;
                         const int pu = pnn & 0xFFFF, pv = pnn >> 16;
                         if (explained && sc.color_check) {
+                            // the rendered colour of q, from the triangle its z-buffer word holds
+                            const int qu = (int)(kq.pix & 0xFFFFu), qv = (int)(kq.pix >> 16);
+                            const int qi = (qv - tv0) * tw + (qu - tu0);
+                            const int qtri = K32 ? (int)(zbuf[qi] & 0xFFFFu)
+                                                 : (int)(uint32_t)reinterpret_cast<const unsigned long long*>(zbuf)[qi];
+                            TriSetup o;
+                            get_triangle<VC>(sc, J.m, P, vc, qtri, o);
+                            const uint32_t rgb = interp_colour(J.m, o, qu, qv);
                             float4 lp = __ldg(&sc.lab[pv * sc.W + pu]);
-                            float3 lq = srgb8_to_lab(kq.rgb & 255, (kq.rgb >> 8) & 255, (kq.rgb >> 16) & 255);
+                            float3 lq = srgb8_to_lab(rgb & 255, (rgb >> 8) & 255, (rgb >> 16) & 255);
                             if (ciede2000(lq, make_float3(lp.x, lp.y, lp.z)) > sc.tau_c) explained = false;
                         }
                         if (TREE && explained && J.tree.out_mark) {

@@ -472,12 +472,14 @@ struct TriSetup {
 };
 
 struct __align__(16) TriStage {   // a set-up triangle staged for its warp (64 bytes, 4 x 16-byte moves)
-    int x[3], y[3];               // snapped positions, 1/16 px
+    // edge i at the sample of pixel (u, v): a[i] u + b[i] v + c[i] + bias_i
+    // (two's-complement arithmetic, exact), bias_i = 1 unless edge i owns
+    // the samples lying on it; covered iff every a[i] u + b[i] v + c[i] >= 0
+    int a[3], b[3], c[3];
     float iz[3];                  // 1/Z
     int A, tri;                   // doubled area, triangle id
-    int u0, v0, bw;               // pixel box origin and width (in the tile)
-    int owns;                     // bit i: edge i owns samples lying on it
-    float izmax;                  // largest 1/Z of the three vertices
+    int uv0;                      // pixel box origin u0 | v0 << 16
+    int bw_bias;                  // box width | bias bits << 16
 };
 
 __device__ __forceinline__ int edge_fn(int ax, int ay, int bx, int by, int px, int py)
@@ -492,6 +494,14 @@ __device__ __forceinline__ bool owns(int dx, int dy)
 
 __device__ __forceinline__ int floor16(int x) { return x >> 4; }         // arithmetic shift
 __device__ __forceinline__ int ceil16(int x) { return -((-x) >> 4); }
+
+// Bit i set iff edge i of the oriented triangle (edge 0: vertex 1 -> 2, edge
+// 1: 2 -> 0, edge 2: 0 -> 1) owns the samples lying on it.
+__device__ __forceinline__ int owns_of(const TriSetup& o)
+{
+    return (owns(o.x[2] - o.x[1], o.y[2] - o.y[1]) ? 1 : 0) | (owns(o.x[0] - o.x[2], o.y[0] - o.y[2]) ? 2 : 0) |
+           (owns(o.x[1] - o.x[0], o.y[1] - o.y[0]) ? 4 : 0);
+}
 
 // Doubled area and orientation of a loaded triangle: a negative area swaps
 // vertices 1 and 2 (two-sided rendering).  False if degenerate (A == 0).
@@ -1010,6 +1020,38 @@ __device__ __forceinline__ void raster_sample(const int* x, const int* y, const 
     if (cov && sample_depth(w0, w1, w2, iz, A, d)) zmin<K32>(zbuf, idx, d, tri, err);
 }
 
+// Coverage, depth and the z-buffer update of sample (u, v) of a staged
+// triangle: the same tests as raster_sample from the edge coefficients (no
+// vertex differences per sample), coverage first so that an uncovered sample
+// reads no z-buffer word.
+template <bool K32>
+__device__ __forceinline__ void raster_staged(const TriStage& e, int u, int v, uint32_t* zbuf, int tu0, int tv0,
+                                              int tw, int tcap, int* err)
+{
+    const int t0 = (int)((unsigned)e.a[0] * (unsigned)u + (unsigned)e.b[0] * (unsigned)v + (unsigned)e.c[0]);
+    const int t1 = (int)((unsigned)e.a[1] * (unsigned)u + (unsigned)e.b[1] * (unsigned)v + (unsigned)e.c[1]);
+    const int t2 = (int)((unsigned)e.a[2] * (unsigned)u + (unsigned)e.b[2] * (unsigned)v + (unsigned)e.c[2]);
+    if ((t0 | t1 | t2) < 0) return;
+    const int idx = (v - tv0) * tw + (u - tu0);
+    if (!PERCH_CHECKED((unsigned)idx < (unsigned)tcap, err)) return;
+    {   // the early out of raster_sample
+        const float izmax = fmaxf(e.iz[0], fmaxf(e.iz[1], e.iz[2]));
+        unsigned dh;
+        if (K32) {
+            const uint32_t w = zbuf[idx];
+            dh = w == 0xFFFFFFFFu ? 0xFFFFFFFFu : (w >> 16);
+        } else {
+            const unsigned long long w = reinterpret_cast<const unsigned long long*>(zbuf)[idx];
+            dh = w == kEmptyKey ? 0xFFFFFFFFu : (unsigned)(w >> 32);
+        }
+        if (dh < 0xFFFFFFF0u && __fmul_rn(izmax, __uint2float_rn(dh + 2u)) < 9999.0f) return;
+    }
+    const int bias = e.bw_bias >> 16;
+    unsigned d;
+    if (sample_depth(t0 + (bias & 1), t1 + ((bias >> 1) & 1), t2 + (bias >> 2), e.iz, e.A, d))
+        zmin<K32>(zbuf, idx, d, e.tri, err);
+}
+
 // Rasterise every triangle of mesh m at pose P into the z-buffer tile
 // [tu0,tu1) x [tv0,tv1) (row pitch tw).  A warp sets up 32 triangles (one per
 // lane); a triangle with one sample in its box is tested in its own lane, the
@@ -1050,15 +1092,23 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
                                        err);
                 } else {
                     area = (u1 - u0 + 1) * (v1 - v0 + 1);
+                    // edge i from vertex p to vertex q at the sample (16 u, 16 v):
+                    // (xq - xp)(16 v - yp) - (yq - yp)(16 u - xp), less its tie bias
                     TriStage e;
-                    for (int k = 0; k < 3; ++k) { e.x[k] = o.x[k]; e.y[k] = o.y[k]; e.iz[k] = o.iz[k]; }
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const int p = (i + 1) % 3, q = (i + 2) % 3;
+                        const unsigned dx = (unsigned)o.x[q] - (unsigned)o.x[p];
+                        const unsigned dy = (unsigned)o.y[q] - (unsigned)o.y[p];
+                        e.a[i] = (int)(0u - 16u * dy);
+                        e.b[i] = (int)(16u * dx);
+                        e.c[i] = (int)(dy * (unsigned)o.x[p] - dx * (unsigned)o.y[p] - (unsigned)(((owns_bits >> i) & 1) ^ 1));
+                        e.iz[i] = o.iz[i];
+                    }
                     e.A = o.A;
                     e.tri = t;
-                    e.u0 = u0;
-                    e.v0 = v0;
-                    e.bw = u1 - u0 + 1;
-                    e.owns = owns_bits;
-                    e.izmax = izmax;
+                    e.uv0 = u0 | (v0 << 16);
+                    e.bw_bias = (u1 - u0 + 1) | ((~owns_bits & 7) << 16);
                     TS[lane] = e;                  // whole-record store
                 }
             }
@@ -1086,9 +1136,10 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
             if (f >= total) continue;
             const TriStage e = TS[j];              // whole-record load
             const int local = f - (j > 0 ? excl : 0);
-            const int dv = div_small(local, e.bw);
-            raster_sample<K32>(e.x, e.y, e.iz, e.A, e.owns, e.tri, e.u0 + (local - dv * e.bw), e.v0 + dv, zbuf,
-                               tu0, tv0, tw, tcap, e.izmax, err);
+            const int bw = e.bw_bias & 0xFFFF;
+            const int dv = div_small(local, bw);
+            raster_staged<K32>(e, (e.uv0 & 0xFFFF) + (local - dv * bw), (e.uv0 >> 16) + dv, zbuf, tu0, tv0, tw, tcap,
+                               err);
         }
         __syncwarp();
     }

@@ -350,7 +350,7 @@ def batched_leg(P, torch, dev, n_scenes=64):
     dp = torch.from_numpy(np.concatenate(poses)).to(dev)
     dc = torch.zeros((n, 2), dtype=torch.int32, device=dev)
     s = torch.cuda.Stream(dev)
-    threads, zbuf = P.perch_autotune(ctx.ctx, items, dp, dc)
+    threads, zbuf, bins = P.perch_autotune(ctx.ctx, items, dp, dc)
 
     def timed(fn, reps=3):
         best = float("inf")
@@ -382,7 +382,7 @@ def batched_leg(P, torch, dev, n_scenes=64):
     ctx.close()
     return {"workload": f"{n_scenes} scenes 320x240, 1-6 objects from a 500-30k triangle mesh pool, "
                         f"ROI 64x64..320x240, 500-40k hypotheses per scene, colour on",
-            "items": len(specs), "hypotheses": n, "autotuned": {"threads": threads, "zbuf_words": zbuf},
+            "items": len(specs), "hypotheses": n, "autotuned": {"threads": threads, "zbuf_words": zbuf, "tile_bin_capacity": bins},
             "per_scene_launches": {"ms": t_plain, "hyp_s": n / t_plain * 1e3, "launches": len(specs)},
             "batched_launch": {"ms": t_batch, "hyp_s": n / t_batch * 1e3},
             "graph_replay": {"ms": t_graph, "hyp_s": n / t_graph * 1e3},

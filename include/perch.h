@@ -251,6 +251,19 @@ PERCH_API perch_status perch_best_noalloc(const int32_t *costs, const uint64_t *
 PERCH_API perch_status perch_set_launch_config(perch_ctx *ctx, int32_t threads, int32_t zbuf_words,
                                                int32_t mark_bits);
 
+/* Tile bins of the rasteriser (Sec. IV-A "Parallel Rendering" renders every
+ * triangle of a pose into its image; a pixel box larger than the shared-memory
+ * z-buffer is rendered tile by tile).  bin_cap > 0: when a hypothesis's pixel
+ * box needs 2 to 32 tiles, one pass first lists in each tile's bin the
+ * triangles whose sample boxes meet it (at most bin_cap per tile), and each
+ * tile is then rasterised from its bin alone instead of from the whole mesh;
+ * a tile whose bin overflowed is rasterised from the whole mesh.  Plain
+ * scoring (jo_mode 0) only.  The bins live in the vertex-cache slots (32 x
+ * bin_cap x 4 bytes per resident block, charged to the budget).  Results do
+ * not depend on it.  0 (the default) = no bins; otherwise 64 <= bin_cap <=
+ * 65536, else PERCH_E_INVALID.  The autotuner sets it. */
+PERCH_API perch_status perch_set_raster_bins(perch_ctx *ctx, int32_t bin_cap);
+
 /* ---- batched form ----------------------------------------------------------
  * Hypotheses of many (scene, mesh) searches scored by ONE call: each item gets
  * a persistent launch of the whole resident grid with its scene and mesh in
@@ -294,16 +307,18 @@ PERCH_API perch_status perch_batch_graph_launch(perch_batch_graph *g, void *cuda
 PERCH_API perch_status perch_batch_graph_destroy(perch_batch_graph *g);
 
 /* Autotuner: time the candidate launch shapes (threads per block x z-buffer
- * words) on a sample of this batch -- every 8th item in order of size,
- * whole; batches of fewer than 16 items whole (DEVICE poses/costs; the
- * sampled items' costs are overwritten) --, keep the
- * fastest as the context's launch configuration and remember it for batches
- * of the same class (largest ROI area and triangle count, each rounded to a
- * power of two); a later call for a known class returns the remembered shape
- * without timing.  *threads and *zbuf_words receive the choice. */
+ * words x tile-bin capacity, the bins tried with the 2048- and 4096-word
+ * z-buffers only) on a sample of this batch -- every 8th item in order of
+ * size, whole; batches of fewer than 16 items whole (DEVICE poses/costs; the
+ * sampled items' costs are overwritten) --, keep the fastest as the
+ * context's launch configuration and remember it for batches of the same
+ * class (largest ROI area and triangle count, each rounded to a power of
+ * two); a later call for a known class returns the remembered shape without
+ * timing.  *threads, *zbuf_words and *bin_cap (may be NULL) receive the
+ * choice. */
 PERCH_API perch_status perch_autotune(perch_ctx *ctx, const perch_work_item *items, int32_t n_items,
                                       const float *poses, int32_t *costs, int32_t *threads,
-                                      int32_t *zbuf_words);
+                                      int32_t *zbuf_words, int32_t *bin_cap);
 
 /* ---- served form -----------------------------------------------------------
  * A continuous-batching server on a context: requests (one search each: a

@@ -304,10 +304,10 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
         return fail(c, PERCH_E_CUDA, "scoring kernel does not fit on the device");
     }
     // vertex caches: a pool of one slot per resident block, used when snapped
-    // coordinates fit in int16
-    long long vstride = 0;
+    // coordinates fit in int16; with tile bins each slot also holds the bins
+    long long vstride = 0, bin_off = 0;
     if (small_images) {
-        vstride = ((long long)max_verts + 31) / 32 * 32;
+        vstride = perch::vcache_slot_words(max_verts, cfg.bin_cap, &bin_off);
         size_t need = (size_t)grid * vstride * sizeof(unsigned long long);
         if (need > X.vcache_bytes) {
             cudaEventSynchronize(X.last);
@@ -340,6 +340,8 @@ perch_status run_jobs(perch_ctx* c, ScoreScratch& X, const std::vector<perch::Jo
     a.vstride = vstride;
     a.vmask = X.next + nj;
     a.vslots = grid;
+    a.bin_cap = vstride ? cfg.bin_cap : 0;
+    a.bin_off = bin_off;
     cudaError_t e = cudaStreamWaitEvent(st, X.last, 0);
     if (!e) e = cudaMemsetAsync(X.next, 0, words * sizeof(unsigned), st);
     const bool fan = nj > 1;
@@ -947,6 +949,17 @@ perch_status perch_set_launch_config(perch_ctx* c, int32_t threads, int32_t zbuf
     c->cfg.threads = threads;
     c->cfg.zcap_words = zbuf_words & ~3;
     c->cfg.mark_bits = mark_bits;
+    return PERCH_OK;
+}
+
+perch_status perch_set_raster_bins(perch_ctx* c, int32_t bin_cap)
+{
+    if (!c) return PERCH_E_INVALID;
+    c->err.clear();
+    if (refuse_while_serving(c) != PERCH_OK) return PERCH_E_BUSY;
+    if (bin_cap != 0 && (bin_cap < 64 || bin_cap > 65536))
+        return fail(c, PERCH_E_INVALID, "bin capacity %d: 0 or 64 .. 65536", bin_cap);
+    c->cfg.bin_cap = bin_cap;
     return PERCH_OK;
 }
 

@@ -122,7 +122,8 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
         max_verts = std::max(max_verts, j.m.n_verts);
         small_images = small_images && j.sc.W <= 1023 && j.sc.H <= 1023;
     }
-    const long long vstride = small_images ? ((long long)max_verts + 31) / 32 * 32 : 0;
+    long long bin_off = 0;
+    const long long vstride = small_images ? perch::vcache_slot_words(max_verts, cfg.bin_cap, &bin_off) : 0;
     const size_t words = nj + ((size_t)resident + 31) / 32;
     void* p = nullptr;
     if ((st = dalloc(c, words * sizeof(unsigned), &p)) == PERCH_OK) G->next = (unsigned*)p;
@@ -156,6 +157,8 @@ perch_status perch_batch_graph_create(perch_ctx* c, const perch_work_item* items
         a.next = G->next + j;
         a.vcache = vstride ? (unsigned long long*)G->vcache : nullptr;
         a.vstride = vstride;
+        a.bin_cap = vstride ? cfg.bin_cap : 0;
+        a.bin_off = bin_off;
         a.vmask = G->next + nj;
         a.vslots = resident;
         cudaGraphNode_t dep = (j >= 4 && nodes[j - 4]) ? nodes[j - 4] : reset;
@@ -211,7 +214,8 @@ perch_status perch_batch_graph_destroy(perch_batch_graph* G)
 }
 
 perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t n_items,
-                            const float* poses, int32_t* costs, int32_t* threads, int32_t* zbuf_words)
+                            const float* poses, int32_t* costs, int32_t* threads, int32_t* zbuf_words,
+                            int32_t* bin_cap)
 {
     if (!c || !threads || !zbuf_words) return PERCH_E_INVALID;
     c->err.clear();
@@ -236,8 +240,10 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
     if (hit != c->tuned.end()) {
         c->cfg.threads = hit->second.threads;
         c->cfg.zcap_words = hit->second.zcap_words;
+        c->cfg.bin_cap = hit->second.bin_cap;
         *threads = c->cfg.threads;
         *zbuf_words = c->cfg.zcap_words;
+        if (bin_cap) *bin_cap = c->cfg.bin_cap;
         return PERCH_OK;
     }
     // time each shape on a sample of whole items (launches of the real
@@ -261,13 +267,18 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // threads x z-buffer words x tile-bin capacity; bins only where small
+    // z-buffers make several tiles per hypothesis likely
     const int th[3] = {128, 256, 512};
     const int zw[4] = {2048, 4096, 8192, 16384};
+    const int bc[3] = {0, 1024, 4096};
     for (int ti = 0; ti < 3 && st == PERCH_OK; ++ti) {
         for (int zi = 0; zi < 4 && st == PERCH_OK; ++zi) {
+          for (int bi = 0; bi < (zw[zi] <= 4096 ? 3 : 1) && st == PERCH_OK; ++bi) {
             perch::ScoreConfig cfg = saved;
             cfg.threads = th[ti];
             cfg.zcap_words = zw[zi];
+            cfg.bin_cap = bc[bi];
             if (perch::score_smem_bytes(cfg, mw) > 200 * 1024) continue;
             float ms = 3.0e38f;
             for (int rep = 0; rep < 2 && st == PERCH_OK; ++rep) {
@@ -283,6 +294,7 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
                 best_ms = ms;
                 best = cfg;
             }
+          }
         }
     }
     cudaEventDestroy(e0);
@@ -290,9 +302,11 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
     if (st != PERCH_OK) return st;
     c->cfg.threads = best.threads;
     c->cfg.zcap_words = best.zcap_words;
+    c->cfg.bin_cap = best.bin_cap;
     c->tuned[key] = c->cfg;
     *threads = c->cfg.threads;
     *zbuf_words = c->cfg.zcap_words;
+    if (bin_cap) *bin_cap = c->cfg.bin_cap;
     return check_device_error(c);
 }
 

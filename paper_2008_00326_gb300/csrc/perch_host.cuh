@@ -127,7 +127,7 @@ struct perch_ctx {
     cudaEvent_t best_last = nullptr;                // the last argmin launch (they share the scratch)
     perch_host::ScoreScratch plain;                    // scratch of the context's own scoring launches
     std::map<uint64_t, perch::ScoreConfig> tuned;   // autotuner results by batch class
-    perch::ScoreConfig cfg{256, 8192, 1 << 16};
+    perch::ScoreConfig cfg{256, 8192, 1 << 16, 0};
     // A running server's threads share the context: they and the calls that
     // may overlap them (loading and releasing meshes and observations) hold
     // mu around the maps, the budget and the allocations.  Every other call

@@ -86,7 +86,16 @@ struct ScoreArgs {
     long long vstride;
     unsigned* vmask;          // (vslots + 31) / 32 words, bit set = slot in use; zero when idle
     int vslots;
+    // z-buffer tile bins: when a hypothesis's pixel box needs 2 .. kBinTiles
+    // tiles, each tile's triangles are listed first (bin_cap ids per tile, as
+    // int32 at 8-byte offset bin_off of the block's vertex-cache slot) and the
+    // tile rasterises only those; 0 = no bins.
+    int bin_cap;
+    long long bin_off;
 };
+
+// Most z-buffer tiles a hypothesis may be binned into.
+constexpr int kBinTiles = 32;
 
 // Error bits written by kernels into the context's error word.
 enum : int { kErrKeyRange = 1, kErrMarkCap = 2, kErrHashFull = 4, kErrSourceCap = 8, kErrNoSlot = 16,
@@ -115,7 +124,17 @@ struct ScoreConfig {
     int threads;              // 128, 256 or 512
     int zcap_words;           // z-buffer words (32-bit keys: pixels; 64-bit: half)
     int mark_bits;            // admissible-box bitset capacity in bits
+    int bin_cap;              // triangles per z-buffer tile bin, 0 = no bins
 };
+
+// 8-byte words of one vertex-cache slot: the vertex records, then (bin_cap > 0)
+// kBinTiles bins of bin_cap int32 triangle ids.
+inline long long vcache_slot_words(int max_verts, int bin_cap, long long* bin_off)
+{
+    const long long v = ((long long)max_verts + 31) / 32 * 32;
+    *bin_off = v;
+    return bin_cap > 0 ? v + ((long long)kBinTiles * bin_cap + 63) / 64 * 32 : v;
+}
 
 size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words);
 // Blocks of the persistent scoring kernel that fit on the device at once.

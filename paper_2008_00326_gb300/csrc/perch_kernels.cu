@@ -895,6 +895,7 @@ struct ScoreSmem {
     TriStage* stage;              // per warp 32 staged triangles (aliases probe)
     int* next_batch;
     int* refused;                 // tree edges: the object would occlude a placed one
+    int* bin_cnt;                 // kBinTiles: triangles binned per z-buffer tile
 };
 
 // ---- per-hypothesis vertex cache (one slot of global scratch per block) ----
@@ -1058,24 +1059,35 @@ __device__ __forceinline__ void raster_staged(const TriStage& e, int u, int v, u
 // others are staged in shared memory (TS, 32 entries per warp) and the
 // samples of their boxes spread evenly over the lanes (a prefix sum of the box
 // areas, then a binary search per sample for its triangle).  No barrier inside.
-template <int NT, bool K32, bool VC>
+//
+// LIST: the triangles are list[0 .. n_list) (the tile's bin, written by this
+// block) instead of the whole mesh.
+template <int NT, bool K32, bool VC, bool LIST = false>
 __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& mesh, const float* P,
                                             const unsigned long long* vc, TriStage* TS, uint32_t* zbuf,
-                                            int tu0, int tv0, int tu1, int tv1, int tw, int* err)
+                                            int tu0, int tv0, int tu1, int tv1, int tw, int* err,
+                                            const int* list = nullptr, int n_list = 0)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tcap = tw * (tv1 - tv0);
-    // vertex ids of the lane's next triangle, loaded one iteration ahead
-    int4 tv_next = warp * 32 + lane < mesh.n_tris ? __ldg(&mesh.tris[warp * 32 + lane]) : make_int4(0, 0, 0, 0);
-    for (int base = warp * 32; base < mesh.n_tris; base += NT) {
-        const int t = base + lane;
+    const int n = LIST ? n_list : mesh.n_tris;
+    // id and vertex ids of the lane's next triangle, loaded one iteration ahead
+    int t_next = warp * 32 + lane;
+    if (LIST && t_next < n) t_next = list[t_next];
+    int4 tv_next = warp * 32 + lane < n ? __ldg(&mesh.tris[t_next]) : make_int4(0, 0, 0, 0);
+    for (int base = warp * 32; base < n; base += NT) {
+        const int i = base + lane;
+        const int t = LIST ? t_next : i;
         const int4 tv = tv_next;
-        if (t + NT < mesh.n_tris) tv_next = __ldg(&mesh.tris[t + NT]);
+        if (i + NT < n) {
+            t_next = LIST ? list[i + NT] : i + NT;
+            tv_next = __ldg(&mesh.tris[t_next]);
+        }
         int area = 0;
         TriSetup o;
         // the sample box does not depend on the orientation: test it first, so
         // that the many triangles covering no sample of the tile skip the rest
-        if (t < mesh.n_tris && load_tri<VC>(sc, mesh, P, vc, tv, o)) {
+        if (i < n && load_tri<VC>(sc, mesh, P, vc, tv, o)) {
             int xmin = min(o.x[0], min(o.x[1], o.x[2])), xmax = max(o.x[0], max(o.x[1], o.x[2]));
             int ymin = min(o.y[0], min(o.y[1], o.y[2])), ymax = max(o.y[0], max(o.y[1], o.y[2]));
             int u0 = max(ceil16(xmin), tu0), u1 = min(floor16(xmax), tu1 - 1);
@@ -1142,6 +1154,41 @@ __device__ __forceinline__ void raster_tile(const DevScene& sc, const DevMesh& m
                                err);
         }
         __syncwarp();
+    }
+}
+
+// Tile bins of one hypothesis: the pixel box rbox is rasterised in tiles of tw
+// x th pixels (n_tx per row of tiles); every triangle whose sample box meets a
+// tile is listed in that tile's bin (bins + tile * cap, count in cnt[tile];
+// a count above cap marks a bin that overflowed).  A triangle covers samples
+// only inside its sample box, so a tile rasterised from its bin gets the same
+// z-buffer as from the whole mesh.  Bin order depends on timing; the
+// z-buffer does not (atomicMin).
+template <int NT, bool VC>
+__device__ void bin_triangles(const DevScene& sc, const DevMesh& mesh, const float* P, const unsigned long long* vc,
+                              const int* rbox, int tw, int th, int n_tx, int* bins, int cap, int* cnt)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int4 tv_next = warp * 32 + lane < mesh.n_tris ? __ldg(&mesh.tris[warp * 32 + lane]) : make_int4(0, 0, 0, 0);
+    for (int base = warp * 32; base < mesh.n_tris; base += NT) {
+        const int t = base + lane;
+        const int4 tv = tv_next;
+        if (t + NT < mesh.n_tris) tv_next = __ldg(&mesh.tris[t + NT]);
+        TriSetup o;
+        if (t >= mesh.n_tris || !load_tri<VC>(sc, mesh, P, vc, tv, o)) continue;
+        const int u0 = max(ceil16(min(o.x[0], min(o.x[1], o.x[2]))), rbox[0]);
+        const int u1 = min(floor16(max(o.x[0], max(o.x[1], o.x[2]))), rbox[2] - 1);
+        const int v0 = max(ceil16(min(o.y[0], min(o.y[1], o.y[2]))), rbox[1]);
+        const int v1 = min(floor16(max(o.y[0], max(o.y[1], o.y[2]))), rbox[3] - 1);
+        if (u0 > u1 || v0 > v1) continue;
+        const int tx0 = div_small(u0 - rbox[0], tw), tx1 = div_small(u1 - rbox[0], tw);
+        const int ty0 = div_small(v0 - rbox[1], th), ty1 = div_small(v1 - rbox[1], th);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                const int tile = ty * n_tx + tx;
+                const int k = atomicAdd(&cnt[tile], 1);
+                if (k < cap) bins[tile * cap + k] = t;
+            }
     }
 }
 
@@ -1225,7 +1272,7 @@ enum : int { kModePlain = 0, kModeTree = 1, kModeEq3 = 2 };
 // Rasterise, resolve and radius-search the pixel box rbox in z-buffer tiles.
 // J_r is accumulated when count_jr; marks are set for nearest neighbours that
 // fall in rows [mv0, mv1) of the admissible box vbox.
-template <int NT, bool K32, bool VC, int MODE>
+template <int NT, bool K32, bool VC, int MODE, bool BINS>
 __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, const unsigned long long* vc,
                             const int* rbox, const ScoreSmem& S, const int* vbox, int mv0, int mv1,
                             bool count_jr, int& jr_local)
@@ -1244,15 +1291,30 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
     const uint32_t empty32 = 0xFFFFFFFFu;
     const int vw = vbox[2] - vbox[0];
     uint32_t* zbuf = S.zbuf;
+    // a pixel box of several tiles: each tile's triangles binned first
+    const int n_tx = (rw + tw - 1) / tw, n_tiles = n_tx * ((rh + th - 1) / th);
+    const bool binned = BINS && VC && a.bin_cap > 0 && n_tiles > 1 && n_tiles <= kBinTiles;
+    int* bins = binned ? reinterpret_cast<int*>(const_cast<unsigned long long*>(vc) + a.bin_off) : nullptr;
+    if (binned) {
+        for (int i = threadIdx.x; i < n_tiles; i += NT) S.bin_cnt[i] = 0;
+        __syncthreads();
+        if (BINS) bin_triangles<NT, VC>(sc, J.m, P, vc, rbox, tw, th, n_tx, bins, a.bin_cap, S.bin_cnt);
+        __syncthreads();
+    }
+    int tile = 0;
     for (int tv0 = rbox[1]; tv0 < rbox[3]; tv0 += th) {
-        for (int tu0 = rbox[0]; tu0 < rbox[2]; tu0 += tw) {
+        for (int tu0 = rbox[0]; tu0 < rbox[2]; tu0 += tw, ++tile) {
             const int tu1 = min(tu0 + tw, rbox[2]), tv1 = min(tv0 + th, rbox[3]);
             const int tpx = tw * (tv1 - tv0);
             const int words = K32 ? tpx : 2 * tpx;
             for (int i = threadIdx.x; i < words; i += NT) zbuf[i] = empty32;
             if (threadIdx.x == 0) *S.next_batch = 0;
             __syncthreads();
-            raster_tile<NT, K32, VC>(sc, J.m, P, vc, TS, zbuf, tu0, tv0, tu1, tv1, tw, a.err);
+            if (BINS && binned && S.bin_cnt[tile] <= a.bin_cap)
+                raster_tile<NT, K32, VC, BINS>(sc, J.m, P, vc, TS, zbuf, tu0, tv0, tu1, tv1, tw, a.err,
+                                               bins + tile * a.bin_cap, S.bin_cnt[tile]);
+            else
+                raster_tile<NT, K32, VC>(sc, J.m, P, vc, TS, zbuf, tu0, tv0, tu1, tv1, tw, a.err);
             __syncthreads();
             if (a.dump) {
                 for (int i = threadIdx.x; i < tpx; i += NT) {
@@ -1423,7 +1485,7 @@ __device__ __noinline__ void jo_colour_band(const ScoreArgs& a, const Job& J, co
 }
 
 // Score hypothesis h (one block).  Writes costs[2h] = J_o, costs[2h+1] = J_r.
-template <int NT, int MODE>
+template <int NT, int MODE, bool BINS>
 __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const ScoreSmem& S, float* s_pose,
                           int* s_rbox, int* s_vbox, int* s_k32, int (*s_red)[NT / 32],
                           unsigned long long* vc)
@@ -1468,11 +1530,11 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = mfill;
         __syncthreads();
         if (*s_k32) {
-            if (use_vc) score_tiles<NT, true, true, MODE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, true, false, MODE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, true, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, true, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
         } else {
-            if (use_vc) score_tiles<NT, false, true, MODE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, false, false, MODE>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, false, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            else score_tiles<NT, false, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
         }
         __syncthreads();
         if (jo1 && sc.color_check) {
@@ -1608,12 +1670,12 @@ __device__ int claim_vslot(unsigned* mask, int nslots)
 // it.  The job is read from the kernel parameters, so its fields are
 // constant-bank operands.  MODE kModeTree: the job's hypotheses are edges of the
 // Monotone Scene Generation tree from the state in job.tree.
-template <int NT, int MODE>
+template <int NT, int MODE, bool BINS>
 __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
-    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_slot, s_refused;
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_slot, s_refused, s_bin_cnt[kBinTiles];
     __shared__ long long s_h;
     __shared__ int s_red[3][NT / 32];
 
@@ -1626,6 +1688,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.stage = reinterpret_cast<TriStage*>(smem + L.probe);
     S.next_batch = &s_next;
     S.refused = &s_refused;
+    S.bin_cnt = s_bin_cnt;
     if (threadIdx.x == 0) s_slot = a.vcache ? claim_vslot(a.vmask, a.vslots) : -1;
     __syncthreads();
     unsigned long long* vc = s_slot >= 0 ? a.vcache + (size_t)s_slot * a.vstride : nullptr;
@@ -1634,7 +1697,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
         __syncthreads();
         const long long h = s_h;
         if (h >= a.n) break;
-        score_one<NT, MODE>(a, a.job, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
+        score_one<NT, MODE, BINS>(a, a.job, h, S, s_pose, s_rbox, s_vbox, &s_k32, s_red, vc);
     }
     // every thread has passed the barrier after its last use of the slot
     if (threadIdx.x == 0 && s_slot >= 0) {
@@ -1648,16 +1711,16 @@ size_t score_smem_bytes(const ScoreConfig& cfg, int mark_words)
     return smem_layout(cfg.zcap_words, mark_words, cfg.threads).total;
 }
 
-template <int NT, int MODE>
+template <int NT, int MODE, bool BINS>
 static int score_grid_nt(size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_score<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(k_score<NT, MODE, BINS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT, MODE>, NT, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_score<NT, MODE, BINS>, NT, smem) != cudaSuccess)
         return -1;
     return max(1, per) * max(1, sms);
 }
@@ -1665,9 +1728,9 @@ static int score_grid_nt(size_t smem)
 template <int NT>
 static int score_grid_all(size_t smem)
 {
-    // the three specialisations share the vertex-cache pool: size for the smallest
-    return min(score_grid_nt<NT, kModePlain>(smem),
-               min(score_grid_nt<NT, kModeTree>(smem), score_grid_nt<NT, kModeEq3>(smem)));
+    // the specialisations share the vertex-cache pool: size for the smallest
+    return min(min(score_grid_nt<NT, kModePlain, false>(smem), score_grid_nt<NT, kModePlain, true>(smem)),
+               min(score_grid_nt<NT, kModeTree, false>(smem), score_grid_nt<NT, kModeEq3, false>(smem)));
 }
 
 int score_grid(const ScoreConfig& cfg, int mark_words)
@@ -1680,13 +1743,15 @@ int score_grid(const ScoreConfig& cfg, int mark_words)
     }
 }
 
-// The kernel specialisation a job runs on.
+// The kernel specialisation a launch runs on (tile bins: plain scoring only;
+// the other modes rasterise every tile from the whole mesh).
 template <int NT>
-static const void* score_kernel(const Job& j)
+static const void* score_kernel(const ScoreArgs& a)
 {
-    if (j.tree.depth) return (const void*)k_score<NT, kModeTree>;
-    if (j.sc.jo_mode == 1) return (const void*)k_score<NT, kModeEq3>;
-    return (const void*)k_score<NT, kModePlain>;
+    if (a.job.tree.depth) return (const void*)k_score<NT, kModeTree, false>;
+    if (a.job.sc.jo_mode == 1) return (const void*)k_score<NT, kModeEq3, false>;
+    if (a.bin_cap > 0) return (const void*)k_score<NT, kModePlain, true>;
+    return (const void*)k_score<NT, kModePlain, false>;
 }
 
 template <int NT>
@@ -1694,7 +1759,7 @@ static cudaError_t launch_score_nt(const ScoreArgs& a, const ScoreConfig& cfg, i
 {
     const size_t smem = score_smem_bytes(cfg, a.mark_words);
     const unsigned g = (unsigned)(a.n < grid ? a.n : grid);
-    const void* fn = score_kernel<NT>(a.job);
+    const void* fn = score_kernel<NT>(a);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ScoreArgs copy = a;
@@ -1708,7 +1773,7 @@ static cudaError_t add_score_node_nt(cudaGraph_t g, const cudaGraphNode_t* deps,
                                      cudaGraphNode_t* out)
 {
     const size_t smem = score_smem_bytes(cfg, a.mark_words);
-    const void* fn = score_kernel<NT>(a.job);
+    const void* fn = score_kernel<NT>(a);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ScoreArgs copy = a;
@@ -2023,7 +2088,8 @@ __device__ void gicp_source(const GicpArgs& a, const Job& J, const float* P, con
             const int nu = us0 < tu1 ? (tu1 - 1 - us0) / s + 1 : 0;
             const int nv = vs0 < tv1 ? (tv1 - 1 - vs0) / s + 1 : 0;
             for (int k = threadIdx.x; k < nu * nv; k += NT) {
-                const int u = us0 + (k % nu) * s, v = vs0 + (k / nu) * s;
+                const int kv = div_small(k, nu);
+                const int u = us0 + (k - kv * nu) * s, v = vs0 + kv * s;
                 const int zi = (v - tv0) * tw + (u - tu0);
                 unsigned d = 0;
                 int tri = -1;

@@ -31,7 +31,7 @@ EXPORTS = ("perch_default_params", "perch_create", "perch_destroy", "perch_last_
            "perch_ticket_times", "perch_server_stop", "perch_pose_proposals",
            "perch_default_gicp_params", "perch_refine_hypotheses", "perch_tree_search",
            "perch_measure_smem_atomics", "perch_add_s", "perch_add_s_auc", "perch_sync",
-           "perch_ticket_release", "perch_server_tickets", "perch_best_key")
+           "perch_ticket_release", "perch_server_tickets", "perch_best_key", "perch_set_raster_bins")
 
 
 class PerchError(RuntimeError):
@@ -195,7 +195,8 @@ def load(path: str | None = None):
         "perch_batch_graph_create": ([P, P, I32, P, P, P], I32),
         "perch_batch_graph_launch": ([P, P], I32),
         "perch_batch_graph_destroy": ([P], I32),
-        "perch_autotune": ([P, P, I32, P, P, P, P], I32),
+        "perch_autotune": ([P, P, I32, P, P, P, P, P], I32),
+        "perch_set_raster_bins": ([P, I32], I32),
         "perch_server_start": ([P, P, P], I32),
         "perch_submit": ([P, P, P], I32),
         "perch_poll": ([P, U64], I32),
@@ -418,11 +419,13 @@ def perch_batch_graph_destroy(graph):
 
 
 def perch_autotune(ctx, items, poses, costs):
+    """(threads, z-buffer words, tile-bin capacity) chosen for this batch's class."""
     t = C.c_int32()
     z = C.c_int32()
+    b = C.c_int32()
     _check(ctx, load().perch_autotune(ctx, items, len(items), _ptr_of(poses), _ptr_of(costs),
-                                       C.byref(t), C.byref(z)))
-    return t.value, z.value
+                                       C.byref(t), C.byref(z), C.byref(b)))
+    return t.value, z.value, b.value
 
 
 def perch_pose_proposals(ctx, scene_id, mesh_id, label, bbox, M, N, K, poses=None, z_range=None,
@@ -542,6 +545,10 @@ def perch_set_launch_config(ctx, threads, zbuf_words, mark_bits=0):
     _check(ctx, load().perch_set_launch_config(ctx, threads, zbuf_words, mark_bits))
 
 
+def perch_set_raster_bins(ctx, bin_cap):
+    _check(ctx, load().perch_set_raster_bins(ctx, bin_cap))
+
+
 def perch_debug_render_keys(ctx, scene_id, mesh_id, roi, pose, W, H):
     keep, proi = _roi(roi)
     p, pp = _host(pose, np.float32)
@@ -596,8 +603,9 @@ class Context:
     def refine(self, scene_id, mesh_id, label, roi, poses, params=None, **kw):
         return perch_refine_hypotheses(self.ctx, scene_id, mesh_id, label, roi, poses, params, **kw)
 
-    def set_launch_config(self, threads, zbuf_words, mark_bits=0):
+    def set_launch_config(self, threads, zbuf_words, mark_bits=0, bin_cap=0):
         perch_set_launch_config(self.ctx, threads, zbuf_words, mark_bits)
+        perch_set_raster_bins(self.ctx, bin_cap)
 
     def render_keys(self, scene_id, mesh_id, roi, pose, W, H):
         return perch_debug_render_keys(self.ctx, scene_id, mesh_id, roi, pose, W, H)

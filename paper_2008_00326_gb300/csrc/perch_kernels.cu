@@ -635,7 +635,7 @@ static_assert(sizeof(WarpProbe) % 16 == 0, "per-warp scratch keeps 16-byte align
 // that candidate i of the group is point runs[r].x + i for the first run r
 // with i < runs[r].y.
 __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, const int* gy,
-                                             const int* gz, int ng, WarpProbe& W, int lane)
+                                             const int* gz, int ng, WarpProbe& W, int lane, int* nruns)
 {
     const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
 #pragma unroll
@@ -701,6 +701,7 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
             W.runs[g][__popc(nonempty & ((1u << lane) - 1u))] =
                 make_int2((int)start - (int)(incl - cnt), (int)incl);
         if (lane == 31) W.total[g] = (int)incl;
+        nruns[g] = __popc(nonempty);
     }
 }
 
@@ -756,23 +757,29 @@ __device__ __forceinline__ unsigned long long scan_staged(const DevScene& sc, co
     return local;
 }
 
-// Candidates c0 .. c0 + 63 of group g's runs staged in the warp's shared
-// memory (two coalesced loads per lane); r is the lane's run cursor, carried
-// from chunk to chunk.
-__device__ __forceinline__ void stage_chunk(const DevScene& sc, WarpProbe& W, int g, int c0, int T, int lane, int& r,
+// Candidates c0 .. c0 + 63 of a group's runs staged in the warp's shared
+// memory (two coalesced loads per lane).  Lane j < (the group's run count)
+// holds run j as run = (start - first candidate index, end candidate index)
+// (the other lanes: end = INT_MAX); the run of candidate c is the first whose
+// end exceeds c, found by a five-step binary search over the lanes.
+__device__ __forceinline__ int candidate_point(int2 run, int c)
+{
+    int r = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int e = __shfl_sync(0xffffffffu, run.y, r + step - 1);
+        if (e <= c) r += step;
+    }
+    return __shfl_sync(0xffffffffu, run.x, r) + c;
+}
+
+__device__ __forceinline__ void stage_chunk(const DevScene& sc, WarpProbe& W, int2 run, int c0, int T, int lane,
                                             int* err)
 {
     const int ci = c0 + lane, cj = ci + 32;
-    if (ci < T) {
-        while (W.runs[g][r].y <= ci) ++r;
-        if (PERCH_CHECKED((unsigned)(W.runs[g][r].x + ci) < (unsigned)sc.n_pts, err))
-            W.stage[lane] = __ldg(&sc.pts[W.runs[g][r].x + ci]);
-    }
-    if (cj < T) {
-        while (W.runs[g][r].y <= cj) ++r;
-        if (PERCH_CHECKED((unsigned)(W.runs[g][r].x + cj) < (unsigned)sc.n_pts, err))
-            W.stage[lane + 32] = __ldg(&sc.pts[W.runs[g][r].x + cj]);
-    }
+    const int pi = candidate_point(run, ci), pj = candidate_point(run, cj);
+    if (ci < T && PERCH_CHECKED((unsigned)pi < (unsigned)sc.n_pts, err)) W.stage[lane] = __ldg(&sc.pts[pi]);
+    if (cj < T && PERCH_CHECKED((unsigned)pj < (unsigned)sc.n_pts, err)) W.stage[lane + 32] = __ldg(&sc.pts[pj]);
 }
 
 template <bool MARK>
@@ -818,7 +825,8 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
             }
         }
         if (valid && my_g >= g0 && my_g < g0 + kGroups) W.qlist[my_g - g0][my_pos] = (unsigned char)lane;
-        lookup_cells(sc, gx, gy, gz, ng, W, lane);
+        int nruns[kGroups];
+        lookup_cells(sc, gx, gy, gz, ng, W, lane, nruns);
         __syncwarp();
         for (int g = 0; g < ng; ++g) {
             const int T = W.total[g];
@@ -833,9 +841,9 @@ __device__ unsigned long long probe_batch(const DevScene& sc, bool valid, float 
             const int ql = active ? W.qlist[g][qj] : 0;
             const float4 q = W.q[ql];
             unsigned long long local = kEmptyKey;
-            int r = 0;
+            const int2 run = lane < nruns[g] ? W.runs[g][lane] : make_int2(0, INT_MAX);
             for (int c0 = 0; c0 < T; c0 += 64) {
-                stage_chunk(sc, W, g, c0, T, lane, r, mb.err);
+                stage_chunk(sc, W, run, c0, T, lane, mb.err);
                 __syncwarp();
                 const int n = min(64, T - c0);
                 if (active)
@@ -1495,10 +1503,13 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
     if (threadIdx.x < 12) s_pose[threadIdx.x] = J.poses[h * 12 + threadIdx.x];
     if (TREE && threadIdx.x == 0) *S.refused = 0;
     __syncthreads();
+    // the two boxes in two warps, in parallel with each other and with the
+    // other warps' share of the vertex pass
     if (threadIdx.x == 0) {
         float zmax;
         project_box(sc, s_pose, J.m.lo, J.m.hi, J.roi[0], J.roi[1], J.roi[2], J.roi[3], s_rbox, &zmax);
         *s_k32 = (J.m.n_tris <= 65535 && zmax < 6.5f) ? 1 : 0;
+    } else if (threadIdx.x == 32) {
         if (J.label >= 0) {
             s_vbox[0] = J.roi[0]; s_vbox[1] = J.roi[1]; s_vbox[2] = J.roi[2]; s_vbox[3] = J.roi[3];
         } else {

@@ -904,6 +904,8 @@ struct ScoreSmem {
     int* next_batch;
     int* refused;                 // tree edges: the object would occlude a placed one
     int* bin_cnt;                 // kBinTiles: triangles binned per z-buffer tile
+    int* jo_next;                 // plain scoring: next chunk of J_o's |I cap V|
+    int* raster_done;             // plain scoring: warps done with the tile's raster
 };
 
 // ---- per-hypothesis vertex cache (one slot of global scratch per block) ----
@@ -1277,13 +1279,62 @@ __device__ __forceinline__ void jo_colour_pass(const Job& J, const float* P, con
 // plain path carries none of the other two's code.
 enum : int { kModePlain = 0, kModeTree = 1, kModeEq3 = 2 };
 
+// Is the observed point p of pixel pix in the admissible set V(O) at pose P
+// (Sec. IV-A J_o; labels Sec. V-C)?  The inscribed cylinder about the
+// object's z-axis (radius^2 rr, height vol_h) in the object frame, R^T (p - t),
+// or the pixel's label.
+__device__ __forceinline__ bool in_admissible(const DevScene& sc, const Job& J, const float* P, float rr, int pix,
+                                              float4 p)
+{
+    if (J.label >= 0) return __ldg(&sc.labels[pix]) == J.label;
+    float e0 = __fsub_rn(p.x, P[3]), e1 = __fsub_rn(p.y, P[7]), e2 = __fsub_rn(p.z, P[11]);
+    float q0 = __fadd_rn(__fadd_rn(__fmul_rn(P[0], e0), __fmul_rn(P[4], e1)), __fmul_rn(P[8], e2));
+    float q1 = __fadd_rn(__fadd_rn(__fmul_rn(P[1], e0), __fmul_rn(P[5], e1)), __fmul_rn(P[9], e2));
+    float q2 = __fadd_rn(__fadd_rn(__fmul_rn(P[2], e0), __fmul_rn(P[6], e1)), __fmul_rn(P[10], e2));
+    return __fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)) <= rr && q2 >= 0.0f && q2 <= J.m.vol_h;
+}
+
+// |I cap V| of plain scoring, counted in chunks of kJoChunk lattice pixels of
+// the whole admissible box taken from a shared counter (zero at the start of
+// the hypothesis).  It needs nothing rendered, so warps that finish the
+// raster early count chunks while the others still rasterise (`stop`: the
+// count of warps done with the raster; they stop once all are), and the
+// chunks left over are counted after the search.
+constexpr int kJoChunk = 256;
+
+template <int NT>
+__device__ void jo_count_in(const DevScene& sc, const Job& J, const float* P, const int* vbox, int* counter,
+                            const int* stop, int& n_in)
+{
+    const int s = sc.stride, lane = threadIdx.x & 31;
+    const int us0 = ((vbox[0] + s - 1) / s) * s, vs0 = ((vbox[1] + s - 1) / s) * s;
+    const int nu = us0 < vbox[2] ? (vbox[2] - 1 - us0) / s + 1 : 0;
+    const int nv = vs0 < vbox[3] ? (vbox[3] - 1 - vs0) / s + 1 : 0;
+    const int npx = nu * nv;
+    const float rr = __fmul_rn(J.m.vol_r, J.m.vol_r);
+    for (;;) {
+        if (stop && *reinterpret_cast<const volatile int*>(stop) >= NT / 32) break;
+        int c = 0;
+        if (lane == 0) c = atomicAdd(counter, 1);
+        const int k0 = __shfl_sync(0xffffffffu, c, 0) * kJoChunk;
+        if (k0 >= npx) break;
+        const int k1 = min(k0 + kJoChunk, npx);
+        for (int k = k0 + lane; k < k1; k += 32) {
+            const int kv = div_small(k, nu);
+            const int pix = (vs0 + kv * s) * sc.W + us0 + (k - kv * nu) * s;
+            const float4 p = __ldg(&sc.pxyz[pix]);
+            if (p.w != 0.0f && in_admissible(sc, J, P, rr, pix, p)) ++n_in;
+        }
+    }
+}
+
 // Rasterise, resolve and radius-search the pixel box rbox in z-buffer tiles.
 // J_r is accumulated when count_jr; marks are set for nearest neighbours that
 // fall in rows [mv0, mv1) of the admissible box vbox.
 template <int NT, bool K32, bool VC, int MODE, bool BINS>
 __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, const unsigned long long* vc,
                             const int* rbox, const ScoreSmem& S, const int* vbox, int mv0, int mv1,
-                            bool count_jr, int& jr_local)
+                            bool count_jr, int& jr_local, int& n_in)
 {
     constexpr bool TREE = MODE == kModeTree, EQ3 = MODE == kModeEq3;
     const DevScene& sc = J.sc;
@@ -1316,13 +1367,22 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
             const int tpx = tw * (tv1 - tv0);
             const int words = K32 ? tpx : 2 * tpx;
             for (int i = threadIdx.x; i < words; i += NT) zbuf[i] = empty32;
-            if (threadIdx.x == 0) *S.next_batch = 0;
+            if (threadIdx.x == 0) {
+                *S.next_batch = 0;
+                *S.raster_done = 0;
+            }
             __syncthreads();
             if (BINS && binned && S.bin_cnt[tile] <= a.bin_cap)
                 raster_tile<NT, K32, VC, BINS>(sc, J.m, P, vc, TS, zbuf, tu0, tv0, tu1, tv1, tw, a.err,
                                                bins + tile * a.bin_cap, S.bin_cnt[tile]);
             else
                 raster_tile<NT, K32, VC>(sc, J.m, P, vc, TS, zbuf, tu0, tv0, tu1, tv1, tw, a.err);
+            if (MODE == kModePlain && count_jr) {
+                // the raster's early finishers count J_o's |I cap V| meanwhile
+                if (lane == 0) atomicAdd(S.raster_done, 1);
+                __syncwarp();
+                jo_count_in<NT>(sc, J, P, vbox, S.jo_next, S.raster_done, n_in);
+            }
             __syncthreads();
             if (a.dump) {
                 for (int i = threadIdx.x; i < tpx; i += NT) {
@@ -1502,6 +1562,7 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
     const DevScene& sc = J.sc;
     if (threadIdx.x < 12) s_pose[threadIdx.x] = J.poses[h * 12 + threadIdx.x];
     if (TREE && threadIdx.x == 0) *S.refused = 0;
+    if (threadIdx.x == 0) *S.jo_next = 0;
     __syncthreads();
     // the two boxes in two warps, in parallel with each other and with the
     // other warps' share of the vertex pass
@@ -1541,11 +1602,15 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = mfill;
         __syncthreads();
         if (*s_k32) {
-            if (use_vc) score_tiles<NT, true, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, true, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, true, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
+                                                               n_in);
+            else score_tiles<NT, true, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
+                                                               n_in);
         } else {
-            if (use_vc) score_tiles<NT, false, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
-            else score_tiles<NT, false, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr);
+            if (use_vc) score_tiles<NT, false, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
+                                                               n_in);
+            else score_tiles<NT, false, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
+                                                               n_in);
         }
         __syncthreads();
         if (jo1 && sc.color_check) {
@@ -1557,6 +1622,24 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
                 if (use_vc) jo_colour_band<NT, false, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
                 else jo_colour_band<NT, false, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
             }
+        }
+        if (MODE == kModePlain) {
+            // ---- J_o's marked part: the band's marked pixels that lie in V(h)
+            // (every mark is a nearest neighbour, a pixel of I); |I cap V| is
+            // counted by jo_count_in
+            for (int w = threadIdx.x; w < mwords; w += NT) {
+                unsigned bits = S.marks[w];
+                while (bits) {
+                    const int bit = 32 * w + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int r = div_small(bit, vw);
+                    const int pix = (mv0 + r) * sc.W + s_vbox[0] + (bit - r * vw);
+                    const float4 p = __ldg(&sc.pxyz[pix]);
+                    if (p.w != 0.0f && in_admissible(sc, J, P, rr, pix, p)) ++n_marked;
+                }
+            }
+            __syncthreads();
+            continue;
         }
         // ---- J_o over the admissible set V(h), rows [mv0, mv1)
         const int us0 = ((s_vbox[0] + s - 1) / s) * s, vs0 = ((mv0 + s - 1) / s) * s;
@@ -1602,6 +1685,8 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         }
         __syncthreads();
     }
+    // the chunks of |I cap V| the raster's early finishers did not count
+    if (MODE == kModePlain) jo_count_in<NT>(sc, J, P, s_vbox, S.jo_next, nullptr, n_in);
     // ---- warp-shuffle reduction of (J_r, |I cap V|, marked)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1686,7 +1771,8 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
-    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_slot, s_refused, s_bin_cnt[kBinTiles];
+    __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_slot, s_refused, s_bin_cnt[kBinTiles], s_jo_next,
+        s_raster_done;
     __shared__ long long s_h;
     __shared__ int s_red[3][NT / 32];
 
@@ -1700,6 +1786,8 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArg
     S.next_batch = &s_next;
     S.refused = &s_refused;
     S.bin_cnt = s_bin_cnt;
+    S.jo_next = &s_jo_next;
+    S.raster_done = &s_raster_done;
     if (threadIdx.x == 0) s_slot = a.vcache ? claim_vslot(a.vmask, a.vslots) : -1;
     __syncthreads();
     unsigned long long* vc = s_slot >= 0 ? a.vcache + (size_t)s_slot * a.vstride : nullptr;

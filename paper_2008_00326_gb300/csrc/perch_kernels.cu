@@ -1334,10 +1334,11 @@ __device__ void jo_count_in(const DevScene& sc, const Job& J, const float* P, co
 template <int NT, bool K32, bool VC, int MODE, bool BINS>
 __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, const unsigned long long* vc,
                             const int* rbox, const ScoreSmem& S, const int* vbox, int mv0, int mv1,
-                            bool count_jr, int& jr_local, int& n_in)
+                            bool count_jr, int& jr_local, int& n_in, int& n_marked)
 {
     constexpr bool TREE = MODE == kModeTree, EQ3 = MODE == kModeEq3;
     const DevScene& sc = J.sc;
+    const float rr = __fmul_rn(J.m.vol_r, J.m.vol_r);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpProbe& WP = *reinterpret_cast<WarpProbe*>(reinterpret_cast<char*>(S.probe) + warp * kWarpScratch);
     TriStage* TS = reinterpret_cast<TriStage*>(reinterpret_cast<char*>(S.stage) + warp * kWarpScratch);
@@ -1502,8 +1503,16 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                         } else if (!EQ3) {
                             if (pu >= vbox[0] && pu < vbox[2] && pv >= mv0 && pv < mv1) {
                                 int bit = (pv - mv0) * vw + (pu - vbox[0]);
-                                if (PERCH_CHECKED((unsigned)bit < 32u * (unsigned)a.mark_words, a.err))
-                                    atomicOr(&S.marks[bit >> 5], 1u << (bit & 31));
+                                if (PERCH_CHECKED((unsigned)bit < 32u * (unsigned)a.mark_words, a.err)) {
+                                    const unsigned m = 1u << (bit & 31);
+                                    const unsigned was = atomicOr(&S.marks[bit >> 5], m);
+                                    if (MODE == kModePlain && !(was & m)) {
+                                        // J_o's marked part: the first mark of a pixel of V
+                                        const int npix = pv * sc.W + pu;
+                                        const float4 pn = __ldg(&sc.pxyz[npix]);
+                                        if (pn.w != 0.0f && in_admissible(sc, J, P, rr, npix, pn)) ++n_marked;
+                                    }
+                                }
                             }
                         }
                     }
@@ -1603,14 +1612,14 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         __syncthreads();
         if (*s_k32) {
             if (use_vc) score_tiles<NT, true, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
-                                                               n_in);
+                                                               n_in, n_marked);
             else score_tiles<NT, true, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
-                                                               n_in);
+                                                               n_in, n_marked);
         } else {
             if (use_vc) score_tiles<NT, false, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
-                                                               n_in);
+                                                               n_in, n_marked);
             else score_tiles<NT, false, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
-                                                               n_in);
+                                                               n_in, n_marked);
         }
         __syncthreads();
         if (jo1 && sc.color_check) {
@@ -1623,24 +1632,10 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
                 else jo_colour_band<NT, false, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
             }
         }
-        if (MODE == kModePlain) {
-            // ---- J_o's marked part: the band's marked pixels that lie in V(h)
-            // (every mark is a nearest neighbour, a pixel of I); |I cap V| is
-            // counted by jo_count_in
-            for (int w = threadIdx.x; w < mwords; w += NT) {
-                unsigned bits = S.marks[w];
-                while (bits) {
-                    const int bit = 32 * w + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const int r = div_small(bit, vw);
-                    const int pix = (mv0 + r) * sc.W + s_vbox[0] + (bit - r * vw);
-                    const float4 p = __ldg(&sc.pxyz[pix]);
-                    if (p.w != 0.0f && in_admissible(sc, J, P, rr, pix, p)) ++n_marked;
-                }
-            }
-            __syncthreads();
-            continue;
-        }
+        // plain scoring: J_o's marked part was counted as the marks were set
+        // (each pixel of V once, by the lane whose atomicOr set its bit) and
+        // |I cap V| is counted by jo_count_in
+        if (MODE == kModePlain) continue;
         // ---- J_o over the admissible set V(h), rows [mv0, mv1)
         const int us0 = ((s_vbox[0] + s - 1) / s) * s, vs0 = ((mv0 + s - 1) / s) * s;
         const int nu = us0 < s_vbox[2] ? (s_vbox[2] - 1 - us0) / s + 1 : 0;

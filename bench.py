@@ -783,7 +783,7 @@ def main():
                    "sharding": ("one GPU" if world == 1 else
                                 f"{world} ranks: each scores 43^2 positions x 16 yaws per object of a "
                                 f"{16 * world}-yaw grid; one all-reduce MIN of 3 packed (J, id) keys per step"),
-                   "launch": {"threads": 256, "zbuf_words": 8192, "mark_bits": 65536}},
+                   "launch": {"threads": 256, "zbuf_words": 7064, "mark_bits": 32768}},
         "argmin": argmin,
         "latency_ms": {"search_p50": lat[len(lat) // 2], "search_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "what": f"one object's {len(reqs[0].poses):,}-hypothesis search (score + argmin), device-timed"},

@@ -244,10 +244,12 @@ PERCH_API perch_status perch_best_noalloc(const int32_t *costs, const uint64_t *
  * than 65536 triangles and the hypothesis lies within 6.5 m, else a 64-bit key
  * per pixel), and the capacity in bits of the bitset that marks nearest
  * neighbours inside the admissible box (1024 <= mark_bits <= 2^22, 0 = the
- * default 65536).  Pixel boxes larger than the z-buffer are processed in
+ * default 32768).  Pixel boxes larger than the z-buffer are processed in
  * tiles, admissible boxes larger than the bitset in row bands.  Results do not
- * depend on these choices; only speed and shared memory do.  The autotuner of
- * the batched form calls it.  PERCH_E_INVALID outside the ranges. */
+ * depend on these choices; only speed and shared memory do.  A new context
+ * uses 256 threads, 7064 words and 32768 bits (four blocks per SM).  The
+ * autotuner of the batched form calls it.  PERCH_E_INVALID outside the
+ * ranges. */
 PERCH_API perch_status perch_set_launch_config(perch_ctx *ctx, int32_t threads, int32_t zbuf_words,
                                                int32_t mark_bits);
 

@@ -270,10 +270,10 @@ perch_status perch_autotune(perch_ctx* c, const perch_work_item* items, int32_t 
     // threads x z-buffer words x tile-bin capacity; bins only where small
     // z-buffers make several tiles per hypothesis likely
     const int th[3] = {128, 256, 512};
-    const int zw[4] = {2048, 4096, 8192, 16384};
+    const int zw[5] = {2048, 4096, 7064, 8192, 16384};
     const int bc[3] = {0, 1024, 4096};
     for (int ti = 0; ti < 3 && st == PERCH_OK; ++ti) {
-        for (int zi = 0; zi < 4 && st == PERCH_OK; ++zi) {
+        for (int zi = 0; zi < 5 && st == PERCH_OK; ++zi) {
           for (int bi = 0; bi < (zw[zi] <= 4096 ? 3 : 1) && st == PERCH_OK; ++bi) {
             perch::ScoreConfig cfg = saved;
             cfg.threads = th[ti];

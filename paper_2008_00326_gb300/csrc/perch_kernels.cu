@@ -587,7 +587,6 @@ __device__ __forceinline__ void zmin(uint32_t* zbuf, int idx, unsigned d, int tr
 
 constexpr int kWarpQueue = 64;    // kept rendered points queued per warp (a ring)
 constexpr int kGroups = 1;        // distinct query cells looked up together per warp
-constexpr int kCellCache = 32;    // per-warp cache of recent 27-cell lookups (hash index; direct mapped)
 
 // A group of G queries shares a 27-cell candidate list; k = floor(32 / G)
 // lanes test each query's candidates.  Lane l serves query floor(l / k),
@@ -613,7 +612,6 @@ struct __align__(16) WarpProbe {
     unsigned char qlist[kGroups][32];  // per group: the lanes of its queries, in lane order
     float4 q[32];                 // query of each lane
     unsigned long long best[32];  // nearest-neighbour key of each lane's query
-    uint4 cache[kCellCache];      // recent cell lookups: (key lo, key hi, start, count)
     float4 stage[64];             // a chunk of the group's candidates, shared by its queries
 };
 
@@ -654,40 +652,21 @@ __device__ __forceinline__ void lookup_cells(const DevScene& sc, const int* gx, 
                     cnt = __ldg(&sc.cell_start[row + x1 + 1]) - start;
                 }
             }
-        } else {
-            bool hit = false;
-            unsigned long long key = kEmptyKey;
-            uint32_t cs = 0;
-            if (lane < 27) {
-                key = cell_key(gx[g] + dx, gy[g] + dy, gz[g] + dz);
-                // neighbouring query cells share most of their 27 neighbours: look in
-                // the warp's cache of recent lookups before going to the table
-                cs = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 58) & (kCellCache - 1);
-                const uint4 c = W.cache[cs];
-                hit = ((unsigned long long)c.x | ((unsigned long long)c.y << 32)) == key;
-                if (hit) {
-                    start = c.z;
-                    cnt = c.w;
-                } else {
-                    uint32_t slot = hash_slot(key, sc.table_mask);
-                    for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
-                        const uint4 x = __ldg(&sc.table[slot]);
-                        unsigned long long k = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
-                        if (k == key) {
-                            start = x.z;
-                            cnt = x.w;
-                            break;
-                        }
-                        if (k == kEmptyKey) break;
-                        slot = (slot + 1) & sc.table_mask;
-                    }
+        } else if (lane < 27) {
+            // voxel hash (a cell box too large for the dense index): lane j
+            // probes the table for neighbour j
+            const unsigned long long key = cell_key(gx[g] + dx, gy[g] + dy, gz[g] + dz);
+            uint32_t slot = hash_slot(key, sc.table_mask);
+            for (uint32_t probe = 0; probe <= sc.table_mask; ++probe) {
+                const uint4 x = __ldg(&sc.table[slot]);
+                unsigned long long k = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+                if (k == key) {
+                    start = x.z;
+                    cnt = x.w;
+                    break;
                 }
-            }
-            // fill the cache: one writer per cache slot among the lanes that missed
-            const unsigned miss = __ballot_sync(0xffffffffu, lane < 27 && !hit);
-            if (lane < 27 && !hit) {
-                const unsigned same = __match_any_sync(miss, cs);
-                if (lane == __ffs(same) - 1) W.cache[cs] = make_uint4((uint32_t)key, (uint32_t)(key >> 32), start, cnt);
+                if (k == kEmptyKey) break;
+                slot = (slot + 1) & sc.table_mask;
             }
         }
         uint32_t incl = cnt;
@@ -1412,8 +1391,6 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
             const int nblocks = nbx * nby;
             KeptPoint* wq = S.kept + warp * kWarpQueue;
             const MarkBand mband = {S.marks, vbox[0], vbox[2], mv0, mv1, vw, a.err};
-            // the raster stage shared these bytes: start with an empty lookup cache
-            for (int i = lane; i < kCellCache; i += 32) WP.cache[i] = make_uint4(~0u, ~0u, 0u, 0u);
             __syncwarp();
             int wq_head = 0, wq_count = 0;
             for (;;) {
@@ -1760,9 +1737,12 @@ __device__ int claim_vslot(unsigned* mask, int nslots)
 // next hypothesis index from a device counter (zero at launch) and scores
 // it.  The job is read from the kernel parameters, so its fields are
 // constant-bank operands.  MODE kModeTree: the job's hypotheses are edges of the
-// Monotone Scene Generation tree from the state in job.tree.
+// Monotone Scene Generation tree from the state in job.tree.  At most 64
+// registers per thread (128 and 256 threads): four 256-thread blocks, 32 warps,
+// fit an SM when the block's shared memory allows (the default launch shape),
+// which hides latency better than three blocks of 80 registers.
 template <int NT, int MODE, bool BINS>
-__global__ void __launch_bounds__(NT, NT == 512 ? 1 : 768 / NT) k_score(ScoreArgs a)
+__global__ void __launch_bounds__(NT, NT == 512 ? 1 : 1024 / NT) k_score(ScoreArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
@@ -2277,8 +2257,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_gicp(GicpArgs a)
             __syncthreads();
             continue;
         }
-        // the raster stage used these bytes: start with an empty lookup cache
-        for (int i = lane; i < kCellCache; i += 32) WP.cache[i] = make_uint4(~0u, ~0u, 0u, 0u);
         if (threadIdx.x == 0) {
             for (int i = 0; i < 9; ++i) { s_R[i] = (i % 4 == 0) ? 1.0 : 0.0; s_Rf[i] = (float)s_R[i]; }
             for (int i = 0; i < 3; ++i) { s_t[i] = 0.0; s_tf[i] = 0.0f; }

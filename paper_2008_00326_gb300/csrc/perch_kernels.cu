@@ -885,6 +885,7 @@ struct ScoreSmem {
     int* bin_cnt;                 // kBinTiles: triangles binned per z-buffer tile
     int* jo_next;                 // plain scoring: next chunk of J_o's |I cap V|
     int* raster_done;             // plain scoring: warps done with the tile's raster
+    int* vbounds;                 // snapped vertex bounds of the hypothesis (vertex_pass)
 };
 
 // ---- per-hypothesis vertex cache (one slot of global scratch per block) ----
@@ -895,11 +896,15 @@ struct ScoreSmem {
 // triangle that uses it.  Used when 32 W and 32 H fit in int16.
 constexpr int kCulledX = -32768;
 
+//
+// bounds (optional, shared memory, initialised to INT_MAX, INT_MAX, INT_MIN,
+// INT_MIN): the smallest and largest snapped x and y of the vertices kept.
 __device__ __forceinline__ void vertex_pass(const DevScene& sc, const DevMesh& m, const float* P,
-                                            unsigned long long* vc, int nt)
+                                            unsigned long long* vc, int nt, int* bounds = nullptr)
 {
     const float gx0 = (float)(-16 * sc.W), gx1 = (float)(32 * sc.W);
     const float gy0 = (float)(-16 * sc.H), gy1 = (float)(32 * sc.H);
+    int xmin = INT_MAX, ymin = INT_MAX, xmax = INT_MIN, ymax = INT_MIN;
 #pragma unroll 2
     for (int i = threadIdx.x; i < m.n_verts; i += nt) {
         float4 v = __ldg(&m.verts[i]);
@@ -914,13 +919,28 @@ __device__ __forceinline__ void vertex_pass(const DevScene& sc, const DevMesh& m
             float sx = __fmul_rn(__fadd_rn(__fmul_rn(sc.fx, __fdiv_rn(X, Z)), sc.cx), 16.0f);
             float sy = __fmul_rn(__fadd_rn(__fmul_rn(sc.fy, __fdiv_rn(Y, Z)), sc.cy), 16.0f);
             if (sx >= gx0 && sx < gx1 && sy >= gy0 && sy < gy1) {
-                uint32_t xs = (uint16_t)(int16_t)__float2int_rn(sx);
-                uint32_t ys = (uint16_t)(int16_t)__float2int_rn(sy);
+                const int xi = __float2int_rn(sx), yi = __float2int_rn(sy);
+                xmin = min(xmin, xi); xmax = max(xmax, xi);
+                ymin = min(ymin, yi); ymax = max(ymax, yi);
+                uint32_t xs = (uint16_t)(int16_t)xi;
+                uint32_t ys = (uint16_t)(int16_t)yi;
                 rec = (unsigned long long)(xs | (ys << 16)) |
                       ((unsigned long long)__float_as_uint(__frcp_rn(Z)) << 32);
             }
         }
         vc[i] = rec;
+    }
+    if (bounds) {
+        xmin = __reduce_min_sync(0xffffffffu, xmin);
+        ymin = __reduce_min_sync(0xffffffffu, ymin);
+        xmax = __reduce_max_sync(0xffffffffu, xmax);
+        ymax = __reduce_max_sync(0xffffffffu, ymax);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&bounds[0], xmin);
+            atomicMin(&bounds[1], ymin);
+            atomicMax(&bounds[2], xmax);
+            atomicMax(&bounds[3], ymax);
+        }
     }
 }
 
@@ -1549,6 +1569,7 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
     if (threadIdx.x < 12) s_pose[threadIdx.x] = J.poses[h * 12 + threadIdx.x];
     if (TREE && threadIdx.x == 0) *S.refused = 0;
     if (threadIdx.x == 0) *S.jo_next = 0;
+    if (threadIdx.x < 4) S.vbounds[threadIdx.x] = threadIdx.x < 2 ? INT_MAX : INT_MIN;
     __syncthreads();
     // the two boxes in two warps, in parallel with each other and with the
     // other warps' share of the vertex pass
@@ -1566,8 +1587,25 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         }
     }
     const bool use_vc = vc != nullptr;
-    if (use_vc) vertex_pass(sc, J.m, s_pose, vc, NT);
+    if (use_vc) vertex_pass(sc, J.m, s_pose, vc, NT, S.vbounds);
     __syncthreads();
+    // The pixel box of the render: the projected object-frame box, tightened
+    // (with the vertex cache) to the samples between the kept vertices'
+    // smallest and largest snapped coordinates -- every covered sample lies
+    // in its triangle's vertex box, so nothing outside can be covered.
+    int rb[4] = {s_rbox[0], s_rbox[1], s_rbox[2], s_rbox[3]};
+    if (use_vc) {
+        const int* vb = S.vbounds;
+        if (vb[0] > vb[2]) {
+            rb[2] = rb[0];
+            rb[3] = rb[1];
+        } else {
+            rb[0] = max(rb[0], ceil16(vb[0]));
+            rb[1] = max(rb[1], ceil16(vb[1]));
+            rb[2] = max(rb[0], min(rb[2], floor16(vb[2]) + 1));
+            rb[3] = max(rb[1], min(rb[3], floor16(vb[3]) + 1));
+        }
+    }
 
     // The admissible box is handled in bands of rows that fit the marks
     // bitset (jo_mode 1: one 64-bit key per pixel); each band repeats the
@@ -1588,25 +1626,25 @@ __device__ void score_one(const ScoreArgs& a, const Job& J, long long h, const S
         for (int i = threadIdx.x; i < mwords; i += NT) S.marks[i] = mfill;
         __syncthreads();
         if (*s_k32) {
-            if (use_vc) score_tiles<NT, true, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
+            if (use_vc) score_tiles<NT, true, true, MODE, BINS>(a, J, P, vc, rb, S, s_vbox, mv0, mv1, band == 0, jr,
                                                                n_in, n_marked);
-            else score_tiles<NT, true, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
+            else score_tiles<NT, true, false, MODE, BINS>(a, J, P, vc, rb, S, s_vbox, mv0, mv1, band == 0, jr,
                                                                n_in, n_marked);
         } else {
-            if (use_vc) score_tiles<NT, false, true, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
+            if (use_vc) score_tiles<NT, false, true, MODE, BINS>(a, J, P, vc, rb, S, s_vbox, mv0, mv1, band == 0, jr,
                                                                n_in, n_marked);
-            else score_tiles<NT, false, false, MODE, BINS>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1, band == 0, jr,
+            else score_tiles<NT, false, false, MODE, BINS>(a, J, P, vc, rb, S, s_vbox, mv0, mv1, band == 0, jr,
                                                                n_in, n_marked);
         }
         __syncthreads();
         if (jo1 && sc.color_check) {
             // Eq. 4 from the observed side, once the band's keys are final
             if (*s_k32) {
-                if (use_vc) jo_colour_band<NT, true, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
-                else jo_colour_band<NT, true, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
+                if (use_vc) jo_colour_band<NT, true, true>(a, J, P, vc, rb, S, s_vbox, mv0, mv1);
+                else jo_colour_band<NT, true, false>(a, J, P, vc, rb, S, s_vbox, mv0, mv1);
             } else {
-                if (use_vc) jo_colour_band<NT, false, true>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
-                else jo_colour_band<NT, false, false>(a, J, P, vc, s_rbox, S, s_vbox, mv0, mv1);
+                if (use_vc) jo_colour_band<NT, false, true>(a, J, P, vc, rb, S, s_vbox, mv0, mv1);
+                else jo_colour_band<NT, false, false>(a, J, P, vc, rb, S, s_vbox, mv0, mv1);
             }
         }
         // plain scoring: J_o's marked part was counted as the marks were set
@@ -1747,7 +1785,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 1024 / NT) k_score(ScoreAr
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_pose[12];
     __shared__ int s_rbox[4], s_vbox[4], s_k32, s_next, s_slot, s_refused, s_bin_cnt[kBinTiles], s_jo_next,
-        s_raster_done;
+        s_raster_done, s_vbounds[4];
     __shared__ long long s_h;
     __shared__ int s_red[3][NT / 32];
 
@@ -1763,6 +1801,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 1 : 1024 / NT) k_score(ScoreAr
     S.bin_cnt = s_bin_cnt;
     S.jo_next = &s_jo_next;
     S.raster_done = &s_raster_done;
+    S.vbounds = s_vbounds;
     if (threadIdx.x == 0) s_slot = a.vcache ? claim_vslot(a.vmask, a.vslots) : -1;
     __syncthreads();
     unsigned long long* vc = s_slot >= 0 ? a.vcache + (size_t)s_slot * a.vstride : nullptr;

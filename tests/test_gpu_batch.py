@@ -116,7 +116,7 @@ def test_autotune_keeps_results(P, loaded):
     dp = torch.from_numpy(poses).cuda()
     dc = torch.zeros((len(poses), 2), dtype=torch.int32, device="cuda")
     t, z, b = P.perch_autotune(ctx.ctx, items, dp, dc)
-    assert t in (128, 256, 512) and z in (2048, 4096, 8192, 16384)
+    assert t in (128, 256, 512) and z in (2048, 4096, 7064, 8192, 16384) and b in (0, 1024, 4096)
     assert P.perch_autotune(ctx.ctx, items, dp, dc) == (t, z, b)    # remembered for the class
     got = P.perch_score_batch(ctx.ctx, items, poses)
     for k, (g, a) in enumerate(zip(_split(got, specs), alone)):

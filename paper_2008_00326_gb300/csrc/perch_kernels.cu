@@ -1456,6 +1456,17 @@ __device__ void score_tiles(const ScoreArgs& a, const Job& J, const float* P, co
                                 float3 q = back_project(sc, u, v, d);
                                 kp.x = q.x; kp.y = q.y; kp.z = q.z; kp.pix = (uint32_t)u | ((uint32_t)v << 16);
                                 kept = true;
+                                if (sc.near_bits) {
+                                    // no observed point in the 27 cells: unexplained
+                                    // without a search (the radius search's own filter)
+                                    const long long b = near_index(sc, cell_coord(q.x, sc.inv_cell),
+                                                                   cell_coord(q.y, sc.inv_cell),
+                                                                   cell_coord(q.z, sc.inv_cell));
+                                    if (b < 0 || !((__ldg(&sc.near_bits[b >> 5]) >> (b & 31)) & 1u)) {
+                                        kept = false;
+                                        if (count_jr) ++jr_local;
+                                    }
+                                }
                             }
                         }
                     }

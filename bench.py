@@ -212,10 +212,13 @@ def cpu_baseline(sc, seconds, rng_seed=0):
         O.score(osc, oms[req.mesh_index], req.poses[pick], label=req.label, roi=req.roi, threads=1, nn="grid")
         t1 += time.perf_counter() - t0
         n1 += len(pick)
-    # work counts: brute force on a few hypotheses per object
+    # work counts: brute force on a fixed sample of 32 hypotheses per object
+    # (its own seed, so that every run counts the same hypotheses and the
+    # roofline's achieved rate moves only with the kernel's time)
     work = []
+    wrng = np.random.default_rng(12345)
     for req in sc.requests:
-        pick = rng.choice(len(req.poses), max(1, threads), replace=False)
+        pick = wrng.choice(len(req.poses), min(32, len(req.poses)), replace=False)
         _, _, w = O.score(osc, oms[req.mesh_index], req.poses[pick], label=req.label, roi=req.roi,
                           with_work=True, nn="brute")
         work.append(np.concatenate([w, np.full((len(w), 1), req.mesh_index, np.int64)], axis=1))
